@@ -1,0 +1,281 @@
+#!/usr/bin/env python
+"""Benchmark of the TRMC-R hot path on GB300: one step = free transport with
+specular walls + stable cell sort + collision step (split, recursive trees,
+VHS hard-sphere acceptance, Maxwellian renormalisation, TRMC-RAD) over the
+1D Riemann shock-tube workload: four tubes on [0,1] (one per Knudsen number
+1e-1, 1e-2, 1e-3, 1e-4), 400 cells and 500 particles per cell on average
+each, CFL 0.5, FP64.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per rank, launched by torchrun), each
+on its own problem ids; value is the total over ranks.  --impl reference
+times the CPU oracle (FP64, all host cores) on a bounded sample of the same
+workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+EPS = (1e-1, 1e-2, 1e-3, 1e-4)
+N_CELLS, MEAN = 400, 500
+WORKLOAD = ("1D Riemann shock tube on [0,1] (rho 1/0.125, T 1/0.8, u 0), hard-sphere VHS, specular walls, "
+            "CFL 0.5, TRMC-RAD (P_xx indicator, delta 0.005/0.01, m0 2); 4 tubes x 400 cells x 500 "
+            "particles/cell mean, eps 1e-1/1e-2/1e-3/1e-4, FP64")
+METRIC = "particle-steps/s"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.devnull if False else f"/tmp/trmc_clocks_{os.getpid()}.csv", "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        self.proc.wait()
+        self.out.close()
+        rows = []
+        for line in open(self.out.name):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_tube_rate(n_cells, mean, steps, threads, seed=0, budget_s=None):
+    """Particle-steps/s of the FP64 CPU oracle on one shock tube (eps 1e-2)."""
+    from oracle import oracle as O
+    from paper_1009_2768_gb300 import synth
+    counts = synth.shock_tube_counts(n_cells, mean)
+    cs = synth.starts(counts)
+    n = int(cs[-1])
+    ci = np.zeros((n_cells, O.INIT_COLS))
+    for c in range(n_cells):
+        ci[c] = [O.INIT_MAXWELL, 0, 0, 0, 1.0 if c < n_cells // 2 else 0.8, 0, 0, c / n_cells, (c + 1) / n_cells]
+    x, v = O.init_cells(ci, cs, seed)
+    rho_scale = 0.5625 * n_cells / n
+    cp = np.tile([1e-2, 0.0, rho_scale, 1.0], (n_cells, 1))
+    prm = O.collide_params(trunc=O.TRUNC_RAD, m=2, seed=seed)
+    ms = np.full(n_cells, 2, np.int32)
+    doms = [(0, n_cells, 0.0, 1.0)]
+    done, t0 = 0, time.perf_counter()
+    for s in range(steps):
+        dt = O.cfl_dt(v, cs, doms, 0.5)
+        x, v, cs = O.transport(x, v, cs, doms, dt)
+        cp[:, 1] = dt[0]
+        v, _, ms = O.collide(v, cs, prm, s, m_state=ms, cell_param=cp.ravel(), threads=threads)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return n * done / el, n, done, el
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle.build import build_oracle
+    build_oracle()
+    threads = os.cpu_count() or 1
+    # bounded sample: one tube, cells scaled so that W + K steps take about two minutes
+    rate, n, _, el = oracle_tube_rate(40, MEAN, 2, threads)
+    per_step = n / rate
+    cells = int(np.clip(40 * 120.0 / max(per_step * (args.steps + args.warmup) * 10, 1e-9), 8, N_CELLS))
+    cells -= cells % 2
+    oracle_tube_rate(cells, MEAN, args.warmup, threads)
+    rate, n, done, el = oracle_tube_rate(cells, MEAN, args.steps, threads)
+    sample = f"one tube (eps 1e-2) of {cells} cells x {MEAN}/cell mean ({n} particles), {done} steps"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ------------------------------------------------------------------ GPU arm
+def ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1009_2768_gb300 import build
+    build.build()
+    from paper_1009_2768_gb300 import trmc as T
+    from paper_1009_2768_gb300.workloads import ShockTubes
+
+    sim = ShockTubes(EPS, N_CELLS, MEAN, precision=T.FP64, seed=rank)
+    n = sim.n_particles
+    stats = torch.zeros(len(T.STATS_FIELDS), dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")      # > L2 (129 MB)
+    for _ in range(args.warmup):
+        sim.step()
+    T.trmc_check(sim.ctx)
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.2)
+    t_wall = time.perf_counter()
+    for k in range(K):
+        flush.zero_()
+        sim.step(stats=stats, events=ev[k])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    T.trmc_check(sim.ctx)
+    step_ms = np.array([ev[k][0].elapsed_time(ev[k][2]) for k in range(K)])
+    tr_ms = np.array([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)])
+    co_ms = np.array([ev[k][1].elapsed_time(ev[k][2]) for k in range(K)])
+    total_ms = float(step_ms.sum())
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n * world * K / (total_ms / 1e3)
+    st = dict(zip(T.STATS_FIELDS, stats.cpu().numpy().tolist()))
+
+    # roofline of the dominant kernel, from the same events
+    peak, peak_kind = peaks()
+    rb = 8  # bytes per velocity component (FP64)
+    collide_bytes = 3 * rb * (n + st["changed"] / K)               # read all, write changed (per launch)
+    transport_bytes = (2 * rb + 8 * rb) * n                        # count: x,vx; scatter: read x,v + write x,v
+    co_avg, tr_avg = co_ms.mean() / 1e3, tr_ms.mean() / 1e3
+    if co_avg >= tr_avg:
+        kern, abytes, dur = "collide_kernel<double>", collide_bytes, co_avg
+    else:
+        kern, abytes, dur = "transport (count+scan+scatter)", transport_bytes, tr_avg
+    achieved = abytes / dur / 1e9
+    roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+            "collide_ms": float(co_ms.mean()), "transport_ms": float(tr_ms.mean()),
+            "algorithmic_bytes_per_launch": abytes}
+
+    # end to end: host-resident state, H2D + step + D2H every step
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty_like(sim.state.x, device="cpu").pin_memory()
+        hv = torch.empty_like(sim.state.v, device="cpu").pin_memory()
+        hx.copy_(sim.state.x)
+        hv.copy_(sim.state.v)
+        hcs = sim.state.cell_start.cpu().pin_memory()
+        Ke = max(1, min(K, 200))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(Ke):
+            sim.state.x.copy_(hx, non_blocking=True)
+            sim.state.v.copy_(hv, non_blocking=True)
+            sim.state.cell_start.copy_(hcs, non_blocking=True)
+            sim.step()
+            hx.copy_(sim.state.x, non_blocking=True)
+            hv.copy_(sim.state.v, non_blocking=True)
+            hcs.copy_(sim.state.cell_start, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        h2d = hx.numel() * hx.element_size() + hv.numel() * hv.element_size() + hcs.numel() * 8
+        e2e = {"value": n * world * Ke / (e_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": h2d, "steps": Ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle.build import build_oracle
+        build_oracle()
+        threads = os.cpu_count() or 1
+        rate, nn, done, el = oracle_tube_rate(N_CELLS, MEAN, 1000, threads, budget_s=15.0)
+        cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
+               "sample": f"one full tube (eps 1e-2, {nn} particles), {done} steps in {el:.1f} s"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles_per_gpu": n, "cells_per_gpu": N_CELLS * len(EPS),
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": sim.launches_per_step * K, "clocks": clk,
+            "step_stats": {k: st[k] / K for k in ("collisions", "dummy", "maxwell", "changed", "passes")},
+            "wall_s": t_wall}))
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * trmc.h -- C ABI of libtrmc, a GB300 (sm_103a) implementation of the
+ * collision step of the recursive Time Relaxed Monte Carlo method (TRMC-R)
+ * together with the free transport and the cell sort around it.
+ *
+ * Paper: S. Trazzi, L. Pareschi, B. Wennberg, "Adaptive and Recursive Time
+ * Relaxed Monte Carlo methods for rarefied gas dynamics", arXiv:1009.2768.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named *_dev and every pointer inside trmc_state are CUDA device
+ *    pointers owned by the caller; the library never frees them.  Other
+ *    pointers are host pointers, read before the call returns.
+ *  - Every call is asynchronous on the given stream (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream) and returns a trmc_status.  Argument
+ *    errors are found on the host and returned at once with nothing launched.
+ *  - Errors found by a kernel (a cell larger than the workspace, a particle
+ *    that moved more than one cell in a transport step) set a device status
+ *    word; trmc_check() reads it (synchronising the stream) and clears it.
+ *  - One trmc_ctx per host thread; a context holds the library's workspace
+ *    (device scratch) and must not be used by two streams at once.
+ *  - Particle arrays are structure-of-arrays, sorted by cell: cell c owns the
+ *    particles [cell_start[c], cell_start[c+1]).  They are double in
+ *    TRMC_FP64 contexts and float in TRMC_FP32_MIXED contexts.
+ *  - Results depend only on (seed, problem id, cell index within the problem,
+ *    step, particle order within the cell), never on launch shape or on
+ *    which other cells share the call.
+ */
+#ifndef TRMC_H
+#define TRMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum trmc_status {
+    TRMC_OK = 0,
+    TRMC_ERR_ARG = 1,       /* invalid argument (found on the host)            */
+    TRMC_ERR_CUDA = 2,      /* a CUDA call failed                              */
+    TRMC_ERR_NOMEM = 3,     /* device allocation failed                        */
+    TRMC_ERR_CAPACITY = 4,  /* a cell did not fit in the workspace             */
+    TRMC_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up              */
+    TRMC_ERR_STATE = 6      /* state inconsistent (e.g. particle moved > 1 cell) */
+} trmc_status;
+
+typedef enum trmc_precision {
+    TRMC_FP64 = 0,          /* velocities and all arithmetic in double          */
+    TRMC_FP32_MIXED = 1     /* float velocities and collisions; moments, bounds,
+                               level probabilities and the renormalisation in double */
+} trmc_precision;
+
+/* Tree truncation (Sec. 4.1 fixed order m, Sec. 4.3 adaptive TRMC-RAD). */
+typedef enum trmc_trunc {
+    TRMC_TRUNC_FIXED = 0,     /* m = params.m_fixed                              */
+    TRMC_TRUNC_RAD = 1,       /* m per cell in state.m_max, adapted each step     */
+    TRMC_TRUNC_UNLIMITED = 2  /* m = params.m_cap (depth limited only by N)       */
+} trmc_trunc;
+
+typedef enum trmc_indicator { TRMC_IND_PXX = 0, TRMC_IND_M4 = 1 } trmc_indicator;
+
+typedef enum trmc_init_kind {
+    TRMC_INIT_MAXWELL = 0,    /* Maxwellian M(rho,u,T), Eq. Max                     */
+    TRMC_INIT_BIMAXWELL = 1,  /* T_par along x, T_perp along y and z                */
+    TRMC_INIT_BKW = 2         /* BKW solution for Maxwell molecules, shape K        */
+} trmc_init_kind;
+
+#define TRMC_MCAP 64            /* deepest collision tree supported                 */
+#define TRMC_INIT_COLS 9        /* kind, ux, uy, uz, T (or T_par), T_perp, K, x_lo, x_hi */
+#define TRMC_MOM_COLS 10        /* N, rho, ux, uy, uz, T, P_xx, M_4, E, max|v|^2     */
+#define TRMC_REPORT_LEN (16 + 3 * (TRMC_MCAP + 2))
+
+/* Per-cell physical parameters (device array, optional).  rho_c = N_c * rho_scale. */
+typedef struct trmc_cell_param {
+    double eps;        /* Knudsen number, Eq. BE-r                          */
+    double dt;         /* time step (written by trmc_transport in CFL mode)  */
+    double rho_scale;  /* particle mass / cell volume                        */
+    double alpha;      /* VHS exponent: B = |q|^alpha (0 Maxwell, 1 hard sphere) */
+} trmc_cell_param;
+
+/* The particle state.  All pointers are device pointers owned by the caller. */
+typedef struct trmc_state {
+    void *vx, *vy, *vz;           /* [capacity] velocities                        */
+    void *x;                      /* [capacity] positions; NULL if space-homogeneous */
+    void *vx_alt, *vy_alt, *vz_alt, *x_alt;  /* [capacity] sort targets (transport) */
+    int64_t *cell_start;          /* [n_cells+1]                                  */
+    int64_t *cell_start_alt;      /* [n_cells+1] sort target (transport)          */
+    int32_t *m_max;               /* [n_cells] TRMC-RAD tree depth; NULL unless RAD */
+    trmc_cell_param *cell_param;  /* [n_cells] or NULL (then the params scalars)   */
+    const uint64_t *cell_key;     /* [n_cells] (problem << 32 | cell in problem) or NULL */
+    double *cell_vmax2;           /* [n_cells] max |v|^2 after the last collide, or NULL */
+    int64_t capacity;             /* length of each particle array                */
+    int32_t n_cells;
+    uint32_t problem_id;          /* used when cell_key is NULL                   */
+} trmc_state;
+
+/* Collision-step parameters (host struct, read at call time). */
+typedef struct trmc_collide_params {
+    double dt, eps, alpha, rho_scale;  /* for cells without a trmc_cell_param      */
+    double delta1, delta2;             /* TRMC-RAD thresholds (Sec. 4.3)            */
+    int32_t trunc;                     /* trmc_trunc                                */
+    int32_t m_fixed;                   /* order for TRMC_TRUNC_FIXED                */
+    int32_t m_min, m_cap;              /* TRMC-RAD bounds, 1 <= m_min <= m_cap <= TRMC_MCAP */
+    int32_t indicator;                 /* trmc_indicator for TRMC-RAD               */
+    int32_t reserved;                  /* must be 0                                 */
+} trmc_collide_params;
+
+/* One 1D problem for trmc_transport: cells [cell_begin, cell_begin+n_cells)
+ * of equal width cover [x_lo, x_hi]; both ends are specular walls. */
+typedef struct trmc_domain {
+    int32_t cell_begin, n_cells;
+    double x_lo, x_hi;
+} trmc_domain;
+
+/* Step statistics, accumulated with integer atomics (device struct, optional). */
+typedef struct trmc_stats {
+    unsigned long long collisions;   /* real binary collisions                       */
+    unsigned long long dummy;        /* VHS dummy (rejected) collisions              */
+    unsigned long long maxwell;      /* particles resampled from the Maxwellian       */
+    unsigned long long exceed;       /* pairs with |q|^alpha above the bound Sigma    */
+    unsigned long long passes;       /* TRMC-RAD passes (1 per cell without a redo)   */
+    unsigned long long feas;         /* tree-depth reductions for lack of leaves      */
+    unsigned long long cells;        /* cells processed                               */
+    unsigned long long capacity_skips; /* cells skipped: larger than the workspace     */
+    unsigned long long changed;      /* particles whose velocity was rewritten         */
+    unsigned long long particles;    /* particles in the processed cells               */
+} trmc_stats;
+
+typedef struct trmc_ctx trmc_ctx;
+
+/* Create a context on the current CUDA device.  workspace_bytes sizes the
+ * device scratch used by cells whose working set does not fit in shared
+ * memory (0 = a default of 1 GiB).  seed keys every random draw. */
+trmc_status trmc_create(trmc_ctx **out, int32_t precision, uint64_t seed, size_t workspace_bytes);
+trmc_status trmc_destroy(trmc_ctx *ctx);
+/* Text of the last error of this context (static storage, never NULL). */
+const char *trmc_last_error(const trmc_ctx *ctx);
+/* Synchronise the stream, then return and clear the device status word. */
+trmc_status trmc_check(trmc_ctx *ctx, void *stream);
+
+/* Sample initial velocities (and positions, if state->x != NULL) for every
+ * particle of every cell, from the synthetic closed-form laws listed in
+ * trmc_init_kind.  cell_init_dev: [n_cells][TRMC_INIT_COLS] doubles on the
+ * device (kind, ux, uy, uz, T or T_par, T_perp, K, x_lo, x_hi).  Also fills
+ * cell_vmax2 when present.  Draws use Philox tag INIT at step 0. */
+trmc_status trmc_init_cells(trmc_ctx *ctx, trmc_state *state, const double *cell_init_dev, void *stream);
+
+/* One homogeneous collision step in every cell (Sec. 3.1 splitting, Eq. WST,
+ * Alg. 4.2-4.4, conservative Maxwellian resampling, TRMC-RAD of Sec. 4.3).
+ * The cell's mass, momentum and energy are conserved to round-off.
+ * step keys the random draws.  report_dev (optional) receives
+ * [n_cells][TRMC_REPORT_LEN] int64 per-cell plan records; stats_dev
+ * (optional) accumulates trmc_stats. */
+trmc_status trmc_collide(trmc_ctx *ctx, trmc_state *state, const trmc_collide_params *params,
+                         uint64_t step, int64_t *report_dev, trmc_stats *stats_dev, void *stream);
+
+/* Free transport x += v_x dt with specular walls, then a stable regrouping
+ * of the particles by cell (operator splitting, Sec. 3.1).  domains_dev:
+ * [n_domains] trmc_domain on the device.  If cfl > 0, dt_dev[d] receives
+ * cfl * dx / max|v| over domain d (from state->cell_vmax2, which must be
+ * present) and, when state->cell_param is present, cell_param[c].dt is set
+ * for every cell of the domain; otherwise dt_dev[d] is read.  Requires
+ * dt * max|v_x| <= dx (a particle moves at most one cell).  The sorted
+ * particles land in the *_alt arrays and the state's pointers are swapped,
+ * so on return state->vx etc. name the sorted arrays. */
+trmc_status trmc_transport(trmc_ctx *ctx, trmc_state *state, const trmc_domain *domains_dev,
+                           int32_t n_domains, double cfl, double *dt_dev, void *stream);
+
+/* Per-cell moments [n_cells][TRMC_MOM_COLS] doubles on the device:
+ * N, rho = N rho_scale, u (3), T, P_xx, M_4 = <|v|^4>, E = <|v|^2>/2, max |v|^2
+ * (Sec. 2 and Sec. 5.1 definitions, per unit mass). */
+trmc_status trmc_moments(trmc_ctx *ctx, const trmc_state *state, double *out_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRMC_H */

@@ -1,0 +1,173 @@
+// api.cu -- the C ABI of libtrmc: context lifetime, argument checks,
+// launches.  Every entry point validates on the host, launches
+// asynchronously on the caller's stream and returns a trmc_status.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace trmc {
+
+trmc_status set_error(trmc_ctx *ctx, trmc_status code, const std::string &msg)
+{
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+trmc_status cuda_error(trmc_ctx *ctx, cudaError_t e, const char *where)
+{
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+    return set_error(ctx, TRMC_ERR_CUDA, buf);
+}
+
+namespace {
+
+constexpr size_t kControlBytes = 4096;
+
+trmc_status check_state(trmc_ctx *ctx, const trmc_state *st)
+{
+    if (!st) return set_error(ctx, TRMC_ERR_ARG, "state is NULL");
+    if (st->n_cells < 0) return set_error(ctx, TRMC_ERR_ARG, "n_cells < 0");
+    if (st->n_cells > 0 && (!st->vx || !st->vy || !st->vz || !st->cell_start))
+        return set_error(ctx, TRMC_ERR_ARG, "state velocity arrays or cell_start are NULL");
+    if (st->capacity < 0) return set_error(ctx, TRMC_ERR_ARG, "capacity < 0");
+    return TRMC_OK;
+}
+
+}  // namespace
+}  // namespace trmc
+
+using namespace trmc;
+
+extern "C" {
+
+trmc_status trmc_create(trmc_ctx **out, int32_t precision, uint64_t seed, size_t workspace_bytes)
+{
+    if (!out) return TRMC_ERR_ARG;
+    *out = nullptr;
+    if (precision != TRMC_FP64 && precision != TRMC_FP32_MIXED) return TRMC_ERR_ARG;
+    trmc_ctx *ctx = new (std::nothrow) trmc_ctx();
+    if (!ctx) return TRMC_ERR_NOMEM;
+    ctx->precision = precision;
+    ctx->seed = seed;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    cudaDeviceProp prop;
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, ctx->device);
+    if (e != cudaSuccess) { delete ctx; return TRMC_ERR_CUDA; }
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    if (workspace_bytes == 0) workspace_bytes = size_t(1) << 30;
+    ctx->workspace_bytes = workspace_bytes + kControlBytes;
+    e = cudaMalloc(&ctx->workspace, ctx->workspace_bytes);
+    if (e != cudaSuccess) { delete ctx; return TRMC_ERR_NOMEM; }
+    e = cudaMemset(ctx->workspace, 0, kControlBytes);
+    if (e != cudaSuccess) { cudaFree(ctx->workspace); delete ctx; return TRMC_ERR_CUDA; }
+    ctx->status = reinterpret_cast<int *>(ctx->workspace);
+    ctx->tickets = reinterpret_cast<unsigned int *>(ctx->workspace + 64);
+    ctx->slabs = ctx->workspace + kControlBytes;
+    ctx->slabs_bytes = workspace_bytes;
+    *out = ctx;
+    return TRMC_OK;
+}
+
+trmc_status trmc_destroy(trmc_ctx *ctx)
+{
+    if (!ctx) return TRMC_ERR_ARG;
+    if (ctx->workspace) cudaFree(ctx->workspace);
+    if (ctx->tr_counts) cudaFree(ctx->tr_counts);
+    delete ctx;
+    return TRMC_OK;
+}
+
+const char *trmc_last_error(const trmc_ctx *ctx)
+{
+    if (!ctx) return "no context";
+    return ctx->last_error.c_str();
+}
+
+trmc_status trmc_check(trmc_ctx *ctx, void *stream)
+{
+    if (!ctx) return TRMC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "trmc_check");
+    int st[2] = {0, 0};
+    e = cudaMemcpy(st, ctx->status, sizeof st, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "trmc_check read");
+    if (st[0] == 0) return TRMC_OK;
+    e = cudaMemset(ctx->status, 0, 2 * sizeof(int));
+    if (e != cudaSuccess) return cuda_error(ctx, e, "trmc_check clear");
+    char buf[160];
+    const char *what = st[0] == TRMC_ERR_CAPACITY ? "cell did not fit in the workspace (left unchanged)"
+                       : st[0] == TRMC_ERR_STATE  ? "a particle moved more than one cell (dt too large)"
+                       : st[0] == TRMC_ERR_TIMEOUT ? "device wait timed out"
+                                                   : "device error";
+    std::snprintf(buf, sizeof buf, "%s; first cell %d", what, st[1]);
+    return set_error(ctx, static_cast<trmc_status>(st[0]), buf);
+}
+
+trmc_status trmc_init_cells(trmc_ctx *ctx, trmc_state *state, const double *cell_init_dev, void *stream)
+{
+    if (!ctx) return TRMC_ERR_ARG;
+    trmc_status r = check_state(ctx, state);
+    if (r != TRMC_OK) return r;
+    if (state->n_cells > 0 && !cell_init_dev) return set_error(ctx, TRMC_ERR_ARG, "cell_init_dev is NULL");
+    return launch_init(ctx, state, cell_init_dev, static_cast<cudaStream_t>(stream));
+}
+
+trmc_status trmc_collide(trmc_ctx *ctx, trmc_state *state, const trmc_collide_params *p, uint64_t step,
+                         int64_t *report_dev, trmc_stats *stats_dev, void *stream)
+{
+    if (!ctx) return TRMC_ERR_ARG;
+    trmc_status r = check_state(ctx, state);
+    if (r != TRMC_OK) return r;
+    if (!p) return set_error(ctx, TRMC_ERR_ARG, "params is NULL");
+    if (p->reserved != 0) return set_error(ctx, TRMC_ERR_ARG, "params.reserved must be 0");
+    if (p->trunc < TRMC_TRUNC_FIXED || p->trunc > TRMC_TRUNC_UNLIMITED) return set_error(ctx, TRMC_ERR_ARG, "bad trunc");
+    if (p->m_cap < 1 || p->m_cap > TRMC_MCAP) return set_error(ctx, TRMC_ERR_ARG, "m_cap outside [1, TRMC_MCAP]");
+    if (p->trunc == TRMC_TRUNC_FIXED && (p->m_fixed < 1 || p->m_fixed > p->m_cap))
+        return set_error(ctx, TRMC_ERR_ARG, "m_fixed outside [1, m_cap]");
+    if (p->trunc == TRMC_TRUNC_RAD) {
+        if (!state->m_max) return set_error(ctx, TRMC_ERR_ARG, "TRMC-RAD needs state.m_max");
+        if (p->m_min < 1 || p->m_min > p->m_cap) return set_error(ctx, TRMC_ERR_ARG, "m_min outside [1, m_cap]");
+        if (!(p->delta1 >= 0.0) || !(p->delta2 >= p->delta1)) return set_error(ctx, TRMC_ERR_ARG, "need 0 <= delta1 <= delta2");
+        if (p->indicator != TRMC_IND_PXX && p->indicator != TRMC_IND_M4) return set_error(ctx, TRMC_ERR_ARG, "bad indicator");
+    }
+    if (!state->cell_param) {
+        if (!(p->eps > 0.0)) return set_error(ctx, TRMC_ERR_ARG, "eps must be > 0");
+        if (!(p->dt >= 0.0)) return set_error(ctx, TRMC_ERR_ARG, "dt must be >= 0");
+        if (!(p->alpha >= 0.0 && p->alpha <= 1.0)) return set_error(ctx, TRMC_ERR_ARG, "alpha outside [0, 1]");
+        if (!(p->rho_scale >= 0.0)) return set_error(ctx, TRMC_ERR_ARG, "rho_scale must be >= 0");
+    }
+    if (state->n_cells == 0) return TRMC_OK;
+    return launch_collide(ctx, state, p, step, report_dev, stats_dev, static_cast<cudaStream_t>(stream));
+}
+
+trmc_status trmc_transport(trmc_ctx *ctx, trmc_state *state, const trmc_domain *domains_dev, int32_t n_domains,
+                           double cfl, double *dt_dev, void *stream)
+{
+    if (!ctx) return TRMC_ERR_ARG;
+    trmc_status r = check_state(ctx, state);
+    if (r != TRMC_OK) return r;
+    if (state->n_cells == 0) return TRMC_OK;
+    if (!state->x || !state->x_alt || !state->vx_alt || !state->vy_alt || !state->vz_alt || !state->cell_start_alt)
+        return set_error(ctx, TRMC_ERR_ARG, "transport needs x and the *_alt arrays");
+    if (n_domains < 1 || !domains_dev) return set_error(ctx, TRMC_ERR_ARG, "need at least one domain");
+    if (!dt_dev) return set_error(ctx, TRMC_ERR_ARG, "dt_dev is NULL");
+    if (cfl > 1.0) return set_error(ctx, TRMC_ERR_ARG, "cfl > 1 would move particles more than one cell");
+    if (cfl > 0.0 && !state->cell_vmax2) return set_error(ctx, TRMC_ERR_ARG, "CFL mode needs state.cell_vmax2");
+    return launch_transport(ctx, state, domains_dev, n_domains, cfl, dt_dev, static_cast<cudaStream_t>(stream));
+}
+
+trmc_status trmc_moments(trmc_ctx *ctx, const trmc_state *state, double *out_dev, void *stream)
+{
+    if (!ctx) return TRMC_ERR_ARG;
+    trmc_status r = check_state(ctx, state);
+    if (r != TRMC_OK) return r;
+    if (state->n_cells > 0 && !out_dev) return set_error(ctx, TRMC_ERR_ARG, "out_dev is NULL");
+    return launch_moments(ctx, state, out_dev, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

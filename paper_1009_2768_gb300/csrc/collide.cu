@@ -1,0 +1,714 @@
+// collide.cu -- the TRMC-R collision step on sm_103a.
+//
+// One CTA handles one cell at a time (persistent CTAs, cells taken from a
+// ticket counter).  The cell's velocities are staged in shared memory when
+// they fit, otherwise in a per-CTA slab of the context's device workspace.
+// Per cell, in order:
+//   1. moments (FP64 block reductions): momentum, energy, mean, VHS bound
+//      Sigma = (2 max|v - u|)^alpha, mu = rho Sigma, q = exp(-mu dt / eps);
+//   2. split into collision sets N_0..N_m, N_{m+1} with Iround (Alg. 4.2);
+//   3. tree plan, top level first: per level n, C_n = ceil((N_n + D_n)/2)
+//      collisions (odd counts: fair coin between dropping one quota particle
+//      and keeping a surplus output), each taking k uniform in {0..n-1}
+//      (Alg. 4.1/4.3); the label histogram of level n fixes the demand D_k
+//      on the levels below; leaves that cannot be served lower the depth;
+//   4. roles: a Feistel permutation of the cell's particles picks the
+//      uncollided, the leaves and the thermalised set (the "random choice");
+//   5. collision waves, level 1 first, all collisions of a level in
+//      parallel (Eq. Maxwell_coll, sigma from Eq. n3d, VHS acceptance of
+//      Alg. 4.4); products go to their consumers or outputs through a
+//      per-level permutation (the store of siblings, Sec. 4.1);
+//   6. outputs replace the leaves; TRMC-RAD (Sec. 4.3) tests the relative
+//      change of the indicator with the analytic Maxwellian part and, if
+//      it is too large, continues the split with levels m+1..2m on the
+//      thermalised set, keeping every collision already done;
+//   7. the thermalised particles are resampled from the local Maxwellian
+//      and renormalised to the exact momentum and energy they carried;
+//   8. changed particles are written back (coalesced, predicated).
+// FP64 contexts compute everything in double and match the CPU oracle draw
+// for draw; FP32-mixed contexts store velocities and collide in float while
+// moments, Sigma, q and the renormalisation stay in double.
+#include <cfloat>
+
+#include "internal.h"
+#include "trmc_device.cuh"
+
+namespace trmc {
+namespace {
+
+constexpr int NLEV = kMC + 2;
+constexpr double kTwoPi = 6.283185307179586;
+
+struct Args {
+    void *vx, *vy, *vz;
+    const int64_t *cell_start;
+    int32_t n_cells;
+    int32_t *m_max;
+    const trmc_cell_param *cell_param;
+    const uint64_t *cell_key;
+    double *cell_vmax2;
+    uint32_t problem_id;
+    uint64_t seed, step;
+    trmc_collide_params prm;
+    int64_t *report;
+    trmc_stats *stats;
+    int *status;
+    unsigned int *tickets;
+    char *slabs;
+    size_t slab_bytes;
+    int smem_bytes;
+};
+
+template <typename Real>
+struct Sh {
+    int32_t Nq[NLEV], Nn[NLEV], D[NLEV], C[NLEV], out[NLEV], O[NLEV], IB[NLEV];
+    int32_t Pn[kMC + 1];
+    double red[32 * 8];
+    int32_t cell, n, m, lo, m_eff, pass, n0, D0, R, npart, m_next, Dge1;
+    int32_t n0_prev, D0_prev;
+    int32_t feas, pdrop, psurp, pdrop_tot, psurp_tot, skip, cont, m_top, m_first, n0_first;
+    double q, Sigma, U[3], P[3], E, S_pre, Pnt[3], Ent, Snt;
+    double alpha, dt, eps, rho_scale;
+    uint64_t problem, lcell;
+    U64x4 keyK;
+    Real *V;
+    uint32_t *flags;
+    int32_t *inv[2];
+    int32_t *Mt, *St;
+    Real *IBuf, *OBuf;
+    char *smem_rest, *slab_rest;
+    size_t smem_rest_cap, slab_rest_cap;
+    char *pass_smem, *pass_slab;
+    size_t pass_smem_cap, pass_slab_cap;
+};
+
+__device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+__device__ __forceinline__ int tri(int n) { return (n * (n - 1)) >> 1; }
+
+// Bump allocator over two arenas: shared memory first, then the slab.
+__device__ __forceinline__ void *take(char *&smem, size_t &scap, char *&slab, size_t &gcap, size_t bytes)
+{
+    bytes = al16(bytes);
+    if (bytes <= scap) { void *p = smem; smem += bytes; scap -= bytes; return p; }
+    if (bytes <= gcap) { void *p = slab; slab += bytes; gcap -= bytes; return p; }
+    return nullptr;
+}
+
+template <typename Real> struct Math;
+template <> struct Math<double> {
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double pow_(double x, double a) { return pow(x, a); }
+    static __device__ __forceinline__ double uni(uint64_t w) { return u01(w); }
+    static __device__ __forceinline__ void angle(double u, double &s, double &c)
+    {
+        const double phi = kTwoPi * u;
+        s = sin(phi);
+        c = cos(phi);
+    }
+    static __device__ __forceinline__ void normals(const U64x4 &w, double &z0, double &z1, double &z2)
+    {
+        const double r1 = sqrt(-2.0 * log(u01_open(w.w[0])));
+        const double a1 = kTwoPi * u01(w.w[1]);
+        const double r2 = sqrt(-2.0 * log(u01_open(w.w[2])));
+        const double a2 = kTwoPi * u01(w.w[3]);
+        z0 = r1 * cos(a1);
+        z1 = r1 * sin(a1);
+        z2 = r2 * cos(a2);
+    }
+};
+template <> struct Math<float> {
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float pow_(float x, float a) { return powf(x, a); }
+    static __device__ __forceinline__ float uni(uint64_t w) { return u01f(w); }
+    static __device__ __forceinline__ void angle(float u, float &s, float &c) { sincospif(2.0f * u, &s, &c); }
+    static __device__ __forceinline__ void normals(const U64x4 &w, float &z0, float &z1, float &z2)
+    {
+        const float r1 = sqrtf(-2.0f * logf(u01f_open(w.w[0])));
+        const float r2 = sqrtf(-2.0f * logf(u01f_open(w.w[2])));
+        float s1, c1, s2, c2;
+        sincospif(2.0f * u01f(w.w[1]), &s1, &c1);
+        sincospif(2.0f * u01f(w.w[3]), &s2, &c2);
+        z0 = r1 * c1;
+        z1 = r1 * s1;
+        z2 = r2 * c2;
+        (void)s2;
+    }
+};
+
+__device__ __forceinline__ double indicator(double x, double y, double z, const double U[3], int ind)
+{
+    if (ind == TRMC_IND_M4) {
+        const double e = x * x + y * y + z * z;
+        return e * e;
+    }
+    const double d = x - U[0];
+    return d * d;
+}
+
+__device__ __forceinline__ void raise_status(int *status, int code, int cell)
+{
+    if (atomicCAS(status, 0, code) == 0) status[1] = cell;
+}
+
+template <typename Real>
+__device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, char *slab, int cell,
+                             double (&cnt)[3])
+{
+    const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
+    Real *gx = static_cast<Real *>(a.vx), *gy = static_cast<Real *>(a.vy), *gz = static_cast<Real *>(a.vz);
+    const int64_t base = a.cell_start[cell];
+    const int n = int(a.cell_start[cell + 1] - base);
+    const trmc_collide_params &prm = a.prm;
+
+    if (tid == 0) {
+        sh.cell = cell;
+        sh.n = n;
+        if (a.cell_param) {
+            const trmc_cell_param cp = a.cell_param[cell];
+            sh.eps = cp.eps; sh.dt = cp.dt; sh.rho_scale = cp.rho_scale; sh.alpha = cp.alpha;
+        } else {
+            sh.eps = prm.eps; sh.dt = prm.dt; sh.rho_scale = prm.rho_scale; sh.alpha = prm.alpha;
+        }
+        if (a.cell_key) { sh.problem = a.cell_key[cell] >> 32; sh.lcell = a.cell_key[cell] & 0xFFFFFFFFull; }
+        else { sh.problem = a.problem_id; sh.lcell = uint64_t(cell); }
+        int m0 = prm.trunc == TRMC_TRUNC_FIXED ? prm.m_fixed
+                 : prm.trunc == TRMC_TRUNC_RAD ? a.m_max[cell] : prm.m_cap;
+        if (m0 < 1) m0 = 1;
+        if (m0 > prm.m_cap) m0 = prm.m_cap;
+        sh.m = m0; sh.m_next = m0; sh.m_first = m0; sh.lo = 0; sh.pass = 0; sh.npart = n; sh.skip = 0;
+        sh.feas = sh.pdrop = sh.psurp = sh.pdrop_tot = sh.psurp_tot = 0;
+        sh.n0_prev = 0; sh.D0_prev = 0;
+        sh.Pnt[0] = sh.Pnt[1] = sh.Pnt[2] = 0.0; sh.Ent = 0.0; sh.Snt = 0.0;
+        // persistent layout: V, flags, inv[2]
+        char *smem = reinterpret_cast<char *>(dsm);
+        size_t scap = size_t(a.smem_bytes);
+        char *gs = slab;
+        size_t gcap = a.slab_bytes;
+        const size_t pb = al16(3 * size_t(n) * sizeof(Real)) + al16(4 * size_t((n + 31) / 32)) + 2 * al16(4 * size_t(n));
+        char *p;
+        if (pb <= scap) { p = smem; smem += pb; scap -= pb; }
+        else if (pb <= gcap) { p = gs; gs += pb; gcap -= pb; }
+        else { p = nullptr; sh.skip = 1; }
+        if (p) {
+            sh.V = reinterpret_cast<Real *>(p); p += al16(3 * size_t(n) * sizeof(Real));
+            sh.flags = reinterpret_cast<uint32_t *>(p); p += al16(4 * size_t((n + 31) / 32));
+            sh.inv[0] = reinterpret_cast<int32_t *>(p); p += al16(4 * size_t(n));
+            sh.inv[1] = reinterpret_cast<int32_t *>(p);
+        }
+        sh.smem_rest = smem; sh.smem_rest_cap = scap; sh.slab_rest = gs; sh.slab_rest_cap = gcap;
+    }
+    __syncthreads();
+    if (n < 2 || sh.skip) {
+        if (tid == 0) {
+            if (sh.skip) {
+                raise_status(a.status, TRMC_ERR_CAPACITY, cell);
+                if (a.stats) atomicAdd(&a.stats->capacity_skips, 1ull);
+            }
+            if (a.report) {
+                int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
+                for (int j = 0; j < TRMC_REPORT_LEN; ++j) r[j] = 0;
+                r[0] = n;
+                r[4] = prm.trunc == TRMC_TRUNC_RAD ? sh.m : 0;
+                r[6] = n;
+            }
+        }
+        if (a.cell_vmax2 && !sh.skip) {
+            double vm = 0.0;
+            for (int i = tid; i < n; i += bs) {
+                const double x = double(gx[base + i]), y = double(gy[base + i]), z = double(gz[base + i]);
+                vm = fmax(vm, __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+            }
+            vm = block_max(vm, sh.red);
+            if (tid == 0) a.cell_vmax2[cell] = vm;
+        }
+        return;
+    }
+    Real *Vx = sh.V, *Vy = sh.V + n, *Vz = sh.V + 2 * n;
+    const CellRng rng{a.seed, sh.problem, sh.lcell, a.step};
+
+    // ---- 1. stage + moments -------------------------------------------------
+    {
+        double s[5] = {0, 0, 0, 0, 0};
+        for (int i = tid; i < n; i += bs) {
+            const Real x = gx[base + i], y = gy[base + i], z = gz[base + i];
+            Vx[i] = x; Vy[i] = y; Vz[i] = z;
+            const double dx = x, dy = y, dz = z;
+            s[0] += dx; s[1] += dy; s[2] += dz;
+            const double e = dx * dx + dy * dy + dz * dz;
+            s[3] += e;
+            s[4] += e * e;
+        }
+        block_sum<5>(s, sh.red);
+        const double U0 = s[0] / double(n), U1 = s[1] / double(n), U2 = s[2] / double(n);
+        double d2 = 0.0, pxx = 0.0;
+        for (int i = tid; i < n; i += bs) {
+            const double ax = double(Vx[i]) - U0, ay = double(Vy[i]) - U1, az = double(Vz[i]) - U2;
+            d2 = fmax(d2, ax * ax + ay * ay + az * az);
+            pxx += ax * ax;
+        }
+        double t[1] = {pxx};
+        block_sum<1>(t, sh.red);
+        const double dmax = (sh.alpha != 0.0) ? block_max(d2, sh.red) : 0.0;
+        if (tid == 0) {
+            sh.P[0] = s[0]; sh.P[1] = s[1]; sh.P[2] = s[2]; sh.E = s[3];
+            sh.U[0] = U0; sh.U[1] = U1; sh.U[2] = U2;
+            double Sigma = 1.0;
+            if (sh.alpha != 0.0) {
+                const double g = 2.0 * sqrt(dmax);
+                Sigma = (sh.alpha == 1.0) ? g : pow(g, sh.alpha);
+            }
+            sh.Sigma = Sigma;
+            const double rho = double(n) * sh.rho_scale;
+            const double mu = rho * Sigma;
+            sh.q = exp(-(mu * sh.dt) / sh.eps);
+            sh.S_pre = (prm.indicator == TRMC_IND_M4 ? s[4] : t[0]) / double(n);
+        }
+        __syncthreads();
+    }
+
+    // ---- pass loop (pass 0, then TRMC-RAD continuations) --------------------
+    for (;;) {
+        const int pass = sh.pass;
+        // 2. split (Alg. 4.2) and the per-pass arena
+        if (tid == 0) {
+            for (int j = 0; j < NLEV; ++j) sh.Nq[j] = 0;
+            int rem = sh.npart, m_eff = sh.m;
+            for (int lv = sh.lo; lv <= sh.m; ++lv) {
+                const double x = sh.q * double(rem);
+                const double fl = floor(x);
+                const U64x4 w = rng.draw(uint64_t(lv), 0, uint32_t(pass), TAG_SPLIT);
+                const int c = int(fl) + ((u01(w.w[0]) < x - fl) ? 1 : 0);
+                sh.Nq[lv] = c;
+                rem -= c;
+                if (rem == 0) { m_eff = lv; break; }
+            }
+            if (rem > 0) sh.Nq[sh.m + 1] = rem;
+            sh.m_eff = m_eff;
+            sh.m_top = m_eff;
+            sh.pass_smem = sh.smem_rest; sh.pass_smem_cap = sh.smem_rest_cap;
+            sh.pass_slab = sh.slab_rest; sh.pass_slab_cap = sh.slab_rest_cap;
+            const size_t T = size_t(tri(m_eff + 1));
+            sh.Mt = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
+            sh.St = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
+            if (!sh.Mt || !sh.St) sh.skip = 1;
+        }
+        __syncthreads();
+        if (sh.skip) break;
+
+        // 3. tree plan, top level first, with the leaf-feasibility loop
+        for (;;) {
+            if (tid == 0) {
+                for (int j = 0; j < NLEV; ++j) {
+                    sh.D[j] = 0; sh.C[j] = 0; sh.out[j] = 0;
+                    sh.Nn[j] = (j <= sh.m_top) ? sh.Nq[j] : 0;
+                }
+                sh.pdrop = 0; sh.psurp = 0;
+            }
+            __syncthreads();
+            const int m_top = sh.m_top;
+            for (int lv = m_top; lv >= 1; --lv) {
+                if (tid == 0) {
+                    int T = sh.Nn[lv] + sh.D[lv];
+                    if (T & 1) {
+                        const U64x4 w = rng.draw(uint64_t(lv), 0, uint32_t(pass), TAG_PARITY);
+                        if (sh.Nn[lv] >= 1 && u01(w.w[0]) < 0.5) { sh.Nn[lv] -= 1; T -= 1; sh.pdrop++; }
+                        else { T += 1; sh.psurp++; }
+                    }
+                    sh.C[lv] = T >> 1;
+                }
+                int32_t *row = sh.Mt + tri(lv);
+                for (int k = tid; k < lv; k += bs) row[k] = 0;
+                __syncthreads();
+                const int Cn = sh.C[lv];
+                for (int g = tid; g < (Cn + 3) >> 2; g += bs) {
+                    const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (4 * g + j < Cn) atomicAdd(&row[below(w.w[j], uint32_t(lv))], 1);
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    int32_t *srow = sh.St + tri(lv);
+                    for (int k = 0; k < lv; ++k) srow[k] = sh.D[k];
+                    for (int k = 0; k < lv; ++k) sh.D[k] += row[k] + row[lv - 1 - k];
+                    sh.out[lv] = 2 * sh.C[lv] - sh.D[lv];
+                }
+            }
+            if (tid == 0) {
+                const int n0q = sh.Nq[0];
+                const int A = sh.npart - n0q;
+                sh.cont = 0;
+                if (sh.D[0] <= A) { sh.n0 = n0q; sh.D0 = sh.D[0]; sh.R = A - sh.D[0]; }
+                else if (sh.D[0] - A <= n0q) { sh.n0 = n0q - (sh.D[0] - A); sh.D0 = sh.D[0]; sh.R = 0; }
+                else { sh.feas++; sh.m_top = m_top - 1; sh.cont = 1; }
+            }
+            __syncthreads();
+            if (!sh.cont) break;
+        }
+
+        // layout of the product buffers; output / input offsets
+        if (tid == 0) {
+            const int m = sh.m_top;
+            sh.pdrop_tot += sh.pdrop;
+            sh.psurp_tot += sh.psurp;
+            sh.m_eff = m;
+            sh.O[1] = 0; sh.IB[1] = 0;
+            for (int lv = 1; lv <= m; ++lv) { sh.O[lv + 1] = sh.O[lv] + sh.out[lv]; sh.IB[lv + 1] = sh.IB[lv] + sh.D[lv]; }
+            sh.Dge1 = sh.IB[m + 1];
+            sh.IBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                                               3 * size_t(sh.Dge1 + 1) * sizeof(Real)));
+            sh.OBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                                               3 * size_t(sh.D0 + 1) * sizeof(Real)));
+            if (!sh.IBuf || !sh.OBuf) sh.skip = 1;
+            if (pass == 0) sh.n0_first = sh.n0;
+            if (a.report && pass == 0) {
+                int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
+                r[6] = sh.n0;
+                r[14] = m;
+                for (int j = 0; j < NLEV; ++j) {
+                    r[16 + j] = sh.Nq[j];
+                    r[16 + NLEV + j] = sh.C[j];
+                    r[16 + 2 * NLEV + j] = sh.D[j];
+                }
+            }
+        }
+        __syncthreads();
+        if (sh.skip) break;
+        const int m_eff = sh.m_eff, n0 = sh.n0, D0 = sh.D0, npart = sh.npart, Dge1 = sh.Dge1;
+        int32_t *inv = sh.inv[pass & 1];
+        const int32_t *invp = sh.inv[(pass + 1) & 1];
+        const int poolp = sh.n0_prev + sh.D0_prev;
+
+        // 4. roles: permutation of the participants
+        {
+            Perm perm;
+            perm.init(uint32_t(npart), rng.draw(0, 0, uint32_t(pass), TAG_PERM0));
+            for (int b0 = tid - lane; b0 < npart; b0 += bs) {
+                const int i = b0 + lane;
+                bool changed = false;
+                if (i < npart) {
+                    const int r = int(perm.fwd(uint32_t(i)));
+                    inv[r] = (pass == 0) ? i : invp[poolp + i];
+                    changed = r >= n0;
+                }
+                if (pass == 0) {
+                    const unsigned msk = __ballot_sync(0xffffffffu, changed);
+                    if (lane == 0) sh.flags[b0 >> 5] = msk;
+                }
+            }
+        }
+        __syncthreads();
+        if (pass == 0) {
+            // non-thermalised sums, part 1: the uncollided particles
+            double s[5] = {0, 0, 0, 0, 0};
+            for (int r = tid; r < n0; r += bs) {
+                const int sl = inv[r];
+                const double x = Vx[sl], y = Vy[sl], z = Vz[sl];
+                s[0] += x; s[1] += y; s[2] += z;
+                s[3] += x * x + y * y + z * z;
+                s[4] += indicator(x, y, z, sh.U, prm.indicator);
+            }
+            block_sum<5>(s, sh.red);
+            if (tid == 0) { sh.Pnt[0] = s[0]; sh.Pnt[1] = s[1]; sh.Pnt[2] = s[2]; sh.Ent = s[3]; sh.Snt = s[4]; }
+        }
+
+        // 5. collision waves, level 1 first
+        Real *IBx = sh.IBuf, *IBy = sh.IBuf + (Dge1 + 1), *IBz = sh.IBuf + 2 * (Dge1 + 1);
+        Real *OBx = sh.OBuf, *OBy = sh.OBuf + (D0 + 1), *OBz = sh.OBuf + 2 * (D0 + 1);
+        const Real alpha = Real(sh.alpha), Sigma = Real(sh.Sigma);
+        for (int lv = 1; lv <= m_eff; ++lv) {
+            if (tid == 0) {
+                const int32_t *row = sh.Mt + tri(lv);
+                sh.Pn[0] = 0;
+                for (int k = 0; k < lv; ++k) sh.Pn[k + 1] = sh.Pn[k] + row[k];
+                sh.keyK = rng.draw(0, uint64_t(lv), uint32_t(pass), TAG_PERMK);
+            }
+            __syncthreads();
+            const int Cn = sh.C[lv], Dn = sh.D[lv], On = sh.O[lv], IBn = sh.IB[lv];
+            const int32_t *row = sh.Mt + tri(lv), *srow = sh.St + tri(lv);
+            Perm pk;
+            pk.init(uint32_t(2 * Cn), sh.keyK);
+            for (int c = tid; c < Cn; c += bs) {
+                // label of collision c: Pn[k] <= c < Pn[k+1]
+                int lo_ = 0, hi_ = lv - 1;
+                while (lo_ < hi_) {
+                    const int mid = (lo_ + hi_ + 1) >> 1;
+                    if (sh.Pn[mid] <= c) lo_ = mid; else hi_ = mid - 1;
+                }
+                const int k = lo_, j = lv - 1 - k, off = c - sh.Pn[k];
+                const int s0 = srow[k] + off, s1 = srow[j] + row[j] + off;
+                Real ax, ay, az, bx, by, bz;
+                if (k == 0) { const int sl = inv[n0 + s0]; ax = Vx[sl]; ay = Vy[sl]; az = Vz[sl]; }
+                else { const int q = sh.IB[k] + s0; ax = IBx[q]; ay = IBy[q]; az = IBz[q]; }
+                if (j == 0) { const int sl = inv[n0 + s1]; bx = Vx[sl]; by = Vy[sl]; bz = Vz[sl]; }
+                else { const int q = sh.IB[j] + s1; bx = IBx[q]; by = IBy[q]; bz = IBz[q]; }
+                const U64x4 w = rng.draw(uint64_t(c), uint64_t(lv), uint32_t(pass), TAG_COLL);
+                const Real dx = ax - bx, dy = ay - by, dz = az - bz;
+                const Real g = Math<Real>::sqrt_(dx * dx + dy * dy + dz * dz);
+                bool acc = true;
+                if (alpha != Real(0)) {
+                    const Real ga = (alpha == Real(1)) ? g : Math<Real>::pow_(g, alpha);
+                    if (ga > Sigma) cnt[2] += 1.0;
+                    const Real xi = Math<Real>::uni(w.w[0]);
+                    acc = xi * Sigma < ga;
+                }
+                Real oax = ax, oay = ay, oaz = az, obx = bx, oby = by, obz = bz;
+                if (acc) {
+                    const Real ct = Real(2) * Math<Real>::uni(w.w[1]) - Real(1);
+                    const Real st = Math<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
+                    Real sp, cp;
+                    Math<Real>::angle(Math<Real>::uni(w.w[2]), sp, cp);
+                    const Real sx = cp * st, sy = sp * st, sz = ct;
+                    const Real h = Real(0.5) * g;
+                    const Real cx = Real(0.5) * (ax + bx), cy = Real(0.5) * (ay + by), cz = Real(0.5) * (az + bz);
+                    oax = cx + h * sx; oay = cy + h * sy; oaz = cz + h * sz;
+                    obx = cx - h * sx; oby = cy - h * sy; obz = cz - h * sz;
+                    cnt[0] += 1.0;
+                } else {
+                    cnt[1] += 1.0;
+                }
+                const int t0 = int(pk.fwd(uint32_t(2 * c))), t1 = int(pk.fwd(uint32_t(2 * c + 1)));
+                if (t0 < Dn) { const int q = IBn + t0; IBx[q] = oax; IBy[q] = oay; IBz[q] = oaz; }
+                else { const int q = On + t0 - Dn; OBx[q] = oax; OBy[q] = oay; OBz[q] = oaz; }
+                if (t1 < Dn) { const int q = IBn + t1; IBx[q] = obx; IBy[q] = oby; IBz[q] = obz; }
+                else { const int q = On + t1 - Dn; OBx[q] = obx; OBy[q] = oby; OBz[q] = obz; }
+            }
+            __syncthreads();
+        }
+
+        // 6. outputs replace the leaves; their sums join the non-thermalised part
+        {
+            double s[5] = {0, 0, 0, 0, 0};
+            for (int jx = tid; jx < D0; jx += bs) {
+                const int sl = inv[n0 + jx];
+                const Real x = OBx[jx], y = OBy[jx], z = OBz[jx];
+                Vx[sl] = x; Vy[sl] = y; Vz[sl] = z;
+                const double dx = x, dy = y, dz = z;
+                s[0] += dx; s[1] += dy; s[2] += dz;
+                s[3] += dx * dx + dy * dy + dz * dz;
+                s[4] += indicator(dx, dy, dz, sh.U, prm.indicator);
+            }
+            block_sum<5>(s, sh.red);
+            if (tid == 0) {
+                sh.Pnt[0] += s[0]; sh.Pnt[1] += s[1]; sh.Pnt[2] += s[2]; sh.Ent += s[3]; sh.Snt += s[4];
+            }
+        }
+        // TRMC-RAD test (Sec. 4.3)
+        if (tid == 0) {
+            sh.cont = 0;
+            if (prm.trunc == TRMC_TRUNC_RAD) {
+                const int R = sh.R;
+                double Sth = 0.0;
+                if (R == 1) {
+                    const int sl = inv[n0 + D0];
+                    Sth = indicator(double(Vx[sl]), double(Vy[sl]), double(Vz[sl]), sh.U, prm.indicator);
+                } else if (R >= 2) {
+                    const double Pt0 = sh.P[0] - sh.Pnt[0], Pt1 = sh.P[1] - sh.Pnt[1], Pt2 = sh.P[2] - sh.Pnt[2];
+                    const double Et = sh.E - sh.Ent;
+                    double et = Et - (Pt0 * Pt0 + Pt1 * Pt1 + Pt2 * Pt2) / double(R);
+                    if (et < 0.0) et = 0.0;
+                    const double u0 = Pt0 / double(R), u1 = Pt1 / double(R), u2 = Pt2 / double(R);
+                    if (prm.indicator == TRMC_IND_M4) {
+                        const double Tp = et / (3.0 * double(R));
+                        const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+                        Sth = double(R) * (uu * uu + 10.0 * uu * Tp + 15.0 * Tp * Tp);
+                    } else {
+                        const double d = u0 - sh.U[0];
+                        Sth = et / 3.0 + double(R) * d * d;
+                    }
+                }
+                const double S_post = (sh.Snt + Sth) / double(sh.n);
+                const double E1 = (sh.S_pre != 0.0) ? fabs(S_post - sh.S_pre) / fabs(sh.S_pre) : 0.0;
+                const int m = sh.m;
+                if (E1 > prm.delta2 && R > 0 && 2 * m <= prm.m_cap) {
+                    sh.cont = 1;
+                    sh.n0_prev = n0; sh.D0_prev = D0;
+                    sh.npart = R;
+                    sh.lo = m + 1;
+                    sh.m = 2 * m;
+                    sh.pass = pass + 1;
+                } else if (E1 < prm.delta1) {
+                    sh.m_next = (m / 2 > prm.m_min) ? m / 2 : prm.m_min;
+                } else {
+                    sh.m_next = m;
+                }
+            } else {
+                sh.m_next = sh.m;
+            }
+        }
+        __syncthreads();
+        if (!sh.cont) break;
+    }
+    if (sh.skip) {
+        if (tid == 0) {
+            raise_status(a.status, TRMC_ERR_CAPACITY, cell);
+            if (a.stats) atomicAdd(&a.stats->capacity_skips, 1ull);
+        }
+        return;
+    }
+
+    // ---- 7. Maxwellian resampling of the thermalised set + renormalisation --
+    const int pass = sh.pass, R = sh.R;
+    const int32_t *inv = sh.inv[pass & 1];
+    const int pool0 = sh.n0 + sh.D0;
+    if (R >= 2) {
+        double s[3] = {0, 0, 0};
+        for (int t = tid; t < R; t += bs) {
+            Real z0, z1, z2;
+            Math<Real>::normals(rng.draw(uint64_t(t), 0, 0, TAG_MAXW), z0, z1, z2);
+            const int sl = inv[pool0 + t];
+            Vx[sl] = z0; Vy[sl] = z1; Vz[sl] = z2;
+            s[0] += double(z0); s[1] += double(z1); s[2] += double(z2);
+        }
+        block_sum<3>(s, sh.red);
+        const double zb0 = s[0] / double(R), zb1 = s[1] / double(R), zb2 = s[2] / double(R);
+        double e[1] = {0.0};
+        for (int t = tid; t < R; t += bs) {
+            const int sl = inv[pool0 + t];
+            const double a0 = double(Vx[sl]) - zb0, a1 = double(Vy[sl]) - zb1, a2 = double(Vz[sl]) - zb2;
+            e[0] += a0 * a0 + a1 * a1 + a2 * a2;
+        }
+        block_sum<1>(e, sh.red);
+        const double Pt0 = sh.P[0] - sh.Pnt[0], Pt1 = sh.P[1] - sh.Pnt[1], Pt2 = sh.P[2] - sh.Pnt[2];
+        const double Et = sh.E - sh.Ent;
+        double et = Et - (Pt0 * Pt0 + Pt1 * Pt1 + Pt2 * Pt2) / double(R);
+        if (et < 0.0) et = 0.0;
+        const double sc = (e[0] > 0.0) ? sqrt(et / e[0]) : 0.0;
+        const double u0 = Pt0 / double(R), u1 = Pt1 / double(R), u2 = Pt2 / double(R);
+        for (int t = tid; t < R; t += bs) {
+            const int sl = inv[pool0 + t];
+            Vx[sl] = Real(u0 + sc * (double(Vx[sl]) - zb0));
+            Vy[sl] = Real(u1 + sc * (double(Vy[sl]) - zb1));
+            Vz[sl] = Real(u2 + sc * (double(Vz[sl]) - zb2));
+        }
+    }
+    __syncthreads();
+
+    // ---- 8. write back the changed particles; cell max |v|^2 ----------------
+    {
+        double vm = 0.0;
+        for (int i = tid; i < n; i += bs) {
+            const Real x = Vx[i], y = Vy[i], z = Vz[i];
+            if ((sh.flags[i >> 5] >> (i & 31)) & 1u) { gx[base + i] = x; gy[base + i] = y; gz[base + i] = z; }
+            const double dx = x, dy = y, dz = z;
+            vm = fmax(vm, __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+        }
+        if (a.cell_vmax2) {
+            vm = block_max(vm, sh.red);
+            if (tid == 0) a.cell_vmax2[cell] = vm;
+        }
+    }
+    if (tid == 0) {
+        if (prm.trunc == TRMC_TRUNC_RAD) a.m_max[cell] = sh.m_next;
+        if (a.report) {
+            int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
+            r[0] = n; r[1] = sh.pass + 1; r[2] = sh.m_first; r[3] = sh.m; r[4] = sh.m_next; r[5] = R;
+            r[7] = int64_t(n) - r[6] - int64_t(R);
+            r[11] = sh.feas; r[12] = sh.pdrop_tot; r[13] = sh.psurp_tot; r[15] = 0;
+        }
+    }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) collide_kernel(Args a)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ Sh<Real> sh;
+    __shared__ int s_cell;
+    char *slab = a.slabs + size_t(blockIdx.x) * a.slab_bytes;
+    for (;;) {
+        if (threadIdx.x == 0) s_cell = int(atomicAdd(&a.tickets[0], 1u));
+        __syncthreads();
+        const int cell = s_cell;
+        __syncthreads();
+        if (cell >= a.n_cells) break;
+        double cnt[3] = {0, 0, 0};   // collisions, dummy, exceed
+        process_cell<Real>(a, sh, dsm, slab, cell, cnt);
+        __syncthreads();
+        if (a.report || a.stats) {
+            block_sum<3>(cnt, sh.red);
+            if (threadIdx.x == 0 && sh.n >= 2 && !sh.skip) {
+                if (a.report) {
+                    int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
+                    r[8] = (long long)cnt[0]; r[9] = (long long)cnt[1]; r[10] = (long long)cnt[2];
+                }
+                if (a.stats) {
+                    atomicAdd(&a.stats->collisions, (unsigned long long)cnt[0]);
+                    atomicAdd(&a.stats->dummy, (unsigned long long)cnt[1]);
+                    atomicAdd(&a.stats->exceed, (unsigned long long)cnt[2]);
+                    atomicAdd(&a.stats->maxwell, (unsigned long long)(sh.R >= 2 ? sh.R : 0));
+                    atomicAdd(&a.stats->passes, (unsigned long long)(sh.pass + 1));
+                    atomicAdd(&a.stats->feas, (unsigned long long)sh.feas);
+                    atomicAdd(&a.stats->cells, 1ull);
+                    atomicAdd(&a.stats->changed, (unsigned long long)(sh.n - sh.n0_first));
+                    atomicAdd(&a.stats->particles, (unsigned long long)sh.n);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(&a.tickets[1], 1u);
+        if (done == gridDim.x - 1) {
+            a.tickets[0] = 0u;
+            a.tickets[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <typename Real>
+trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *prm, uint64_t step,
+                     int64_t *report, trmc_stats *stats, cudaStream_t s)
+{
+    static int configured_smem = -1;
+    const int smem = int(ctx->smem_optin > 120 * 1024 ? 100 * 1024 : ctx->smem_optin / 2 - 8 * 1024);
+    cudaError_t e;
+    if (configured_smem != smem) {
+        e = cudaFuncSetAttribute(collide_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "cudaFuncSetAttribute(collide)");
+        configured_smem = smem;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_kernel<Real>, kThreads, smem);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "occupancy(collide)");
+    if (per_sm < 1) per_sm = 1;
+    int grid = ctx->num_sms * per_sm;
+    if (grid > st->n_cells) grid = st->n_cells;
+    if (grid < 1) return TRMC_OK;
+    Args a;
+    a.vx = st->vx; a.vy = st->vy; a.vz = st->vz;
+    a.cell_start = st->cell_start;
+    a.n_cells = st->n_cells;
+    a.m_max = st->m_max;
+    a.cell_param = st->cell_param;
+    a.cell_key = st->cell_key;
+    a.cell_vmax2 = st->cell_vmax2;
+    a.problem_id = st->problem_id;
+    a.seed = ctx->seed;
+    a.step = step;
+    a.prm = *prm;
+    a.report = report;
+    a.stats = stats;
+    a.status = ctx->status;
+    a.tickets = ctx->tickets;
+    a.slabs = ctx->slabs;
+    a.slab_bytes = (ctx->slabs_bytes / size_t(grid)) & ~size_t(255);
+    a.smem_bytes = smem;
+    collide_kernel<Real><<<grid, kThreads, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "collide launch");
+    return TRMC_OK;
+}
+
+}  // namespace
+
+trmc_status launch_collide(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *prm, uint64_t step,
+                           int64_t *report, trmc_stats *stats, cudaStream_t s)
+{
+    if (ctx->precision == TRMC_FP64) return launch_t<double>(ctx, st, prm, step, report, stats, s);
+    return launch_t<float>(ctx, st, prm, step, report, stats, s);
+}
+
+}  // namespace trmc

@@ -1,0 +1,45 @@
+// internal.h -- definitions shared by the translation units of libtrmc.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "trmc.h"
+
+struct trmc_ctx {
+    int precision = 0;
+    uint64_t seed = 0;
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    // device workspace: [control block 4 KiB][collide slabs]
+    char *workspace = nullptr;
+    size_t workspace_bytes = 0;
+    int *status = nullptr;            // [0] error code, [1] detail (cell), [2..3] spare
+    unsigned int *tickets = nullptr;  // [0] next cell, [1] CTAs done (collide)
+    char *slabs = nullptr;
+    size_t slabs_bytes = 0;
+    // transport scratch, grown on demand
+    int64_t *tr_counts = nullptr;     // [3 * cells] moves -1/0/+1 per old cell
+    int64_t *tr_scan = nullptr;       // [cells + 1]
+    int tr_cells = 0;
+    std::string last_error;
+};
+
+namespace trmc {
+
+constexpr int kMC = TRMC_MCAP;
+constexpr int kThreads = 256;         // collide CTA size
+
+trmc_status set_error(trmc_ctx *ctx, trmc_status code, const std::string &msg);
+trmc_status cuda_error(trmc_ctx *ctx, cudaError_t e, const char *where);
+
+trmc_status launch_collide(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *prm,
+                           uint64_t step, int64_t *report, trmc_stats *stats, cudaStream_t s);
+trmc_status launch_transport(trmc_ctx *ctx, trmc_state *st, const trmc_domain *domains,
+                             int32_t n_domains, double cfl, double *dt, cudaStream_t s);
+trmc_status launch_init(trmc_ctx *ctx, trmc_state *st, const double *cell_init, cudaStream_t s);
+trmc_status launch_moments(trmc_ctx *ctx, const trmc_state *st, double *out, cudaStream_t s);
+
+}  // namespace trmc

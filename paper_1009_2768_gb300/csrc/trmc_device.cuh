@@ -1,0 +1,164 @@
+// trmc_device.cuh -- device primitives of libtrmc: counter-based random
+// numbers, the pseudo-random permutation and block reductions.
+//
+// Random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel
+// random numbers: as easy as 1, 2, 3", SC'11).  The paper fixes no
+// generator; a counter-based one lets every draw be addressed by
+// (seed, problem | index, aux, cell, step/pass/tag), so a cell's result does
+// not depend on launch shape or batch placement.
+//
+// Permutation: 4-round balanced Feistel network on 2h-bit words with cycle
+// walking onto [0, n) (Black & Rogaway, CT-RSA 2002).  It realises the
+// "random choice" of particles in Alg. 4.3 without materialising shuffles.
+#pragma once
+#include <cstdint>
+
+namespace trmc {
+
+enum Tag : uint32_t {
+    TAG_INIT = 1, TAG_SPLIT = 2, TAG_PARITY = 3, TAG_KSEL = 4,
+    TAG_PERM0 = 5, TAG_PERMK = 6, TAG_COLL = 7, TAG_MAXW = 8
+};
+
+struct U64x4 { uint64_t w[4]; };
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                               uint64_t k0, uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        const uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
+        const uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
+        const uint64_t n0 = hi1 ^ c1 ^ k0;
+        const uint64_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    U64x4 o;
+    o.w[0] = c0; o.w[1] = c1; o.w[2] = c2; o.w[3] = c3;
+    return o;
+}
+
+// Keyed stream of one cell: key = (seed, problem); the fourth counter word
+// packs step, pass and purpose tag.
+struct CellRng {
+    uint64_t seed, problem, cell, step;
+    __device__ __forceinline__ U64x4 draw(uint64_t index, uint64_t aux, uint32_t pass, uint32_t tag) const
+    {
+        const uint64_t c3 = (step << 16) | (uint64_t(pass & 0xFFu) << 8) | uint64_t(tag & 0xFFu);
+        return philox4x64_10(index, aux, cell, c3, seed, problem);
+    }
+};
+
+// 53-bit uniforms on [0,1) and (0,1]; 24-bit float uniform; integer below n.
+__device__ __forceinline__ double u01(uint64_t w) { return double(w >> 11) * 0x1.0p-53; }
+__device__ __forceinline__ double u01_open(uint64_t w) { return double((w >> 11) + 1) * 0x1.0p-53; }
+__device__ __forceinline__ float u01f(uint64_t w) { return float(uint32_t(w >> 40)) * 0x1.0p-24f; }
+__device__ __forceinline__ float u01f_open(uint64_t w) { return float(uint32_t(w >> 40) + 1u) * 0x1.0p-24f; }
+__device__ __forceinline__ uint32_t below(uint64_t w, uint32_t n)
+{
+    return uint32_t(((w >> 32) * uint64_t(n)) >> 32);
+}
+
+// ---- Feistel permutation of [0, n) ------------------------------------------
+__device__ __forceinline__ uint32_t feistel_round(uint32_t r, uint64_t k)
+{
+    uint32_t z = (r ^ uint32_t(k)) * 0x9E3779B1u;
+    z ^= z >> 15;
+    z = (z + uint32_t(k >> 32)) * 0x85EBCA77u;
+    z ^= z >> 13;
+    return z;
+}
+
+struct Perm {
+    uint32_t n;
+    uint32_t h;       // half width in bits; domain 4^h >= n
+    uint64_t k[4];
+
+    __device__ __forceinline__ void init(uint32_t n_, const U64x4 &key)
+    {
+        n = n_;
+        uint32_t hh = 1;
+        while ((1ull << (2 * hh)) < uint64_t(n_)) ++hh;
+        h = hh;
+        k[0] = key.w[0]; k[1] = key.w[1]; k[2] = key.w[2]; k[3] = key.w[3];
+    }
+    __device__ __forceinline__ uint32_t enc(uint32_t x) const
+    {
+        const uint32_t mask = (1u << h) - 1u;
+        uint32_t L = x >> h, R = x & mask;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t t = L ^ (feistel_round(R, k[r]) & mask);
+            L = R;
+            R = t;
+        }
+        return (L << h) | R;
+    }
+    // pi(x) for x < n
+    __device__ __forceinline__ uint32_t fwd(uint32_t x) const
+    {
+        if (n <= 1) return 0;
+        uint32_t y = enc(x);
+        while (y >= n) y = enc(y);
+        return y;
+    }
+};
+
+// ---- warp / block reductions (fixed order, hence deterministic) --------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum K doubles over the block; every thread gets the totals.  scratch must
+// hold 32*K doubles.  Contains two __syncthreads().
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double *scratch)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = warp_sum(v[j]);
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) scratch[warp * K + j] = v[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += scratch[w * K + j];
+        v[j] = s;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double block_max(double v, double *scratch)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_max(v);
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    double m = scratch[0];
+    for (int w = 1; w < nw; ++w) m = fmax(m, scratch[w]);
+    __syncthreads();
+    return m;
+}
+
+}  // namespace trmc

@@ -1,0 +1,222 @@
+"""Python binding of libtrmc (include/trmc.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and passes
+device pointers of torch tensors plus the current torch CUDA stream.  All
+computation happens in the CUDA library; if the library is missing or no
+GPU is present, the calls raise instead of falling back to anything else.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtrmc.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_CAPACITY, ERR_TIMEOUT, ERR_STATE = range(7)
+FP64, FP32_MIXED = 0, 1
+TRUNC_FIXED, TRUNC_RAD, TRUNC_UNLIMITED = 0, 1, 2
+IND_PXX, IND_M4 = 0, 1
+INIT_MAXWELL, INIT_BIMAXWELL, INIT_BKW = 0, 1, 2
+MCAP = 64
+INIT_COLS = 9
+MOM_COLS = 10
+REPORT_LEN = 16 + 3 * (MCAP + 2)
+REPORT_FIELDS = ["N", "passes", "m_first", "m_last", "m_next", "R_final", "N0", "leaves",
+                 "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "reserved"]
+EXPORTS = ["trmc_create", "trmc_destroy", "trmc_last_error", "trmc_check", "trmc_init_cells",
+           "trmc_collide", "trmc_transport", "trmc_moments"]
+
+
+class TrmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"trmc status {code}: {msg}")
+        self.code = code
+
+
+class CellParam(C.Structure):
+    _fields_ = [("eps", C.c_double), ("dt", C.c_double), ("rho_scale", C.c_double), ("alpha", C.c_double)]
+
+
+class State(C.Structure):
+    _fields_ = [("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p), ("x", C.c_void_p),
+                ("vx_alt", C.c_void_p), ("vy_alt", C.c_void_p), ("vz_alt", C.c_void_p), ("x_alt", C.c_void_p),
+                ("cell_start", C.c_void_p), ("cell_start_alt", C.c_void_p), ("m_max", C.c_void_p),
+                ("cell_param", C.c_void_p), ("cell_key", C.c_void_p), ("cell_vmax2", C.c_void_p),
+                ("capacity", C.c_int64), ("n_cells", C.c_int32), ("problem_id", C.c_uint32)]
+
+
+class CollideParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("eps", C.c_double), ("alpha", C.c_double), ("rho_scale", C.c_double),
+                ("delta1", C.c_double), ("delta2", C.c_double), ("trunc", C.c_int32), ("m_fixed", C.c_int32),
+                ("m_min", C.c_int32), ("m_cap", C.c_int32), ("indicator", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Domain(C.Structure):
+    _fields_ = [("cell_begin", C.c_int32), ("n_cells", C.c_int32), ("x_lo", C.c_double), ("x_hi", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(f, C.c_ulonglong) for f in
+                ("collisions", "dummy", "maxwell", "exceed", "passes", "feas", "cells", "capacity_skips",
+                 "changed", "particles")]
+
+
+STATS_FIELDS = [f for f, _ in Stats._fields_]
+_lib = None
+
+
+def load():
+    """Load libtrmc.so (built by build.py); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1009_2768_gb300.build.build() first")
+        lib = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        lib.trmc_create.argtypes = [C.POINTER(P), C.c_int32, C.c_uint64, C.c_size_t]
+        lib.trmc_destroy.argtypes = [P]
+        lib.trmc_last_error.argtypes = [P]
+        lib.trmc_last_error.restype = C.c_char_p
+        lib.trmc_check.argtypes = [P, P]
+        lib.trmc_init_cells.argtypes = [P, C.POINTER(State), P, P]
+        lib.trmc_collide.argtypes = [P, C.POINTER(State), C.POINTER(CollideParams), C.c_uint64, P, P, P]
+        lib.trmc_transport.argtypes = [P, C.POINTER(State), P, C.c_int32, C.c_double, P, P]
+        lib.trmc_moments.argtypes = [P, C.POINTER(State), P, P]
+        for f in EXPORTS:
+            if f != "trmc_last_error":
+                getattr(lib, f).restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _raise(ctx, code):
+    if code != OK:
+        msg = load().trmc_last_error(ctx).decode() if ctx else "no context"
+        raise TrmcError(code, msg)
+
+
+def trmc_create(precision=FP64, seed=0, workspace_bytes=0):
+    ctx = C.c_void_p()
+    code = load().trmc_create(C.byref(ctx), precision, seed, workspace_bytes)
+    if code != OK:
+        raise TrmcError(code, "trmc_create failed")
+    return ctx
+
+
+def trmc_destroy(ctx):
+    _raise(None, load().trmc_destroy(ctx))
+
+
+def trmc_check(ctx, stream=None):
+    _raise(ctx, load().trmc_check(ctx, _stream(stream)))
+
+
+def trmc_init_cells(ctx, state, cell_init, stream=None):
+    _raise(ctx, load().trmc_init_cells(ctx, C.byref(state.c), _ptr(cell_init), _stream(stream)))
+
+
+def trmc_collide(ctx, state, params, step, report=None, stats=None, stream=None):
+    _raise(ctx, load().trmc_collide(ctx, C.byref(state.c), C.byref(params), step, _ptr(report), _ptr(stats),
+                                    _stream(stream)))
+
+
+def trmc_transport(ctx, state, domains, n_domains, cfl, dt, stream=None):
+    code = load().trmc_transport(ctx, C.byref(state.c), _ptr(domains), n_domains, cfl, _ptr(dt), _stream(stream))
+    state.after_transport()
+    _raise(ctx, code)
+
+
+def trmc_moments(ctx, state, out, stream=None):
+    _raise(ctx, load().trmc_moments(ctx, C.byref(state.c), _ptr(out), _stream(stream)))
+
+
+# ---------------------------------------------------------------- helpers
+def collide_params(dt=0.0, eps=1.0, alpha=0.0, rho_scale=1.0, trunc=TRUNC_FIXED, m=2, m_min=1, m_cap=MCAP,
+                   delta1=0.005, delta2=0.01, indicator=IND_PXX):
+    return CollideParams(dt, eps, alpha, rho_scale, delta1, delta2, trunc, m, m_min, m_cap, indicator, 0)
+
+
+class ParticleState:
+    """Device arrays of one particle state (torch tensors) and the C struct
+    that names them.  After trmc_transport the roles of the primary and
+    *_alt arrays swap; after_transport() keeps the tensors in step."""
+
+    def __init__(self, cell_start, capacity=None, precision=FP64, with_x=False, rad=False,
+                 cell_param=None, cell_key=None, problem_id=0, device="cuda"):
+        import torch
+        cs = torch.as_tensor(np.asarray(cell_start, dtype=np.int64)).to(device)
+        n_cells = cs.numel() - 1
+        n = int(cs[-1].item()) if capacity is None else int(capacity)
+        dt = torch.float64 if precision == FP64 else torch.float32
+        self.precision = precision
+        self.v = torch.zeros((3, max(n, 1)), dtype=dt, device=device)
+        self.x = torch.zeros(max(n, 1), dtype=dt, device=device) if with_x else None
+        self.v_alt = torch.zeros_like(self.v) if with_x else None
+        self.x_alt = torch.zeros_like(self.x) if with_x else None
+        self.cell_start = cs
+        self.cell_start_alt = torch.zeros_like(cs) if with_x else None
+        self.m_max = torch.full((max(n_cells, 1),), 2, dtype=torch.int32, device=device) if rad else None
+        self.cell_param = None
+        if cell_param is not None:
+            cp = np.asarray(cell_param, dtype=np.float64).reshape(n_cells, 4)
+            self.cell_param = torch.as_tensor(cp).to(device)
+        self.cell_key = None if cell_key is None else torch.as_tensor(
+            np.asarray(cell_key, dtype=np.uint64).view(np.int64)).to(device)
+        self.cell_vmax2 = torch.zeros(max(n_cells, 1), dtype=torch.float64, device=device)
+        self.n_cells = n_cells
+        self.capacity = n
+        self.c = State()
+        self.c.capacity = n
+        self.c.n_cells = n_cells
+        self.c.problem_id = problem_id
+        self._fill()
+
+    def _fill(self):
+        c = self.c
+        c.vx, c.vy, c.vz = (self.v[i].data_ptr() for i in range(3))
+        c.x = self.x.data_ptr() if self.x is not None else None
+        if self.v_alt is not None:
+            c.vx_alt, c.vy_alt, c.vz_alt = (self.v_alt[i].data_ptr() for i in range(3))
+            c.x_alt = self.x_alt.data_ptr()
+            c.cell_start_alt = self.cell_start_alt.data_ptr()
+        c.cell_start = self.cell_start.data_ptr()
+        c.m_max = self.m_max.data_ptr() if self.m_max is not None else None
+        c.cell_param = self.cell_param.data_ptr() if self.cell_param is not None else None
+        c.cell_key = self.cell_key.data_ptr() if self.cell_key is not None else None
+        c.cell_vmax2 = self.cell_vmax2.data_ptr()
+
+    def after_transport(self):
+        if self.c.vx == self.v_alt[0].data_ptr():
+            self.v, self.v_alt = self.v_alt, self.v
+            self.x, self.x_alt = self.x_alt, self.x
+            self.cell_start, self.cell_start_alt = self.cell_start_alt, self.cell_start
+        self._fill()
+
+    def set_velocities(self, v):
+        import torch
+        self.v[:, :v.shape[1]].copy_(torch.as_tensor(np.asarray(v)).to(self.v.dtype))
+
+    def set_positions(self, x):
+        import torch
+        self.x[:len(x)].copy_(torch.as_tensor(np.asarray(x)).to(self.x.dtype))
+
+
+def report_dict(row):
+    row = np.asarray(row)
+    d = {f: int(row[i]) for i, f in enumerate(REPORT_FIELDS)}
+    d["Nk"] = row[16:16 + MCAP + 2].copy()
+    d["Ck"] = row[16 + MCAP + 2:16 + 2 * (MCAP + 2)].copy()
+    d["Dk"] = row[16 + 2 * (MCAP + 2):16 + 3 * (MCAP + 2)].copy()
+    return d

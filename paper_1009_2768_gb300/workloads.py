@@ -1,0 +1,152 @@
+"""Set-up of the synthetic workloads through the C ABI (trmc_init_cells),
+and one time step of each.  Everything runs in libtrmc; this module only
+lays out the cell tables the library reads.
+
+Workloads (synthetic closed-form initial data, no dataset):
+  * ShockTubes  -- 1D Riemann shock tubes on [0,1] (left rho=1, T=1; right
+    rho=0.125, T=0.8; u=0), specular walls, hard-sphere VHS, CFL 0.5, one
+    tube per Knudsen number, all advanced together;
+  * HomogeneousBKW -- one space-homogeneous cell of Maxwell molecules with
+    BKW initial data (K0 = 0.6, unit density and temperature);
+  * BatchedRelaxation -- independent homogeneous cells with log-uniform
+    particle counts and Knudsen numbers, bi-Maxwellian initial data.
+"""
+import numpy as np
+
+from . import synth
+from . import trmc as T
+
+DOMAIN_DTYPE = np.dtype([("b", "i4"), ("n", "i4"), ("lo", "f8"), ("hi", "f8")])
+
+
+def _dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+class ShockTubes:
+    def __init__(self, eps_list=(1e-1, 1e-2, 1e-3, 1e-4), n_cells=400, mean_per_cell=500,
+                 precision=T.FP64, seed=0, alpha=1.0, trunc=T.TRUNC_RAD, m_init=2, cfl=0.5,
+                 workspace=512 << 20):
+        import torch
+        self.n_tubes = len(eps_list)
+        self.n_cells_tube = n_cells
+        counts1 = synth.shock_tube_counts(n_cells, mean_per_cell)
+        counts = np.tile(counts1, self.n_tubes)
+        cs = synth.starts(counts)
+        self.n_particles = int(cs[-1])
+        nt = int(counts1.sum())
+        rho_scale = 0.5625 * n_cells / nt         # tube mass 0.5*1 + 0.5*0.125 over nt particles, per cell width
+        nc = n_cells * self.n_tubes
+        cp = np.zeros((nc, 4))
+        cp[:, 0] = np.repeat(np.asarray(eps_list, float), n_cells)
+        cp[:, 2] = rho_scale
+        cp[:, 3] = alpha
+        keys = np.array([(t << 32) | c for t in range(self.n_tubes) for c in range(n_cells)], np.uint64)
+        ci = np.zeros((nc, T.INIT_COLS))
+        for t in range(self.n_tubes):
+            for c in range(n_cells):
+                ci[t * n_cells + c] = [T.INIT_MAXWELL, 0, 0, 0, 1.0 if c < n_cells // 2 else 0.8, 0, 0,
+                                       c / n_cells, (c + 1) / n_cells]
+        self.state = T.ParticleState(cs, precision=precision, with_x=True, rad=trunc == T.TRUNC_RAD,
+                                     cell_param=cp, cell_key=keys)
+        if trunc == T.TRUNC_RAD:
+            self.state.m_max.fill_(m_init)
+        self.ctx = T.trmc_create(precision, seed, workspace)
+        T.trmc_init_cells(self.ctx, self.state, _dev(ci))
+        doms = np.array([(t * n_cells, n_cells, 0.0, 1.0) for t in range(self.n_tubes)], DOMAIN_DTYPE)
+        self.domains = _dev(doms.view(np.uint8))
+        self.dt = torch.zeros(self.n_tubes, dtype=torch.float64, device="cuda")
+        self.cfl = cfl
+        self.params = T.collide_params(trunc=trunc, m=m_init, indicator=T.IND_PXX)
+        self.step_index = 0
+
+    def step(self, stats=None, events=None):
+        """One splitting step: transport + sort, then collide.  events, if
+        given, is a list of three CUDA events recorded before transport,
+        between transport and collide, and after collide."""
+        if events:
+            events[0].record()
+        T.trmc_transport(self.ctx, self.state, self.domains, self.n_tubes, self.cfl, self.dt)
+        if events:
+            events[1].record()
+        T.trmc_collide(self.ctx, self.state, self.params, self.step_index, stats=stats)
+        if events:
+            events[2].record()
+        self.step_index += 1
+
+    launches_per_step = 5     # cfl, count, scan, scatter, collide
+
+    def close(self):
+        T.trmc_destroy(self.ctx)
+
+
+class HomogeneousBKW:
+    def __init__(self, n=100000, K0=0.6, eps=1.0, dt=0.05, precision=T.FP64, seed=0, trunc=T.TRUNC_RAD, m_init=2,
+                 workspace=256 << 20):
+        cs = np.array([0, n], np.int64)
+        self.n_particles = n
+        self.state = T.ParticleState(cs, precision=precision, rad=trunc == T.TRUNC_RAD)
+        if trunc == T.TRUNC_RAD:
+            self.state.m_max.fill_(m_init)
+        self.ctx = T.trmc_create(precision, seed, workspace)
+        ci = np.array([[T.INIT_BKW, 0, 0, 0, 1.0, 0, K0, 0, 1]], float)
+        T.trmc_init_cells(self.ctx, self.state, _dev(ci))
+        self.params = T.collide_params(dt=dt, eps=eps, alpha=0.0, rho_scale=1.0 / n, trunc=trunc, m=m_init,
+                                       indicator=T.IND_M4)
+        self.step_index = 0
+
+    def step(self, stats=None, events=None):
+        if events:
+            events[0].record()
+            events[1].record()
+        T.trmc_collide(self.ctx, self.state, self.params, self.step_index, stats=stats)
+        if events:
+            events[2].record()
+        self.step_index += 1
+
+    launches_per_step = 1
+
+    def close(self):
+        T.trmc_destroy(self.ctx)
+
+
+class BatchedRelaxation:
+    def __init__(self, n_cells=4096, lo=64, hi=8192, eps_lo=1e-4, eps_hi=10.0, alpha=0.6, dt=0.05,
+                 precision=T.FP32_MIXED, seed=0, trunc=T.TRUNC_RAD, m_init=2, workspace=1 << 30):
+        g = synth.rng(seed)
+        counts = synth.loguniform_ints(n_cells, lo, hi, g=g)
+        eps = synth.loguniform(n_cells, eps_lo, eps_hi, g=g)
+        ratio = g.uniform(0.3, 3.0, n_cells)          # T_par / T_perp with T = (T_par + 2 T_perp)/3 = 1
+        t_perp = 3.0 / (ratio + 2.0)
+        t_par = ratio * t_perp
+        cs = synth.starts(counts)
+        self.n_particles = int(cs[-1])
+        cp = np.stack([eps, np.full(n_cells, dt), 1.0 / counts, np.full(n_cells, alpha)], axis=1)
+        keys = np.array([(c << 32) for c in range(n_cells)], np.uint64)     # every cell its own problem
+        self.state = T.ParticleState(cs, precision=precision, rad=trunc == T.TRUNC_RAD, cell_param=cp,
+                                     cell_key=keys)
+        if trunc == T.TRUNC_RAD:
+            self.state.m_max.fill_(m_init)
+        self.ctx = T.trmc_create(precision, seed, workspace)
+        ci = np.zeros((n_cells, T.INIT_COLS))
+        ci[:, 0] = T.INIT_BIMAXWELL
+        ci[:, 4] = t_par
+        ci[:, 5] = t_perp
+        T.trmc_init_cells(self.ctx, self.state, _dev(ci))
+        self.params = T.collide_params(trunc=trunc, m=m_init, indicator=T.IND_PXX)
+        self.step_index = 0
+
+    def step(self, stats=None, events=None):
+        if events:
+            events[0].record()
+            events[1].record()
+        T.trmc_collide(self.ctx, self.state, self.params, self.step_index, stats=stats)
+        if events:
+            events[2].record()
+        self.step_index += 1
+
+    launches_per_step = 1
+
+    def close(self):
+        T.trmc_destroy(self.ctx)

@@ -1,0 +1,55 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports
+every entry point declared in include/trmc.h; the binding refuses to run
+without the library (no fallback)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "trmc.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:trmc_status|const char \*)\s*(trmc_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for n in ("trmc_init_cells", "trmc_collide", "trmc_transport", "trmc_moments",
+              "trmc_create", "trmc_destroy", "trmc_last_error", "trmc_check"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1009_2768_gb300 import build
+    lib = build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(trmc_\w+)$", out, re.M))
+    missing = [n for n in declared() if n not in exported]
+    assert not missing, missing
+    import ctypes
+    so = ctypes.CDLL(lib)            # loads without a GPU: no CUDA call at load time
+    for n in declared():
+        assert hasattr(so, n)
+    from paper_1009_2768_gb300 import trmc
+    assert sorted(trmc.EXPORTS) == declared()
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1009_2768_gb300 import trmc
+    monkeypatch.setattr(trmc, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(trmc, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        trmc.trmc_create(trmc.FP64, 0, 0)
+
+
+def test_struct_layouts_match_header():
+    import ctypes
+    from paper_1009_2768_gb300 import trmc
+    assert ctypes.sizeof(trmc.State) == 14 * 8 + 8 + 4 + 4
+    assert ctypes.sizeof(trmc.CollideParams) == 6 * 8 + 6 * 4
+    assert ctypes.sizeof(trmc.Domain) == 24
+    assert ctypes.sizeof(trmc.CellParam) == 32
+    assert ctypes.sizeof(trmc.Stats) == 80

@@ -1,0 +1,284 @@
+"""Parity of the CUDA library (FP64 contexts) with the CPU oracle, through
+the C ABI: the per-cell plan records (split quotas, collisions and demand
+per level, roles, passes, counters) must be bit-identical and every
+velocity must agree within 1e-12 relative; transport and the cell sort
+must be bit-identical; init and moments within 1e-12."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1009_2768_gb300 import synth
+from tests.gpu_common import (T, TOL_V, assert_velocity_parity, ctx, gpu_collide, need_gpu, oracle_params,
+                              torch)
+
+pytestmark = pytest.mark.gpu
+
+COUNTS = [2, 3, 5, 17, 64, 255, 256, 257, 889, 1000, 2500, 4100]
+
+
+def cells(counts, seed, kind="bimax"):
+    g = synth.rng(seed)
+    if kind == "bkw":
+        v = np.concatenate([synth.bkw(n, 0.6, g=g) for n in counts], axis=1)
+    else:
+        v = np.concatenate([synth.bimaxwellian(n, 2.0, 0.5, u=(0.3, -0.1, 0.2), g=g) for n in counts], axis=1)
+    return v, synth.starts(counts)
+
+
+def compare(v, cs, p, step, m_state=None, cell_param=None, cell_key=None, workspace=256 << 20):
+    need_gpu()
+    g = gpu_collide(v, cs, p, step, m_state=m_state, cell_param=cell_param, cell_key=cell_key, workspace=workspace)
+    vo, rep, ms = O.collide(v, cs, oracle_params(O, p), step, m_state=m_state,
+                            cell_param=None if cell_param is None else np.asarray(cell_param, np.float64).ravel(),
+                            cell_key=cell_key)
+    assert np.array_equal(g["report"], rep), first_report_diff(g["report"], rep)
+    assert_velocity_parity(g["v"], vo, cs)
+    if m_state is not None:
+        assert np.array_equal(g["m_state"], ms)
+    return g, vo, rep
+
+
+def first_report_diff(a, b):
+    idx = np.argwhere(a != b)
+    if len(idx) == 0:
+        return ""
+    c, f = idx[0]
+    name = T.REPORT_FIELDS[f] if f < 16 else ("Nk", "Ck", "Dk")[(f - 16) // (T.MCAP + 2)] + f"[{(f - 16) % (T.MCAP + 2)}]"
+    return f"cell {c} field {name}: gpu {a[c, f]} oracle {b[c, f]}"
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.6, 1.0])
+@pytest.mark.parametrize("eps", [1e-4, 0.05, 1.0, 50.0])
+@pytest.mark.parametrize("trunc,m", [(T.TRUNC_FIXED, 1), (T.TRUNC_FIXED, 4), (T.TRUNC_RAD, 2), (T.TRUNC_UNLIMITED, 2)])
+def test_collide_parity(alpha, eps, trunc, m):
+    v, cs = cells(COUNTS, seed=int(100 * alpha) + int(1000 * eps) + m)
+    p = T.collide_params(dt=0.05, eps=eps, alpha=alpha, rho_scale=1.0 / 500, trunc=trunc, m=m)
+    ms = np.full(len(COUNTS), m, np.int32) if trunc == T.TRUNC_RAD else None
+    compare(v, cs, p, step=7, m_state=ms)
+
+
+def test_collide_parity_rad_continuations():
+    # far from equilibrium and a long step: several TRMC-RAD passes per cell
+    v, cs = cells([300, 1200, 3000], seed=3)
+    p = T.collide_params(dt=2.0, eps=1.0, alpha=0.0, rho_scale=1.0 / 1000, trunc=T.TRUNC_RAD, m=1,
+                         indicator=T.IND_PXX)
+    g, vo, rep = compare(v, cs, p, step=1, m_state=np.ones(3, np.int32))
+    assert rep[:, 1].max() >= 2, "expected at least one continuation pass"
+
+
+def test_collide_parity_bkw_m4_indicator():
+    v, cs = cells([5000, 20000], seed=4, kind="bkw")
+    p = T.collide_params(dt=0.05, eps=1.0, alpha=0.0, rho_scale=1.0 / 20000, trunc=T.TRUNC_RAD, m=2,
+                         indicator=T.IND_M4)
+    ms = np.array([2, 4], np.int32)
+    for step in range(3):
+        g, v, rep = compare(v, cs, p, step=step, m_state=ms)
+        ms = g["m_state"]
+
+
+def test_collide_parity_single_cell_1e5():
+    """The homogeneous single-cell workload size (N = 1e5, BKW data): the
+    cell does not fit in shared memory and runs from the device slab."""
+    v, cs = cells([100000], seed=5, kind="bkw")
+    p = T.collide_params(dt=0.05, eps=1.0, alpha=0.0, rho_scale=1e-5, trunc=T.TRUNC_RAD, m=2, indicator=T.IND_M4)
+    compare(v, cs, p, step=0, m_state=np.array([2], np.int32))
+
+
+def test_collide_per_cell_params_and_keys():
+    counts = [64, 500, 3000, 8192]
+    v, cs = cells(counts, seed=6)
+    g = synth.rng(7)
+    eps = synth.loguniform(len(counts), 1e-4, 10, g=g)
+    cp = np.stack([eps, np.full(4, 0.05), 1.0 / np.array(counts, float), np.full(4, 0.6)], axis=1)
+    keys = np.array([(11 << 32) | 0, (12 << 32) | 0, (13 << 32) | 0, (14 << 32) | 0], np.uint64)
+    p = T.collide_params(trunc=T.TRUNC_RAD, m=2)
+    compare(v, cs, p, step=3, m_state=np.full(4, 2, np.int32), cell_param=cp, cell_key=keys)
+
+
+def test_collide_deterministic_and_batch_independent():
+    need_gpu()
+    counts = [700, 40, 2000]
+    v, cs = cells(counts, seed=8)
+    keys = np.array([(5 << 32) | 3, (6 << 32) | 1, (7 << 32) | 9], np.uint64)
+    p = T.collide_params(dt=0.3, eps=0.5, alpha=1.0, rho_scale=1e-3, trunc=T.TRUNC_FIXED, m=3)
+    a = gpu_collide(v, cs, p, 2, cell_key=keys)
+    b = gpu_collide(v, cs, p, 2, cell_key=keys)
+    assert np.array_equal(a["v"], b["v"]) and np.array_equal(a["report"], b["report"])
+    alone = gpu_collide(v[:, cs[1]:cs[2]], [0, counts[1]], p, 2, cell_key=keys[1:2])
+    assert np.array_equal(alone["v"], a["v"][:, cs[1]:cs[2]])
+
+
+def test_conservation_fp64():
+    need_gpu()
+    v, cs = cells(COUNTS, seed=9)
+    p = T.collide_params(dt=0.05, eps=0.01, alpha=1.0, rho_scale=1.0 / 500, trunc=T.TRUNC_RAD, m=2)
+    g = gpu_collide(v, cs, p, 0, m_state=np.full(len(COUNTS), 2, np.int32))
+    for c in range(len(COUNTS)):
+        a, b = cs[c], cs[c + 1]
+        scale = np.abs(v[:, a:b]).sum()
+        assert np.all(np.abs(g["v"][:, a:b].sum(1) - v[:, a:b].sum(1)) <= 1e-12 * scale)
+        e0 = (v[:, a:b] ** 2).sum()
+        assert abs((g["v"][:, a:b] ** 2).sum() - e0) <= 1e-12 * e0
+
+
+def test_capacity_error_is_reported_and_cell_left_unchanged():
+    need_gpu()
+    v, cs = cells([20000], seed=10)
+    p = T.collide_params(dt=0.05, eps=1.0, rho_scale=1e-4, trunc=T.TRUNC_FIXED, m=2)
+    c = ctx(T.FP64, 0, 64 << 10)                     # 64 KiB workspace cannot hold 20000 FP64 particles
+    st = T.ParticleState(cs, precision=T.FP64)
+    st.set_velocities(v)
+    T.trmc_collide(c, st, p, 0)
+    with pytest.raises(T.TrmcError) as e:
+        T.trmc_check(c)
+    assert e.value.code == T.ERR_CAPACITY
+    assert np.array_equal(st.v.cpu().numpy(), v)
+    T.trmc_check(c)                                  # cleared
+
+
+def test_argument_errors():
+    need_gpu()
+    c = ctx()
+    st = T.ParticleState([0, 10], precision=T.FP64)
+    for bad in (T.collide_params(m=0), T.collide_params(trunc=7), T.collide_params(eps=0.0),
+                T.collide_params(m_cap=65), T.collide_params(trunc=T.TRUNC_RAD)):
+        with pytest.raises(T.TrmcError) as e:
+            T.trmc_collide(c, st, bad, 0)
+        assert e.value.code == T.ERR_ARG
+
+
+# ---------------------------------------------------------------- transport / sort
+def tube_state(n_cells, mean, seed, ntubes=1):
+    g = synth.rng(seed)
+    counts = np.concatenate([synth.shock_tube_counts(n_cells, mean)] * ntubes)
+    cs = synth.starts(counts)
+    x = np.concatenate([(c % n_cells + g.random(k)) / n_cells for c, k in enumerate(counts)])
+    v = synth.maxwellian(int(cs[-1]), g=g)
+    doms = [(t * n_cells, n_cells, 0.0, 1.0) for t in range(ntubes)]
+    return x, v, cs, doms
+
+
+def gpu_transport(x, v, cs, doms, dt=None, cfl=0.0, vmax2=None):
+    st = T.ParticleState(cs, precision=T.FP64, with_x=True)
+    st.set_velocities(v)
+    st.set_positions(x)
+    if vmax2 is not None:
+        st.cell_vmax2.copy_(torch.as_tensor(vmax2))
+    dd = torch.as_tensor(np.array([tuple(d) for d in doms],
+                                  dtype=[("b", "i4"), ("n", "i4"), ("lo", "f8"), ("hi", "f8")]).view(np.uint8)).cuda()
+    dtt = torch.as_tensor(np.asarray(dt if dt is not None else np.zeros(len(doms)), np.float64)).cuda()
+    c = ctx()
+    T.trmc_transport(c, st, dd, len(doms), cfl, dtt)
+    T.trmc_check(c)
+    n = int(cs[-1])
+    return st.x[:n].cpu().numpy(), st.v[:, :n].cpu().numpy(), st.cell_start.cpu().numpy(), dtt.cpu().numpy()
+
+
+def test_transport_parity_bit_exact():
+    need_gpu()
+    x, v, cs, doms = tube_state(400, 500, seed=11, ntubes=2)
+    dt = O.cfl_dt(v, cs, doms, 0.5)
+    xg, vg, csg, _ = gpu_transport(x, v, cs, doms, dt=dt)
+    xo, vo, cso = O.transport(x, v, cs, doms, dt)
+    assert np.array_equal(csg, cso)
+    assert np.array_equal(xg, xo)
+    assert np.array_equal(vg, vo)
+
+
+def test_transport_cfl_mode_matches_oracle_dt():
+    need_gpu()
+    x, v, cs, doms = tube_state(64, 300, seed=12, ntubes=3)
+    mom = O.moments(v, cs)
+    dto = O.cfl_dt(v, cs, doms, 0.5)
+    xg, vg, csg, dtg = gpu_transport(x, v, cs, doms, cfl=0.5, vmax2=mom[:, 9])
+    assert np.array_equal(dtg, dto)
+    xo, vo, cso = O.transport(x, v, cs, doms, dto)
+    assert np.array_equal(csg, cso) and np.array_equal(xg, xo) and np.array_equal(vg, vo)
+
+
+def test_transport_rejects_moves_beyond_one_cell():
+    need_gpu()
+    x, v, cs, doms = tube_state(32, 50, seed=13)
+    with pytest.raises(T.TrmcError) as e:
+        gpu_transport(x, v, cs, doms, dt=[10.0])
+    assert e.value.code == T.ERR_STATE
+
+
+# ---------------------------------------------------------------- init / moments
+def test_init_parity():
+    need_gpu()
+    counts = [1000, 3, 0, 2000, 500]
+    cs = synth.starts(counts)
+    ci = np.zeros((5, T.INIT_COLS))
+    ci[0] = [T.INIT_MAXWELL, 0.5, -1, 0, 2.0, 0, 0, 0.0, 0.25]
+    ci[1] = [T.INIT_BIMAXWELL, 0, 0, 0, 2.5, 0.25, 0, 0.25, 0.5]
+    ci[2] = [T.INIT_MAXWELL, 0, 0, 0, 1.0, 0, 0, 0.5, 0.75]
+    ci[3] = [T.INIT_BKW, 0, 0, 0, 1.0, 0, 0.6, 0.75, 1.0]
+    ci[4] = [T.INIT_BKW, 0.1, 0, 0, 1.0, 0, 0.8, 0.0, 1.0]
+    st = T.ParticleState(cs, precision=T.FP64, with_x=True)
+    c = T.trmc_create(T.FP64, 42, 1 << 20)
+    T.trmc_init_cells(c, st, torch.as_tensor(ci).cuda())
+    T.trmc_check(c)
+    T.trmc_destroy(c)
+    xo, vo = O.init_cells(ci, cs, 42)
+    n = int(cs[-1])
+    assert_velocity_parity(st.v[:, :n].cpu().numpy(), vo, cs)
+    assert np.allclose(st.x[:n].cpu().numpy(), xo, rtol=0, atol=1e-14)
+    mom = O.moments(vo, cs)
+    assert np.allclose(st.cell_vmax2.cpu().numpy(), mom[:, 9], rtol=1e-12, atol=0)
+
+
+def test_moments_parity():
+    need_gpu()
+    v, cs = cells(COUNTS + [0, 1], seed=14)
+    st = T.ParticleState(cs, precision=T.FP64)
+    st.set_velocities(v)
+    out = torch.zeros((st.n_cells, T.MOM_COLS), dtype=torch.float64, device="cuda")
+    T.trmc_moments(ctx(), st, out)
+    mo = O.moments(v, cs)
+    assert np.allclose(out.cpu().numpy(), mo, rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------- whole steps
+def test_shock_tube_chain_parity():
+    """Transport (CFL 0.5, specular walls) + sort + VHS hard-sphere collide
+    for several steps on a 100-cell shock tube, GPU and oracle each running
+    their own chain from the same initial state."""
+    need_gpu()
+    n_cells = 100
+    counts = synth.shock_tube_counts(n_cells, 200)
+    cs = synth.starts(counts)
+    ci = np.zeros((n_cells, T.INIT_COLS))
+    for c in range(n_cells):
+        T_ = 1.0 if c < n_cells // 2 else 0.8
+        ci[c] = [T.INIT_MAXWELL, 0, 0, 0, T_, 0, 0, c / n_cells, (c + 1) / n_cells]
+    w = 0.5625 / cs[-1] * n_cells             # particle mass / cell width: rho_L = 1
+    cp = np.tile([1e-2, 0.0, w, 1.0], (n_cells, 1))
+    st = T.ParticleState(cs, precision=T.FP64, with_x=True, rad=True, cell_param=cp)
+    c = T.trmc_create(T.FP64, 3, 64 << 20)
+    T.trmc_init_cells(c, st, torch.as_tensor(ci).cuda())
+    xo, vo = O.init_cells(ci, cs, 3)
+    cso = cs.copy()
+    mo = np.full(n_cells, 2, np.int32)
+    doms = [(0, n_cells, 0.0, 1.0)]
+    dd = torch.as_tensor(np.array([tuple(d) for d in doms],
+                                  dtype=[("b", "i4"), ("n", "i4"), ("lo", "f8"), ("hi", "f8")]).view(np.uint8)).cuda()
+    dtt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p = T.collide_params(trunc=T.TRUNC_RAD, m=2)
+    po = oracle_params(O, p)
+    po.seed = 3
+    for step in range(5):
+        T.trmc_transport(c, st, dd, 1, 0.5, dtt)
+        T.trmc_collide(c, st, p, step)
+        T.trmc_check(c)
+        dto = O.cfl_dt(vo, cso, doms, 0.5)
+        xo, vo, cso = O.transport(xo, vo, cso, doms, dto)
+        cpo = cp.copy(); cpo[:, 1] = dto[0]
+        vo, _, mo = O.collide(vo, cso, po, step, m_state=mo, cell_param=cpo.ravel())
+        n = int(cs[-1])
+        assert abs(dtt.item() - dto[0]) <= 1e-14 * dto[0]
+        assert np.array_equal(st.cell_start.cpu().numpy(), cso)
+        assert np.allclose(st.x[:n].cpu().numpy(), xo, rtol=0, atol=1e-12)
+        assert_velocity_parity(st.v[:, :n].cpu().numpy(), vo, cso, tol=1e-11)
+        assert np.array_equal(st.m_max.cpu().numpy(), mo)
+    T.trmc_destroy(c)
