@@ -191,15 +191,21 @@ static void binary_collision(vec3 a, vec3 b, const uint64_t w[4], double alpha, 
 
 typedef struct {
     int64_t coll, dummy, exceed;
+    /* what the collisions changed: sum over this pass's leaves of
+     * (output - original) for v, |v|^2 and the adaptive indicator */
+    double dP[3], dE, dS;
 } counters_t;
 
 /* Execute one planned pass.  part[i] (i < n_total) are the participating
  * particle slots; vin holds their (original) velocities, vfin receives the
  * outputs.  On return pool[0..R-1] lists the thermalised slots in rank order
  * and is_pool/is_level0 flags are updated. */
+static double indicator(vec3 v, const double U[3], int ind);
+
 static void run_pass(const plan_t *pl, const keyctx *k, uint32_t pass,
                      const int64_t *part, int64_t n_total, const vec3 *vin, vec3 *vfin,
-                     int64_t *pool, double alpha, double Sigma, counters_t *cnt)
+                     int64_t *pool, double alpha, double Sigma, const double U[3], int ind,
+                     counters_t *cnt)
 {
     int m = pl->m_eff;
     /* Roles: a uniform permutation of the participants (READING: the paper
@@ -261,8 +267,13 @@ static void run_pass(const plan_t *pl, const keyctx *k, uint32_t pass,
     /* Output j (levels 1..m in order, then by rank) replaces leaf j. */
     int64_t j = 0;
     for (int n = 1; n <= m; ++n)
-        for (int64_t o = 0; o < pl->out[n]; ++o)
-            vfin[leaf[j++]] = prod[n][outp[n][o]];
+        for (int64_t o = 0; o < pl->out[n]; ++o) {
+            vec3 nv = prod[n][outp[n][o]], ov = vin[leaf[j]];
+            cnt->dP[0] += nv.x - ov.x; cnt->dP[1] += nv.y - ov.y; cnt->dP[2] += nv.z - ov.z;
+            cnt->dE += (nv.x * nv.x + nv.y * nv.y + nv.z * nv.z) - (ov.x * ov.x + ov.y * ov.y + ov.z * ov.z);
+            cnt->dS += indicator(nv, U, ind) - indicator(ov, U, ind);
+            vfin[leaf[j++]] = nv;
+        }
     for (int n = 0; n <= MC; ++n) { free(prod[n]); free(feeder[n]); free(outp[n]); }
     free(leaf);
 }
@@ -332,10 +343,9 @@ int orc_collide_cell(double *vx, double *vy, double *vz, int64_t n,
      * continues with levels m+1..2m on the thermalised set (Sec. 4.3). */
     int64_t *part = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     int64_t *pool = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
-    unsigned char *in_pool = (unsigned char *)calloc((size_t)n, 1);
     for (int64_t i = 0; i < n; ++i) part[i] = i;
     int64_t n_part = n;
-    counters_t cnt = { 0, 0, 0 };
+    counters_t cnt = { 0, 0, 0, { 0.0, 0.0, 0.0 }, 0.0, 0.0 };
     int m = m0, lo = 0, m_next = m0;
     uint32_t pass = 0;
     int64_t R = 0, leaves_total = 0;
@@ -360,30 +370,31 @@ int orc_collide_cell(double *vx, double *vy, double *vz, int64_t n,
             report[ORC_R_PDROP] += pl.pdrop;
             report[ORC_R_PSURP] += pl.psurp;
         }
-        run_pass(&pl, &k, pass, part, n_part, vin, vfin, pool, alpha, Sigma, &cnt);
+        run_pass(&pl, &k, pass, part, n_part, vin, vfin, pool, alpha, Sigma, U, prm->indicator, &cnt);
         leaves_total += pl.leaves;
         R = pl.R;
         plan_free(&pl);
-        for (int64_t i = 0; i < n_part; ++i) in_pool[part[i]] = 0;
-        for (int64_t t = 0; t < R; ++t) in_pool[pool[t]] = 1;
         if (prm->trunc != ORC_TRUNC_RAD) { m_next = m; break; }
 
         /* TRMC-RAD test (Sec. 4.3): E1 = |S^{n+1,m} - S^n| / |S^n| with the
          * thermalised part taken from the analytic Maxwellian it will be
-         * sampled from (last paragraph of Sec. 4.3). */
-        double Snt = 0.0, Pnt[3] = { 0, 0, 0 }, Ent = 0.0;
-        for (int64_t i = 0; i < n; ++i) {
-            if (in_pool[i]) continue;
-            Snt += indicator(vfin[i], U, prm->indicator);
-            Pnt[0] += vfin[i].x; Pnt[1] += vfin[i].y; Pnt[2] += vfin[i].z;
-            Ent += vfin[i].x * vfin[i].x + vfin[i].y * vfin[i].y + vfin[i].z * vfin[i].z;
+         * sampled from (last paragraph of Sec. 4.3).  The change of the
+         * indicator sum is formed from the particles that changed: the
+         * collisions' dS, minus the thermalised set's original sum, plus its
+         * analytic Maxwellian sum. */
+        double Pp[3] = { 0, 0, 0 }, Ep = 0.0, Sp = 0.0;
+        for (int64_t t = 0; t < R; ++t) {
+            vec3 v = vin[pool[t]];
+            Pp[0] += v.x; Pp[1] += v.y; Pp[2] += v.z;
+            Ep += v.x * v.x + v.y * v.y + v.z * v.z;
+            Sp += indicator(v, U, prm->indicator);
         }
         double Sth = 0.0;
         if (R == 1) {
             Sth = indicator(vin[pool[0]], U, prm->indicator);
         } else if (R >= 2) {
-            double Pt[3] = { P[0] - Pnt[0], P[1] - Pnt[1], P[2] - Pnt[2] };
-            double Et = E - Ent;
+            double Pt[3] = { Pp[0] - cnt.dP[0], Pp[1] - cnt.dP[1], Pp[2] - cnt.dP[2] };
+            double Et = Ep - cnt.dE;
             double et = Et - (Pt[0] * Pt[0] + Pt[1] * Pt[1] + Pt[2] * Pt[2]) / (double)R;
             if (et < 0.0) et = 0.0;
             double ub[3] = { Pt[0] / (double)R, Pt[1] / (double)R, Pt[2] / (double)R };
@@ -396,8 +407,8 @@ int orc_collide_cell(double *vx, double *vy, double *vz, int64_t n,
                 Sth = et / 3.0 + (double)R * d * d;
             }
         }
-        double S_post = (Snt + Sth) / (double)n;
-        double E1 = (S_pre != 0.0) ? fabs(S_post - S_pre) / fabs(S_pre) : 0.0;
+        double dS_total = cnt.dS + (Sth - Sp);
+        double E1 = (S_pre != 0.0) ? fabs(dS_total) / fabs((double)n * S_pre) : 0.0;
         if (E1 > prm->delta2 && R > 0 && 2 * m <= prm->m_cap) {
             /* Reject: keep what was computed, continue with 2m. */
             for (int64_t t = 0; t < R; ++t) part[t] = pool[t];
@@ -417,14 +428,16 @@ int orc_collide_cell(double *vx, double *vy, double *vz, int64_t n,
      * (READING of the conservative sampling cited at the end of Sec. 4.2:
      * v = P_t/R + s (z - zbar), s fixing the kinetic energy). */
     if (R >= 2) {
-        double Pnt[3] = { 0, 0, 0 }, Ent = 0.0;
-        for (int64_t i = 0; i < n; ++i) {
-            if (in_pool[i]) continue;
-            Pnt[0] += vfin[i].x; Pnt[1] += vfin[i].y; Pnt[2] += vfin[i].z;
-            Ent += vfin[i].x * vfin[i].x + vfin[i].y * vfin[i].y + vfin[i].z * vfin[i].z;
+        /* target: what the thermalised set carried, corrected by what the
+         * collisions' round-off changed (sums over changed particles only) */
+        double Pt[3] = { 0, 0, 0 }, Et = 0.0;
+        for (int64_t t = 0; t < R; ++t) {
+            vec3 v = vin[pool[t]];
+            Pt[0] += v.x; Pt[1] += v.y; Pt[2] += v.z;
+            Et += v.x * v.x + v.y * v.y + v.z * v.z;
         }
-        double Pt[3] = { P[0] - Pnt[0], P[1] - Pnt[1], P[2] - Pnt[2] };
-        double Et = E - Ent;
+        Pt[0] -= cnt.dP[0]; Pt[1] -= cnt.dP[1]; Pt[2] -= cnt.dP[2];
+        Et -= cnt.dE;
         vec3 *z = (vec3 *)malloc(sizeof(vec3) * (size_t)R);
         double zs[3] = { 0, 0, 0 };
         for (int64_t t = 0; t < R; ++t) {
@@ -472,7 +485,7 @@ int orc_collide_cell(double *vx, double *vy, double *vz, int64_t n,
         report[ORC_R_DUMMY] = cnt.dummy;
         report[ORC_R_EXCEED] = cnt.exceed;
     }
-    free(vin); free(vfin); free(part); free(pool); free(in_pool);
+    free(vin); free(vfin); free(part); free(pool);
     return 0;
 }
 

@@ -67,7 +67,7 @@ struct Sh {
     int32_t cell, n, m, lo, m_eff, pass, n0, D0, R, npart, m_next, Dge1;
     int32_t n0_prev, D0_prev;
     int32_t feas, pdrop, psurp, pdrop_tot, psurp_tot, skip, cont, m_top, m_first, n0_first;
-    double q, Sigma, U[3], P[3], E, S_pre, Pnt[3], Ent, Snt;
+    double q, Sigma, U[3], P[3], E, S_pre, dP[3], dE, dS, Pp[3], Ep, Sp;
     double alpha, dt, eps, rho_scale;
     uint64_t problem, lcell;
     U64x4 keyK;
@@ -178,7 +178,7 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
         sh.m = m0; sh.m_next = m0; sh.m_first = m0; sh.lo = 0; sh.pass = 0; sh.npart = n; sh.skip = 0;
         sh.feas = sh.pdrop = sh.psurp = sh.pdrop_tot = sh.psurp_tot = 0;
         sh.n0_prev = 0; sh.D0_prev = 0;
-        sh.Pnt[0] = sh.Pnt[1] = sh.Pnt[2] = 0.0; sh.Ent = 0.0; sh.Snt = 0.0;
+        sh.dP[0] = sh.dP[1] = sh.dP[2] = 0.0; sh.dE = 0.0; sh.dS = 0.0;
         // persistent layout: V, flags, inv[2]
         char *smem = reinterpret_cast<char *>(dsm);
         size_t scap = size_t(a.smem_bytes);
@@ -398,20 +398,6 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
             }
         }
         __syncthreads();
-        if (pass == 0) {
-            // non-thermalised sums, part 1: the uncollided particles
-            double s[5] = {0, 0, 0, 0, 0};
-            for (int r = tid; r < n0; r += bs) {
-                const int sl = inv[r];
-                const double x = Vx[sl], y = Vy[sl], z = Vz[sl];
-                s[0] += x; s[1] += y; s[2] += z;
-                s[3] += x * x + y * y + z * z;
-                s[4] += indicator(x, y, z, sh.U, prm.indicator);
-            }
-            block_sum<5>(s, sh.red);
-            if (tid == 0) { sh.Pnt[0] = s[0]; sh.Pnt[1] = s[1]; sh.Pnt[2] = s[2]; sh.Ent = s[3]; sh.Snt = s[4]; }
-        }
-
         // 5. collision waves, level 1 first
         Real *IBx = sh.IBuf, *IBy = sh.IBuf + (Dge1 + 1), *IBz = sh.IBuf + 2 * (Dge1 + 1);
         Real *OBx = sh.OBuf, *OBy = sh.OBuf + (D0 + 1), *OBz = sh.OBuf + 2 * (D0 + 1);
@@ -476,21 +462,37 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
             __syncthreads();
         }
 
-        // 6. outputs replace the leaves; their sums join the non-thermalised part
+        // 6. outputs replace the leaves.  What the collisions changed (sum of
+        //    output - original over the leaves) and the thermalised set's own
+        //    sums give the renormalisation target and the change of the
+        //    adaptive indicator from the changed particles only, without
+        //    cancelling two sums over the whole cell.
         {
             double s[5] = {0, 0, 0, 0, 0};
             for (int jx = tid; jx < D0; jx += bs) {
                 const int sl = inv[n0 + jx];
+                const double ox = Vx[sl], oy = Vy[sl], oz = Vz[sl];
                 const Real x = OBx[jx], y = OBy[jx], z = OBz[jx];
                 Vx[sl] = x; Vy[sl] = y; Vz[sl] = z;
                 const double dx = x, dy = y, dz = z;
-                s[0] += dx; s[1] += dy; s[2] += dz;
-                s[3] += dx * dx + dy * dy + dz * dz;
-                s[4] += indicator(dx, dy, dz, sh.U, prm.indicator);
+                s[0] += dx - ox; s[1] += dy - oy; s[2] += dz - oz;
+                s[3] += (dx * dx + dy * dy + dz * dz) - (ox * ox + oy * oy + oz * oz);
+                s[4] += indicator(dx, dy, dz, sh.U, prm.indicator) - indicator(ox, oy, oz, sh.U, prm.indicator);
             }
             block_sum<5>(s, sh.red);
+            double p[5] = {0, 0, 0, 0, 0};
+            const int pool0 = n0 + D0, R = sh.R;
+            for (int t = tid; t < R; t += bs) {
+                const int sl = inv[pool0 + t];
+                const double x = Vx[sl], y = Vy[sl], z = Vz[sl];
+                p[0] += x; p[1] += y; p[2] += z;
+                p[3] += x * x + y * y + z * z;
+                p[4] += indicator(x, y, z, sh.U, prm.indicator);
+            }
+            block_sum<5>(p, sh.red);
             if (tid == 0) {
-                sh.Pnt[0] += s[0]; sh.Pnt[1] += s[1]; sh.Pnt[2] += s[2]; sh.Ent += s[3]; sh.Snt += s[4];
+                sh.dP[0] += s[0]; sh.dP[1] += s[1]; sh.dP[2] += s[2]; sh.dE += s[3]; sh.dS += s[4];
+                sh.Pp[0] = p[0]; sh.Pp[1] = p[1]; sh.Pp[2] = p[2]; sh.Ep = p[3]; sh.Sp = p[4];
             }
         }
         // TRMC-RAD test (Sec. 4.3)
@@ -503,8 +505,8 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
                     const int sl = inv[n0 + D0];
                     Sth = indicator(double(Vx[sl]), double(Vy[sl]), double(Vz[sl]), sh.U, prm.indicator);
                 } else if (R >= 2) {
-                    const double Pt0 = sh.P[0] - sh.Pnt[0], Pt1 = sh.P[1] - sh.Pnt[1], Pt2 = sh.P[2] - sh.Pnt[2];
-                    const double Et = sh.E - sh.Ent;
+                    const double Pt0 = sh.Pp[0] - sh.dP[0], Pt1 = sh.Pp[1] - sh.dP[1], Pt2 = sh.Pp[2] - sh.dP[2];
+                    const double Et = sh.Ep - sh.dE;
                     double et = Et - (Pt0 * Pt0 + Pt1 * Pt1 + Pt2 * Pt2) / double(R);
                     if (et < 0.0) et = 0.0;
                     const double u0 = Pt0 / double(R), u1 = Pt1 / double(R), u2 = Pt2 / double(R);
@@ -517,8 +519,8 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
                         Sth = et / 3.0 + double(R) * d * d;
                     }
                 }
-                const double S_post = (sh.Snt + Sth) / double(sh.n);
-                const double E1 = (sh.S_pre != 0.0) ? fabs(S_post - sh.S_pre) / fabs(sh.S_pre) : 0.0;
+                const double dS_total = sh.dS + (Sth - sh.Sp);
+                const double E1 = (sh.S_pre != 0.0) ? fabs(dS_total) / fabs(double(sh.n) * sh.S_pre) : 0.0;
                 const int m = sh.m;
                 if (E1 > prm.delta2 && R > 0 && 2 * m <= prm.m_cap) {
                     sh.cont = 1;
@@ -569,8 +571,8 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
             e[0] += a0 * a0 + a1 * a1 + a2 * a2;
         }
         block_sum<1>(e, sh.red);
-        const double Pt0 = sh.P[0] - sh.Pnt[0], Pt1 = sh.P[1] - sh.Pnt[1], Pt2 = sh.P[2] - sh.Pnt[2];
-        const double Et = sh.E - sh.Ent;
+        const double Pt0 = sh.Pp[0] - sh.dP[0], Pt1 = sh.Pp[1] - sh.dP[1], Pt2 = sh.Pp[2] - sh.dP[2];
+        const double Et = sh.Ep - sh.dE;
         double et = Et - (Pt0 * Pt0 + Pt1 * Pt1 + Pt2 * Pt2) / double(R);
         if (et < 0.0) et = 0.0;
         const double sc = (e[0] > 0.0) ? sqrt(et / e[0]) : 0.0;
