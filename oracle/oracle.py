@@ -113,7 +113,7 @@ def prp_table(n, key, inverse=False):
     return np.array([f(C.byref(p), i) for i in range(n)], dtype=np.int64)
 
 
-def collide_params(dt, eps, alpha=0.0, rho_scale=1.0, trunc=TRUNC_FIXED, m=2, m_min=1,
+def collide_params(dt=0.0, eps=1.0, alpha=0.0, rho_scale=1.0, trunc=TRUNC_FIXED, m=2, m_min=1,
                    m_cap=MCAP, delta1=0.005, delta2=0.01, indicator=IND_PXX, seed=0):
     return CollideParams(dt, eps, alpha, rho_scale, delta1, delta2, trunc, m, m_min, m_cap,
                          indicator, 0, seed)
