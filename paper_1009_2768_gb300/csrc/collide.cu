@@ -37,7 +37,6 @@ namespace trmc {
 namespace {
 
 constexpr int NLEV = kMC + 2;
-constexpr double kTwoPi = 6.283185307179586;
 
 struct Args {
     void *vx, *vy, *vz;
@@ -63,6 +62,7 @@ template <typename Real>
 struct Sh {
     int32_t Nq[NLEV], Nn[NLEV], D[NLEV], C[NLEV], out[NLEV], O[NLEV], IB[NLEV];
     int32_t Pn[kMC + 1];
+    double uS[NLEV], uP[NLEV];
     double red[32 * 8];
     int32_t cell, n, m, lo, m_eff, pass, n0, D0, R, npart, m_next, Dge1;
     int32_t n0_prev, D0_prev;
@@ -99,21 +99,18 @@ template <> struct Math<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double pow_(double x, double a) { return pow(x, a); }
     static __device__ __forceinline__ double uni(uint64_t w) { return u01(w); }
-    static __device__ __forceinline__ void angle(double u, double &s, double &c)
-    {
-        const double phi = kTwoPi * u;
-        s = sin(phi);
-        c = cos(phi);
-    }
+    // sin / cos of 2 pi u: sincospi reduces the argument exactly, so it is
+    // cheaper than sin(2 pi u) and within an ulp of it
+    static __device__ __forceinline__ void angle(double u, double &s, double &c) { sincospi(2.0 * u, &s, &c); }
     static __device__ __forceinline__ void normals(const U64x4 &w, double &z0, double &z1, double &z2)
     {
         const double r1 = sqrt(-2.0 * log(u01_open(w.w[0])));
-        const double a1 = kTwoPi * u01(w.w[1]);
         const double r2 = sqrt(-2.0 * log(u01_open(w.w[2])));
-        const double a2 = kTwoPi * u01(w.w[3]);
-        z0 = r1 * cos(a1);
-        z1 = r1 * sin(a1);
-        z2 = r2 * cos(a2);
+        double s1, c1;
+        sincospi(2.0 * u01(w.w[1]), &s1, &c1);
+        z0 = r1 * c1;
+        z1 = r1 * s1;
+        z2 = r2 * cospi(2.0 * u01(w.w[3]));
     }
 };
 template <> struct Math<float> {
@@ -269,15 +266,24 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
     // ---- pass loop (pass 0, then TRMC-RAD continuations) --------------------
     for (;;) {
         const int pass = sh.pass;
-        // 2. split (Alg. 4.2) and the per-pass arena
+        // 2. split (Alg. 4.2).  The per-level uniforms of the split and of the
+        //    odd-count coin are drawn in parallel; one thread then applies
+        //    Iround level by level.
+        {
+            const int lo = sh.lo, m = sh.m;
+            for (int t = tid; t <= m - lo; t += bs)
+                sh.uS[lo + t] = u01(rng.draw(uint64_t(lo + t), 0, uint32_t(pass), TAG_SPLIT).w[0]);
+            for (int t = tid; t < m; t += bs)
+                sh.uP[t + 1] = u01(rng.draw(uint64_t(t + 1), 0, uint32_t(pass), TAG_PARITY).w[0]);
+        }
+        __syncthreads();
         if (tid == 0) {
             for (int j = 0; j < NLEV; ++j) sh.Nq[j] = 0;
             int rem = sh.npart, m_eff = sh.m;
             for (int lv = sh.lo; lv <= sh.m; ++lv) {
                 const double x = sh.q * double(rem);
                 const double fl = floor(x);
-                const U64x4 w = rng.draw(uint64_t(lv), 0, uint32_t(pass), TAG_SPLIT);
-                const int c = int(fl) + ((u01(w.w[0]) < x - fl) ? 1 : 0);
+                const int c = int(fl) + ((sh.uS[lv] < x - fl) ? 1 : 0);
                 sh.Nq[lv] = c;
                 rem -= c;
                 if (rem == 0) { m_eff = lv; break; }
@@ -295,7 +301,8 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
         __syncthreads();
         if (sh.skip) break;
 
-        // 3. tree plan, top level first, with the leaf-feasibility loop
+        // 3. tree plan, top level first, with the leaf-feasibility loop.  Levels
+        //    with neither a quota nor a demand have no collision and are skipped.
         for (;;) {
             if (tid == 0) {
                 for (int j = 0; j < NLEV; ++j) {
@@ -306,12 +313,14 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
             }
             __syncthreads();
             const int m_top = sh.m_top;
-            for (int lv = m_top; lv >= 1; --lv) {
+            int lv = m_top;
+            while (lv >= 1 && sh.Nn[lv] + sh.D[lv] == 0) --lv;
+            while (lv >= 1) {
+                // Nn is read-only here: every thread reads it to skip empty levels
                 if (tid == 0) {
                     int T = sh.Nn[lv] + sh.D[lv];
                     if (T & 1) {
-                        const U64x4 w = rng.draw(uint64_t(lv), 0, uint32_t(pass), TAG_PARITY);
-                        if (sh.Nn[lv] >= 1 && u01(w.w[0]) < 0.5) { sh.Nn[lv] -= 1; T -= 1; sh.pdrop++; }
+                        if (sh.Nn[lv] >= 1 && sh.uP[lv] < 0.5) { T -= 1; sh.pdrop++; }
                         else { T += 1; sh.psurp++; }
                     }
                     sh.C[lv] = T >> 1;
@@ -327,12 +336,17 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
                         if (4 * g + j < Cn) atomicAdd(&row[below(w.w[j], uint32_t(lv))], 1);
                 }
                 __syncthreads();
-                if (tid == 0) {
-                    int32_t *srow = sh.St + tri(lv);
-                    for (int k = 0; k < lv; ++k) srow[k] = sh.D[k];
-                    for (int k = 0; k < lv; ++k) sh.D[k] += row[k] + row[lv - 1 - k];
-                    sh.out[lv] = 2 * sh.C[lv] - sh.D[lv];
+                // slot bases of this level's consumers, then the demand it adds
+                int32_t *srow = sh.St + tri(lv);
+                for (int k = tid; k < lv; k += bs) {
+                    const int d = sh.D[k];
+                    srow[k] = d;
+                    sh.D[k] = d + row[k] + row[lv - 1 - k];
                 }
+                if (tid == 0) sh.out[lv] = 2 * Cn - sh.D[lv];
+                __syncthreads();
+                --lv;
+                while (lv >= 1 && sh.Nn[lv] + sh.D[lv] == 0) --lv;
             }
             if (tid == 0) {
                 const int n0q = sh.Nq[0];
@@ -360,6 +374,12 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
             sh.OBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
                                                3 * size_t(sh.D0 + 1) * sizeof(Real)));
             if (!sh.IBuf || !sh.OBuf) sh.skip = 1;
+            // invariants of a consistent plan; a violation would index the
+            // buffers out of range, so the cell is left unchanged instead
+            bool ok = sh.n0 >= 0 && sh.D0 >= 0 && sh.R >= 0 && sh.n0 + sh.D0 + sh.R == sh.npart &&
+                      sh.O[m + 1] == sh.D0;
+            for (int lv = 1; lv <= m; ++lv) ok = ok && sh.out[lv] >= 0 && sh.C[lv] >= 0;
+            if (!ok) { sh.skip = 2; }
             if (pass == 0) sh.n0_first = sh.n0;
             if (a.report && pass == 0) {
                 int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
@@ -403,10 +423,21 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
         Real *OBx = sh.OBuf, *OBy = sh.OBuf + (D0 + 1), *OBz = sh.OBuf + 2 * (D0 + 1);
         const Real alpha = Real(sh.alpha), Sigma = Real(sh.Sigma);
         for (int lv = 1; lv <= m_eff; ++lv) {
-            if (tid == 0) {
+            if (sh.C[lv] == 0) continue;
+            if (tid < 32) {
+                // label prefix of the level (lv <= 64 entries, two per lane)
                 const int32_t *row = sh.Mt + tri(lv);
-                sh.Pn[0] = 0;
-                for (int k = 0; k < lv; ++k) sh.Pn[k + 1] = sh.Pn[k] + row[k];
+                int a0 = tid < lv ? row[tid] : 0, a1 = tid + 32 < lv ? row[tid + 32] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t0 = __shfl_up_sync(0xffffffffu, a0, o), t1 = __shfl_up_sync(0xffffffffu, a1, o);
+                    if (tid >= o) { a0 += t0; a1 += t1; }
+                }
+                a1 += __shfl_sync(0xffffffffu, a0, 31);
+                if (tid < lv) sh.Pn[tid + 1] = a0;
+                if (tid + 32 < lv) sh.Pn[tid + 33] = a1;
+                if (tid == 0) sh.Pn[0] = 0;
+            } else if (tid == 32) {
                 sh.keyK = rng.draw(0, uint64_t(lv), uint32_t(pass), TAG_PERMK);
             }
             __syncthreads();
@@ -543,7 +574,7 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
     }
     if (sh.skip) {
         if (tid == 0) {
-            raise_status(a.status, TRMC_ERR_CAPACITY, cell);
+            raise_status(a.status, sh.skip == 2 ? TRMC_ERR_STATE : TRMC_ERR_CAPACITY, cell);
             if (a.stats) atomicAdd(&a.stats->capacity_skips, 1ull);
         }
         return;
@@ -612,7 +643,7 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(kThreads) collide_kernel(Args a)
+__global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ Sh<Real> sh;
@@ -665,7 +696,11 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
                      int64_t *report, trmc_stats *stats, cudaStream_t s)
 {
     static int configured_smem = -1;
-    const int smem = int(ctx->smem_optin > 120 * 1024 ? 100 * 1024 : ctx->smem_optin / 2 - 8 * 1024);
+    // 128-thread CTAs, four per SM: while one cell is in a barrier-bound
+    // serial phase (split, plan), the SM runs the other cells' parallel work
+    const int threads = 128, per_sm_target = 4;
+    const int smem = int(ctx->smem_optin >= 200 * 1024 ? (220 * 1024) / per_sm_target - int(sizeof(Sh<Real>)) - 1024
+                                                        : ctx->smem_optin / 2 - int(sizeof(Sh<Real>)) - 1024);
     cudaError_t e;
     if (configured_smem != smem) {
         e = cudaFuncSetAttribute(collide_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -673,7 +708,7 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
         configured_smem = smem;
     }
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_kernel<Real>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_kernel<Real>, threads, smem);
     if (e != cudaSuccess) return cuda_error(ctx, e, "occupancy(collide)");
     if (per_sm < 1) per_sm = 1;
     int grid = ctx->num_sms * per_sm;
@@ -698,7 +733,7 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     a.slabs = ctx->slabs;
     a.slab_bytes = (ctx->slabs_bytes / size_t(grid)) & ~size_t(255);
     a.smem_bytes = smem;
-    collide_kernel<Real><<<grid, kThreads, smem, s>>>(a);
+    collide_kernel<Real><<<grid, threads, smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "collide launch");
     return TRMC_OK;
