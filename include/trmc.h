@@ -172,6 +172,33 @@ trmc_status trmc_transport(trmc_ctx *ctx, trmc_state *state, const trmc_domain *
  * (Sec. 2 and Sec. 5.1 definitions, per unit mass). */
 trmc_status trmc_moments(trmc_ctx *ctx, const trmc_state *state, double *out_dev, void *stream);
 
+/* ---- a collision step that allocates nothing -----------------------------
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory at the point where they advance the gas, such as an
+ * application running the step where cudaMalloc is forbidden or would
+ * synchronise the device, or a plug-in that is handed particle arrays but no
+ * allocator.  trmc_collide_static computes exactly what trmc_collide computes
+ * (same kernel, same draws), needs no trmc_ctx, and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Its scratch is one file-scope device
+ * array of TRMC_STATIC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits.
+ *  - max_cell_particles: the caller's bound on the largest cell.  The scratch
+ *    is split into one overflow slab per CTA sized for such a cell; if not
+ *    even one slab fits, the call returns TRMC_ERR_CAPACITY and launches
+ *    nothing.  A cell that still does not fit is left unchanged and reported.
+ *  - status_dev (optional, device int[2]): receives device-detected errors
+ *    (code, first cell), as trmc_check() would report them; the caller clears it.
+ *  - The first call on a device looks up the scratch's device address and
+ *    sets the kernel's shared-memory limit; make that first call before any
+ *    stream capture.
+ *  - All calls share the scratch: calls that overlap on the GPU (different
+ *    streams, or two host threads) race and must not be issued.
+ *  - Every call clears the scratch's status word and work counter first. */
+#define TRMC_STATIC_SCRATCH_BYTES (32u << 20)
+trmc_status trmc_collide_static(trmc_state *state, const trmc_collide_params *params, int32_t precision,
+                                uint64_t seed, uint64_t step, int32_t max_cell_particles,
+                                int *status_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

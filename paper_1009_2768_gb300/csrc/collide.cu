@@ -28,6 +28,7 @@
 // FP64 contexts compute everything in double and match the CPU oracle draw
 // for draw; FP32-mixed contexts store velocities and collide in float while
 // moments, Sigma, q and the renormalisation stay in double.
+#include <algorithm>
 #include <cfloat>
 
 #include "internal.h"
@@ -749,3 +750,120 @@ trmc_status launch_collide(trmc_ctx *ctx, trmc_state *st, const trmc_collide_par
 }
 
 }  // namespace trmc
+
+// ---- collision step without any allocation -----------------------------------
+// Some callers cannot allocate device memory when they run the collision step:
+// an application that advances the gas inside a section where cudaMalloc is
+// not allowed (it may synchronise the whole device, or the host's memory
+// manager owns every allocation), or a plug-in embedded in a program that
+// hands it particle arrays but no allocator.  trmc_collide_static serves them:
+// it needs no trmc_ctx, and its scratch (status word, work counter and the
+// per-CTA overflow slabs for cells larger than shared memory) is one
+// file-scope device array of TRMC_STATIC_SCRATCH_BYTES, which every GPU that
+// loads the library keeps until the process exits.
+namespace trmc {
+namespace {
+
+constexpr size_t kStaticControl = 4096;
+static __device__ __align__(256) unsigned char g_static_scratch[TRMC_STATIC_SCRATCH_BYTES];
+
+struct StaticDevice {
+    bool ready = false;
+    char *scratch = nullptr;   // device address of g_static_scratch on this device
+    int num_sms = 0;
+    int smem_optin = 0;
+};
+constexpr int kMaxDevices = 64;
+StaticDevice g_static_dev[kMaxDevices];
+
+// Working-set bound of one cell of n particles in the overflow slab: the
+// staged velocities, flags and role tables, the triangular plan tables at the
+// deepest level, and product buffers for up to 4n consumers and n outputs.
+size_t static_cell_bytes(int64_t n, size_t real)
+{
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const size_t N = size_t(n), T = size_t(TRMC_MCAP) * (TRMC_MCAP + 1) / 2 + 1;
+    return a16(3 * N * real) + a16(4 * ((N + 31) / 32)) + 2 * a16(4 * N) + 2 * a16(4 * T) +
+           a16(3 * (3 * N + 1) * real) + a16(3 * (N + 1) * real) + 256;
+}
+
+template <typename Real>
+trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64_t seed, uint64_t step,
+                          int32_t max_cell, int *status_dev, cudaStream_t s)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TRMC_ERR_CUDA;
+    StaticDevice &D = g_static_dev[dev];
+    const int threads = 128, per_sm_target = 4;
+    if (!D.ready) {
+        // once per device, with that device current: the device address of the
+        // scratch array (host code cannot use the array's name as a pointer)
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) return TRMC_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&D.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TRMC_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&D.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return TRMC_ERR_CUDA;
+        D.scratch = static_cast<char *>(p);
+        D.ready = true;
+    }
+    const int smem = D.smem_optin >= 200 * 1024 ? (220 * 1024) / per_sm_target - int(sizeof(Sh<Real>)) - 1024
+                                                : D.smem_optin / 2 - int(sizeof(Sh<Real>)) - 1024;
+    if (cudaFuncSetAttribute(collide_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return TRMC_ERR_CUDA;
+    const size_t avail = size_t(TRMC_STATIC_SCRATCH_BYTES) - kStaticControl;
+    const size_t need = static_cell_bytes(max_cell, sizeof(Real));
+    int grid = int(std::min<size_t>(avail / need, size_t(D.num_sms) * per_sm_target));
+    if (grid < 1) return TRMC_ERR_CAPACITY;       // a cell of max_cell particles cannot fit the scratch
+    if (grid > st->n_cells) grid = st->n_cells;
+    // the work counter must start at zero; the status word too
+    if (cudaMemsetAsync(D.scratch, 0, kStaticControl, s) != cudaSuccess) return TRMC_ERR_CUDA;
+    Args a;
+    a.vx = st->vx; a.vy = st->vy; a.vz = st->vz;
+    a.cell_start = st->cell_start;
+    a.n_cells = st->n_cells;
+    a.m_max = st->m_max;
+    a.cell_param = st->cell_param;
+    a.cell_key = st->cell_key;
+    a.cell_vmax2 = st->cell_vmax2;
+    a.problem_id = st->problem_id;
+    a.seed = seed;
+    a.step = step;
+    a.prm = *prm;
+    a.report = nullptr;
+    a.stats = nullptr;
+    a.status = status_dev ? status_dev : reinterpret_cast<int *>(D.scratch);
+    a.tickets = reinterpret_cast<unsigned int *>(D.scratch + 64);
+    a.slabs = D.scratch + kStaticControl;
+    a.slab_bytes = (avail / size_t(grid)) & ~size_t(255);
+    a.smem_bytes = smem;
+    collide_kernel<Real><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? TRMC_OK : TRMC_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace trmc
+
+extern "C" trmc_status trmc_collide_static(trmc_state *state, const trmc_collide_params *p, int32_t precision,
+                                           uint64_t seed, uint64_t step, int32_t max_cell_particles,
+                                           int *status_dev, void *stream)
+{
+    using namespace trmc;
+    if (!state || !p) return TRMC_ERR_ARG;
+    if (precision != TRMC_FP64 && precision != TRMC_FP32_MIXED) return TRMC_ERR_ARG;
+    if (state->n_cells < 0 || (state->n_cells > 0 && (!state->vx || !state->vy || !state->vz || !state->cell_start)))
+        return TRMC_ERR_ARG;
+    if (max_cell_particles < 0) return TRMC_ERR_ARG;
+    if (p->reserved != 0 || p->trunc < TRMC_TRUNC_FIXED || p->trunc > TRMC_TRUNC_UNLIMITED) return TRMC_ERR_ARG;
+    if (p->m_cap < 1 || p->m_cap > TRMC_MCAP) return TRMC_ERR_ARG;
+    if (p->trunc == TRMC_TRUNC_FIXED && (p->m_fixed < 1 || p->m_fixed > p->m_cap)) return TRMC_ERR_ARG;
+    if (p->trunc == TRMC_TRUNC_RAD && (!state->m_max || p->m_min < 1 || p->m_min > p->m_cap ||
+                                       !(p->delta1 >= 0.0) || !(p->delta2 >= p->delta1)))
+        return TRMC_ERR_ARG;
+    if (!state->cell_param && (!(p->eps > 0.0) || !(p->dt >= 0.0) || !(p->alpha >= 0.0 && p->alpha <= 1.0)))
+        return TRMC_ERR_ARG;
+    if (state->n_cells == 0) return TRMC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == TRMC_FP64) return launch_static<double>(state, p, seed, step, max_cell_particles, status_dev, s);
+    return launch_static<float>(state, p, seed, step, max_cell_particles, status_dev, s);
+}
+

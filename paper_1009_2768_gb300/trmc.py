@@ -25,7 +25,8 @@ REPORT_LEN = 16 + 3 * (MCAP + 2)
 REPORT_FIELDS = ["N", "passes", "m_first", "m_last", "m_next", "R_final", "N0", "leaves",
                  "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "reserved"]
 EXPORTS = ["trmc_create", "trmc_destroy", "trmc_last_error", "trmc_check", "trmc_init_cells",
-           "trmc_collide", "trmc_transport", "trmc_moments"]
+           "trmc_collide", "trmc_transport", "trmc_moments", "trmc_collide_static"]
+STATIC_SCRATCH_BYTES = 32 << 20
 
 
 class TrmcError(RuntimeError):
@@ -83,6 +84,8 @@ def load():
         lib.trmc_collide.argtypes = [P, C.POINTER(State), C.POINTER(CollideParams), C.c_uint64, P, P, P]
         lib.trmc_transport.argtypes = [P, C.POINTER(State), P, C.c_int32, C.c_double, P, P]
         lib.trmc_moments.argtypes = [P, C.POINTER(State), P, P]
+        lib.trmc_collide_static.argtypes = [C.POINTER(State), C.POINTER(CollideParams), C.c_int32, C.c_uint64,
+                                            C.c_uint64, C.c_int32, P, P]
         for f in EXPORTS:
             if f != "trmc_last_error":
                 getattr(lib, f).restype = C.c_int
@@ -140,6 +143,18 @@ def trmc_transport(ctx, state, domains, n_domains, cfl, dt, stream=None):
 
 def trmc_moments(ctx, state, out, stream=None):
     _raise(ctx, load().trmc_moments(ctx, C.byref(state.c), _ptr(out), _stream(stream)))
+
+
+def trmc_collide_static(state, params, precision, seed, step, max_cell_particles, status=None, stream=None):
+    """Collision step that allocates nothing (no context; scratch is a fixed
+    device array inside the library).  status: optional int32 device tensor
+    of 2 that receives device-detected errors (code, first cell)."""
+    code = load().trmc_collide_static(C.byref(state.c), C.byref(params), precision, seed, step,
+                                      max_cell_particles, _ptr(status), _stream(stream))
+    if code != OK:
+        why = {ERR_ARG: "invalid argument", ERR_CAPACITY: "a cell of max_cell_particles does not fit the static "
+               f"scratch of {STATIC_SCRATCH_BYTES >> 20} MiB", ERR_CUDA: "CUDA call failed"}.get(code, "error")
+        raise TrmcError(code, f"trmc_collide_static: {why}")
 
 
 # ---------------------------------------------------------------- helpers
