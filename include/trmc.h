@@ -139,6 +139,12 @@ const char *trmc_last_error(const trmc_ctx *ctx);
 /* Synchronise the stream, then return and clear the device status word. */
 trmc_status trmc_check(trmc_ctx *ctx, void *stream);
 
+/* Launch shape of the collision kernel: CTA size (a multiple of 32 in
+ * [32, 256]) and the number of CTAs resident per SM the shared-memory budget
+ * is split for (1..16).  Defaults 128 and 4.  Results do not depend on it;
+ * only speed does (the autotuner in the binding sweeps it). */
+trmc_status trmc_set_collide_launch(trmc_ctx *ctx, int32_t threads, int32_t ctas_per_sm);
+
 /* Sample initial velocities (and positions, if state->x != NULL) for every
  * particle of every cell, from the synthetic closed-form laws listed in
  * trmc_init_kind.  cell_init_dev: [n_cells][TRMC_INIT_COLS] doubles on the

@@ -108,6 +108,17 @@ trmc_status trmc_check(trmc_ctx *ctx, void *stream)
     return set_error(ctx, static_cast<trmc_status>(st[0]), buf);
 }
 
+trmc_status trmc_set_collide_launch(trmc_ctx *ctx, int32_t threads, int32_t ctas_per_sm)
+{
+    if (!ctx) return TRMC_ERR_ARG;
+    if (threads < 32 || threads > kThreads || threads % 32 != 0)
+        return set_error(ctx, TRMC_ERR_ARG, "threads must be a multiple of 32 in [32, 256]");
+    if (ctas_per_sm < 1 || ctas_per_sm > 16) return set_error(ctx, TRMC_ERR_ARG, "ctas_per_sm outside [1, 16]");
+    ctx->collide_threads = threads;
+    ctx->collide_ctas_per_sm = ctas_per_sm;
+    return TRMC_OK;
+}
+
 trmc_status trmc_init_cells(trmc_ctx *ctx, trmc_state *state, const double *cell_init_dev, void *stream)
 {
     if (!ctx) return TRMC_ERR_ARG;

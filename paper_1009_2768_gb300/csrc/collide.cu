@@ -38,6 +38,7 @@ namespace trmc {
 namespace {
 
 constexpr int NLEV = kMC + 2;
+constexpr int kWarpLevel = 64;     // levels with at most this many collisions run in one warp
 
 struct Args {
     void *vx, *vy, *vz;
@@ -64,6 +65,7 @@ struct Sh {
     int32_t Nq[NLEV], Nn[NLEV], D[NLEV], C[NLEV], out[NLEV], O[NLEV], IB[NLEV];
     int32_t Pn[kMC + 1];
     double uS[NLEV], uP[NLEV];
+    U64x4 keys[NLEV];
     double red[32 * 8];
     int32_t cell, n, m, lo, m_eff, pass, n0, D0, R, npart, m_next, Dge1;
     int32_t n0_prev, D0_prev;
@@ -266,233 +268,266 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
 
     // ---- pass loop (pass 0, then TRMC-RAD continuations) --------------------
     for (;;) {
-        const int pass = sh.pass;
-        // 2. split (Alg. 4.2).  The per-level uniforms of the split and of the
-        //    odd-count coin are drawn in parallel; one thread then applies
-        //    Iround level by level.
-        {
-            const int lo = sh.lo, m = sh.m;
-            for (int t = tid; t <= m - lo; t += bs)
-                sh.uS[lo + t] = u01(rng.draw(uint64_t(lo + t), 0, uint32_t(pass), TAG_SPLIT).w[0]);
-            for (int t = tid; t < m; t += bs)
-                sh.uP[t + 1] = u01(rng.draw(uint64_t(t + 1), 0, uint32_t(pass), TAG_PARITY).w[0]);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int j = 0; j < NLEV; ++j) sh.Nq[j] = 0;
-            int rem = sh.npart, m_eff = sh.m;
-            for (int lv = sh.lo; lv <= sh.m; ++lv) {
-                const double x = sh.q * double(rem);
-                const double fl = floor(x);
-                const int c = int(fl) + ((sh.uS[lv] < x - fl) ? 1 : 0);
-                sh.Nq[lv] = c;
-                rem -= c;
-                if (rem == 0) { m_eff = lv; break; }
-            }
-            if (rem > 0) sh.Nq[sh.m + 1] = rem;
-            sh.m_eff = m_eff;
-            sh.m_top = m_eff;
-            sh.pass_smem = sh.smem_rest; sh.pass_smem_cap = sh.smem_rest_cap;
-            sh.pass_slab = sh.slab_rest; sh.pass_slab_cap = sh.slab_rest_cap;
-            const size_t T = size_t(tri(m_eff + 1));
-            sh.Mt = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
-            sh.St = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
-            if (!sh.Mt || !sh.St) sh.skip = 1;
-        }
-        __syncthreads();
-        if (sh.skip) break;
+        const int pass = sh.pass, warp = tid >> 5, npart = sh.npart;
+        int32_t *inv = sh.inv[pass & 1];
+        const int32_t *invp = sh.inv[(pass + 1) & 1];
+        int32_t *fwd = sh.inv[1];                       // pass 0: pi(i) of every slot, for the change flags
+        const int poolp = sh.n0_prev + sh.D0_prev;
 
-        // 3. tree plan, top level first, with the leaf-feasibility loop.  Levels
-        //    with neither a quota nor a demand have no collision and are skipped.
-        for (;;) {
-            if (tid == 0) {
-                for (int j = 0; j < NLEV; ++j) {
+        // 2-3. Warp 0 draws the split (Alg. 4.2) and builds the tree plan with
+        //      warp-level synchronisation only; warps 1.. meanwhile compute the
+        //      role permutation of the participants, which the plan does not
+        //      change (only where its ranks are cut into roles).
+        if (warp == 0) {
+            {
+                const int lo = sh.lo, m = sh.m;
+                for (int t = lane; t <= m - lo; t += 32)
+                    sh.uS[lo + t] = u01(rng.draw(uint64_t(lo + t), 0, uint32_t(pass), TAG_SPLIT).w[0]);
+                for (int t = lane; t < m; t += 32) {
+                    sh.uP[t + 1] = u01(rng.draw(uint64_t(t + 1), 0, uint32_t(pass), TAG_PARITY).w[0]);
+                    sh.keys[t + 1] = rng.draw(0, uint64_t(t + 1), uint32_t(pass), TAG_PERMK);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                for (int j = 0; j < NLEV; ++j) sh.Nq[j] = 0;
+                int rem = npart, m_eff = sh.m;
+                for (int lv = sh.lo; lv <= sh.m; ++lv) {
+                    const double x = sh.q * double(rem);
+                    const double fl = floor(x);
+                    const int c = int(fl) + ((sh.uS[lv] < x - fl) ? 1 : 0);
+                    sh.Nq[lv] = c;
+                    rem -= c;
+                    if (rem == 0) { m_eff = lv; break; }
+                }
+                if (rem > 0) sh.Nq[sh.m + 1] = rem;
+                sh.m_eff = m_eff;
+                sh.m_top = m_eff;
+                sh.pass_smem = sh.smem_rest; sh.pass_smem_cap = sh.smem_rest_cap;
+                sh.pass_slab = sh.slab_rest; sh.pass_slab_cap = sh.slab_rest_cap;
+                const size_t T = size_t(tri(m_eff + 1));
+                sh.Mt = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
+                sh.St = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
+                if (!sh.Mt || !sh.St) sh.skip = 1;
+            }
+            __syncwarp();
+            // Tree plan, top level first, with the leaf-feasibility loop.  Levels
+            // with neither quota nor demand have no collision and are skipped;
+            // Nn is read-only below because every lane reads it to skip.
+            while (!sh.skip) {
+                for (int j = lane; j < NLEV; j += 32) {
                     sh.D[j] = 0; sh.C[j] = 0; sh.out[j] = 0;
                     sh.Nn[j] = (j <= sh.m_top) ? sh.Nq[j] : 0;
                 }
-                sh.pdrop = 0; sh.psurp = 0;
-            }
-            __syncthreads();
-            const int m_top = sh.m_top;
-            int lv = m_top;
-            while (lv >= 1 && sh.Nn[lv] + sh.D[lv] == 0) --lv;
-            while (lv >= 1) {
-                // Nn is read-only here: every thread reads it to skip empty levels
-                if (tid == 0) {
-                    int T = sh.Nn[lv] + sh.D[lv];
-                    if (T & 1) {
-                        if (sh.Nn[lv] >= 1 && sh.uP[lv] < 0.5) { T -= 1; sh.pdrop++; }
-                        else { T += 1; sh.psurp++; }
-                    }
-                    sh.C[lv] = T >> 1;
-                }
-                int32_t *row = sh.Mt + tri(lv);
-                for (int k = tid; k < lv; k += bs) row[k] = 0;
-                __syncthreads();
-                const int Cn = sh.C[lv];
-                for (int g = tid; g < (Cn + 3) >> 2; g += bs) {
-                    const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (4 * g + j < Cn) atomicAdd(&row[below(w.w[j], uint32_t(lv))], 1);
-                }
-                __syncthreads();
-                // slot bases of this level's consumers, then the demand it adds
-                int32_t *srow = sh.St + tri(lv);
-                for (int k = tid; k < lv; k += bs) {
-                    const int d = sh.D[k];
-                    srow[k] = d;
-                    sh.D[k] = d + row[k] + row[lv - 1 - k];
-                }
-                if (tid == 0) sh.out[lv] = 2 * Cn - sh.D[lv];
-                __syncthreads();
-                --lv;
+                if (lane == 0) { sh.pdrop = 0; sh.psurp = 0; }
+                __syncwarp();
+                const int m_top = sh.m_top;
+                int lv = m_top;
                 while (lv >= 1 && sh.Nn[lv] + sh.D[lv] == 0) --lv;
-            }
-            if (tid == 0) {
-                const int n0q = sh.Nq[0];
-                const int A = sh.npart - n0q;
-                sh.cont = 0;
-                if (sh.D[0] <= A) { sh.n0 = n0q; sh.D0 = sh.D[0]; sh.R = A - sh.D[0]; }
-                else if (sh.D[0] - A <= n0q) { sh.n0 = n0q - (sh.D[0] - A); sh.D0 = sh.D[0]; sh.R = 0; }
-                else { sh.feas++; sh.m_top = m_top - 1; sh.cont = 1; }
-            }
-            __syncthreads();
-            if (!sh.cont) break;
-        }
-
-        // layout of the product buffers; output / input offsets
-        if (tid == 0) {
-            const int m = sh.m_top;
-            sh.pdrop_tot += sh.pdrop;
-            sh.psurp_tot += sh.psurp;
-            sh.m_eff = m;
-            sh.O[1] = 0; sh.IB[1] = 0;
-            for (int lv = 1; lv <= m; ++lv) { sh.O[lv + 1] = sh.O[lv] + sh.out[lv]; sh.IB[lv + 1] = sh.IB[lv] + sh.D[lv]; }
-            sh.Dge1 = sh.IB[m + 1];
-            sh.IBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
-                                               3 * size_t(sh.Dge1 + 1) * sizeof(Real)));
-            sh.OBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
-                                               3 * size_t(sh.D0 + 1) * sizeof(Real)));
-            if (!sh.IBuf || !sh.OBuf) sh.skip = 1;
-            // invariants of a consistent plan; a violation would index the
-            // buffers out of range, so the cell is left unchanged instead
-            bool ok = sh.n0 >= 0 && sh.D0 >= 0 && sh.R >= 0 && sh.n0 + sh.D0 + sh.R == sh.npart &&
-                      sh.O[m + 1] == sh.D0;
-            for (int lv = 1; lv <= m; ++lv) ok = ok && sh.out[lv] >= 0 && sh.C[lv] >= 0;
-            if (!ok) { sh.skip = 2; }
-            if (pass == 0) sh.n0_first = sh.n0;
-            if (a.report && pass == 0) {
-                int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
-                r[6] = sh.n0;
-                r[14] = m;
-                for (int j = 0; j < NLEV; ++j) {
-                    r[16 + j] = sh.Nq[j];
-                    r[16 + NLEV + j] = sh.C[j];
-                    r[16 + 2 * NLEV + j] = sh.D[j];
+                while (lv >= 1) {
+                    if (lane == 0) {
+                        int T = sh.Nn[lv] + sh.D[lv];
+                        if (T & 1) {
+                            if (sh.Nn[lv] >= 1 && sh.uP[lv] < 0.5) { T -= 1; sh.pdrop++; }
+                            else { T += 1; sh.psurp++; }
+                        }
+                        sh.C[lv] = T >> 1;
+                    }
+                    int32_t *row = sh.Mt + tri(lv);
+                    for (int k = lane; k < lv; k += 32) row[k] = 0;
+                    __syncwarp();
+                    const int Cn = sh.C[lv];
+                    for (int g = lane; g < (Cn + 3) >> 2; g += 32) {
+                        const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (4 * g + j < Cn) atomicAdd(&row[below(w.w[j], uint32_t(lv))], 1);
+                    }
+                    __syncwarp();
+                    // slot bases of this level's consumers, then the demand it adds
+                    int32_t *srow = sh.St + tri(lv);
+                    for (int k = lane; k < lv; k += 32) {
+                        const int d = sh.D[k];
+                        srow[k] = d;
+                        sh.D[k] = d + row[k] + row[lv - 1 - k];
+                    }
+                    if (lane == 0) sh.out[lv] = 2 * Cn - sh.D[lv];
+                    __syncwarp();
+                    --lv;
+                    while (lv >= 1 && sh.Nn[lv] + sh.D[lv] == 0) --lv;
                 }
+                if (lane == 0) {
+                    const int n0q = sh.Nq[0];
+                    const int A = npart - n0q;
+                    sh.cont = 0;
+                    if (sh.D[0] <= A) { sh.n0 = n0q; sh.D0 = sh.D[0]; sh.R = A - sh.D[0]; }
+                    else if (sh.D[0] - A <= n0q) { sh.n0 = n0q - (sh.D[0] - A); sh.D0 = sh.D[0]; sh.R = 0; }
+                    else {
+                        // Lowering the depth by one level at a time (the rule) gives the
+                        // same plan again while the removed top level is empty, so go
+                        // straight below the highest level with a quota; the number of
+                        // one-level reductions is still counted.
+                        int h = m_top;
+                        while (h >= 1 && sh.Nq[h] == 0) --h;
+                        const int nt = (h >= 1 ? h : 1) - 1;
+                        sh.feas += m_top - nt;
+                        sh.m_top = nt;
+                        sh.cont = 1;
+                    }
+                }
+                __syncwarp();
+                if (!sh.cont) break;
+            }
+            // layout of the product buffers; output / input offsets
+            if (lane == 0 && !sh.skip) {
+                const int m = sh.m_top;
+                sh.pdrop_tot += sh.pdrop;
+                sh.psurp_tot += sh.psurp;
+                sh.m_eff = m;
+                sh.O[1] = 0; sh.IB[1] = 0;
+                for (int lv = 1; lv <= m; ++lv) { sh.O[lv + 1] = sh.O[lv] + sh.out[lv]; sh.IB[lv + 1] = sh.IB[lv] + sh.D[lv]; }
+                sh.Dge1 = sh.IB[m + 1];
+                sh.IBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                                                   3 * size_t(sh.Dge1 + 1) * sizeof(Real)));
+                sh.OBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                                                   3 * size_t(sh.D0 + 1) * sizeof(Real)));
+                if (!sh.IBuf || !sh.OBuf) sh.skip = 1;
+                // invariants of a consistent plan; a violation would index the
+                // buffers out of range, so the cell is left unchanged instead
+                bool ok = sh.n0 >= 0 && sh.D0 >= 0 && sh.R >= 0 && sh.n0 + sh.D0 + sh.R == npart &&
+                          sh.O[m + 1] == sh.D0;
+                for (int lv = 1; lv <= m; ++lv) ok = ok && sh.out[lv] >= 0 && sh.C[lv] >= 0;
+                if (!ok) { sh.skip = 2; }
+                if (pass == 0) sh.n0_first = sh.n0;
+                if (a.report && pass == 0) {
+                    int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
+                    r[6] = sh.n0;
+                    r[14] = m;
+                    for (int j = 0; j < NLEV; ++j) {
+                        r[16 + j] = sh.Nq[j];
+                        r[16 + NLEV + j] = sh.C[j];
+                        r[16 + 2 * NLEV + j] = sh.D[j];
+                    }
+                }
+            }
+        }
+        // 4. roles: a permutation of the participants (warps 1.., or warp 0
+        //    afterwards when the CTA is a single warp)
+        if (warp > 0 || bs == 32) {
+            Perm perm;
+            perm.init(uint32_t(npart), rng.draw(0, 0, uint32_t(pass), TAG_PERM0));
+            const int t0 = bs == 32 ? tid : tid - 32, st = bs == 32 ? bs : bs - 32;
+            for (int i = t0; i < npart; i += st) {
+                const int r = int(perm.fwd(uint32_t(i)));
+                inv[r] = (pass == 0) ? i : invp[poolp + i];
+                if (pass == 0) fwd[i] = r;
             }
         }
         __syncthreads();
         if (sh.skip) break;
-        const int m_eff = sh.m_eff, n0 = sh.n0, D0 = sh.D0, npart = sh.npart, Dge1 = sh.Dge1;
-        int32_t *inv = sh.inv[pass & 1];
-        const int32_t *invp = sh.inv[(pass + 1) & 1];
-        const int poolp = sh.n0_prev + sh.D0_prev;
-
-        // 4. roles: permutation of the participants
-        {
-            Perm perm;
-            perm.init(uint32_t(npart), rng.draw(0, 0, uint32_t(pass), TAG_PERM0));
+        const int m_eff = sh.m_eff, n0 = sh.n0, D0 = sh.D0, Dge1 = sh.Dge1;
+        if (pass == 0) {
+            // which slots change: every rank from n0 on (leaves and thermalised)
             for (int b0 = tid - lane; b0 < npart; b0 += bs) {
                 const int i = b0 + lane;
-                bool changed = false;
-                if (i < npart) {
-                    const int r = int(perm.fwd(uint32_t(i)));
-                    inv[r] = (pass == 0) ? i : invp[poolp + i];
-                    changed = r >= n0;
-                }
-                if (pass == 0) {
-                    const unsigned msk = __ballot_sync(0xffffffffu, changed);
-                    if (lane == 0) sh.flags[b0 >> 5] = msk;
-                }
+                const unsigned msk = __ballot_sync(0xffffffffu, i < npart && fwd[i] >= n0);
+                if (lane == 0) sh.flags[b0 >> 5] = msk;
             }
         }
-        __syncthreads();
-        // 5. collision waves, level 1 first
+
+        // 5. collision waves, level 1 first.  Levels of at most kWarpLevel
+        //    collisions (the deep ones) run in warp 0 alone, with warp-level
+        //    synchronisation; a CTA barrier is needed only where a larger
+        //    level follows them.
         Real *IBx = sh.IBuf, *IBy = sh.IBuf + (Dge1 + 1), *IBz = sh.IBuf + 2 * (Dge1 + 1);
         Real *OBx = sh.OBuf, *OBy = sh.OBuf + (D0 + 1), *OBz = sh.OBuf + 2 * (D0 + 1);
         const Real alpha = Real(sh.alpha), Sigma = Real(sh.Sigma);
-        for (int lv = 1; lv <= m_eff; ++lv) {
-            if (sh.C[lv] == 0) continue;
-            if (tid < 32) {
-                // label prefix of the level (lv <= 64 entries, two per lane)
-                const int32_t *row = sh.Mt + tri(lv);
-                int a0 = tid < lv ? row[tid] : 0, a1 = tid + 32 < lv ? row[tid + 32] : 0;
+        auto level_setup = [&](int lv) {          // warp 0: label prefix and product key
+            const int32_t *row = sh.Mt + tri(lv);
+            int a0 = lane < lv ? row[lane] : 0, a1 = lane + 32 < lv ? row[lane + 32] : 0;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t0 = __shfl_up_sync(0xffffffffu, a0, o), t1 = __shfl_up_sync(0xffffffffu, a1, o);
-                    if (tid >= o) { a0 += t0; a1 += t1; }
-                }
-                a1 += __shfl_sync(0xffffffffu, a0, 31);
-                if (tid < lv) sh.Pn[tid + 1] = a0;
-                if (tid + 32 < lv) sh.Pn[tid + 33] = a1;
-                if (tid == 0) sh.Pn[0] = 0;
-            } else if (tid == 32) {
-                sh.keyK = rng.draw(0, uint64_t(lv), uint32_t(pass), TAG_PERMK);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t0 = __shfl_up_sync(0xffffffffu, a0, o), t1 = __shfl_up_sync(0xffffffffu, a1, o);
+                if (lane >= o) { a0 += t0; a1 += t1; }
             }
-            __syncthreads();
-            const int Cn = sh.C[lv], Dn = sh.D[lv], On = sh.O[lv], IBn = sh.IB[lv];
+            a1 += __shfl_sync(0xffffffffu, a0, 31);
+            if (lane < lv) sh.Pn[lane + 1] = a0;
+            if (lane + 32 < lv) sh.Pn[lane + 33] = a1;
+            if (lane == 0) sh.Pn[0] = 0;
+        };
+        auto collide_one = [&](int lv, int c, const Perm &pk) {
+            // the draw and the product slots do not depend on the inputs:
+            // issue them first so their latency overlaps the loads
+            const U64x4 w = rng.draw(uint64_t(c), uint64_t(lv), uint32_t(pass), TAG_COLL);
+            const int t0 = int(pk.fwd(uint32_t(2 * c))), t1 = int(pk.fwd(uint32_t(2 * c + 1)));
+            const int Dn = sh.D[lv], On = sh.O[lv], IBn = sh.IB[lv];
             const int32_t *row = sh.Mt + tri(lv), *srow = sh.St + tri(lv);
-            Perm pk;
-            pk.init(uint32_t(2 * Cn), sh.keyK);
-            for (int c = tid; c < Cn; c += bs) {
-                // label of collision c: Pn[k] <= c < Pn[k+1]
-                int lo_ = 0, hi_ = lv - 1;
-                while (lo_ < hi_) {
-                    const int mid = (lo_ + hi_ + 1) >> 1;
-                    if (sh.Pn[mid] <= c) lo_ = mid; else hi_ = mid - 1;
-                }
-                const int k = lo_, j = lv - 1 - k, off = c - sh.Pn[k];
-                const int s0 = srow[k] + off, s1 = srow[j] + row[j] + off;
-                Real ax, ay, az, bx, by, bz;
-                if (k == 0) { const int sl = inv[n0 + s0]; ax = Vx[sl]; ay = Vy[sl]; az = Vz[sl]; }
-                else { const int q = sh.IB[k] + s0; ax = IBx[q]; ay = IBy[q]; az = IBz[q]; }
-                if (j == 0) { const int sl = inv[n0 + s1]; bx = Vx[sl]; by = Vy[sl]; bz = Vz[sl]; }
-                else { const int q = sh.IB[j] + s1; bx = IBx[q]; by = IBy[q]; bz = IBz[q]; }
-                const U64x4 w = rng.draw(uint64_t(c), uint64_t(lv), uint32_t(pass), TAG_COLL);
-                const Real dx = ax - bx, dy = ay - by, dz = az - bz;
-                const Real g = Math<Real>::sqrt_(dx * dx + dy * dy + dz * dz);
-                bool acc = true;
-                if (alpha != Real(0)) {
-                    const Real ga = (alpha == Real(1)) ? g : Math<Real>::pow_(g, alpha);
-                    if (ga > Sigma) cnt[2] += 1.0;
-                    const Real xi = Math<Real>::uni(w.w[0]);
-                    acc = xi * Sigma < ga;
-                }
-                Real oax = ax, oay = ay, oaz = az, obx = bx, oby = by, obz = bz;
-                if (acc) {
-                    const Real ct = Real(2) * Math<Real>::uni(w.w[1]) - Real(1);
-                    const Real st = Math<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
-                    Real sp, cp;
-                    Math<Real>::angle(Math<Real>::uni(w.w[2]), sp, cp);
-                    const Real sx = cp * st, sy = sp * st, sz = ct;
-                    const Real h = Real(0.5) * g;
-                    const Real cx = Real(0.5) * (ax + bx), cy = Real(0.5) * (ay + by), cz = Real(0.5) * (az + bz);
-                    oax = cx + h * sx; oay = cy + h * sy; oaz = cz + h * sz;
-                    obx = cx - h * sx; oby = cy - h * sy; obz = cz - h * sz;
-                    cnt[0] += 1.0;
-                } else {
-                    cnt[1] += 1.0;
-                }
-                const int t0 = int(pk.fwd(uint32_t(2 * c))), t1 = int(pk.fwd(uint32_t(2 * c + 1)));
-                if (t0 < Dn) { const int q = IBn + t0; IBx[q] = oax; IBy[q] = oay; IBz[q] = oaz; }
-                else { const int q = On + t0 - Dn; OBx[q] = oax; OBy[q] = oay; OBz[q] = oaz; }
-                if (t1 < Dn) { const int q = IBn + t1; IBx[q] = obx; IBy[q] = oby; IBz[q] = obz; }
-                else { const int q = On + t1 - Dn; OBx[q] = obx; OBy[q] = oby; OBz[q] = obz; }
+            // label of collision c: Pn[k] <= c < Pn[k+1]
+            int lo_ = 0, hi_ = lv - 1;
+            while (lo_ < hi_) {
+                const int mid = (lo_ + hi_ + 1) >> 1;
+                if (sh.Pn[mid] <= c) lo_ = mid; else hi_ = mid - 1;
             }
-            __syncthreads();
+            const int k = lo_, j = lv - 1 - k, off = c - sh.Pn[k];
+            const int s0 = srow[k] + off, s1 = srow[j] + row[j] + off;
+            Real ax, ay, az, bx, by, bz;
+            if (k == 0) { const int sl = inv[n0 + s0]; ax = Vx[sl]; ay = Vy[sl]; az = Vz[sl]; }
+            else { const int q = sh.IB[k] + s0; ax = IBx[q]; ay = IBy[q]; az = IBz[q]; }
+            if (j == 0) { const int sl = inv[n0 + s1]; bx = Vx[sl]; by = Vy[sl]; bz = Vz[sl]; }
+            else { const int q = sh.IB[j] + s1; bx = IBx[q]; by = IBy[q]; bz = IBz[q]; }
+            const Real dx = ax - bx, dy = ay - by, dz = az - bz;
+            const Real g = Math<Real>::sqrt_(dx * dx + dy * dy + dz * dz);
+            bool acc = true;
+            if (alpha != Real(0)) {
+                const Real ga = (alpha == Real(1)) ? g : Math<Real>::pow_(g, alpha);
+                if (ga > Sigma) cnt[2] += 1.0;
+                const Real xi = Math<Real>::uni(w.w[0]);
+                acc = xi * Sigma < ga;
+            }
+            Real oax = ax, oay = ay, oaz = az, obx = bx, oby = by, obz = bz;
+            if (acc) {
+                const Real ct = Real(2) * Math<Real>::uni(w.w[1]) - Real(1);
+                const Real st = Math<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
+                Real sp, cp;
+                Math<Real>::angle(Math<Real>::uni(w.w[2]), sp, cp);
+                const Real sx = cp * st, sy = sp * st, sz = ct;
+                const Real h = Real(0.5) * g;
+                const Real cx = Real(0.5) * (ax + bx), cy = Real(0.5) * (ay + by), cz = Real(0.5) * (az + bz);
+                oax = cx + h * sx; oay = cy + h * sy; oaz = cz + h * sz;
+                obx = cx - h * sx; oby = cy - h * sy; obz = cz - h * sz;
+                cnt[0] += 1.0;
+            } else {
+                cnt[1] += 1.0;
+            }
+            if (t0 < Dn) { const int q = IBn + t0; IBx[q] = oax; IBy[q] = oay; IBz[q] = oaz; }
+            else { const int q = On + t0 - Dn; OBx[q] = oax; OBy[q] = oay; OBz[q] = oaz; }
+            if (t1 < Dn) { const int q = IBn + t1; IBx[q] = obx; IBy[q] = oby; IBz[q] = obz; }
+            else { const int q = On + t1 - Dn; OBx[q] = obx; OBy[q] = oby; OBz[q] = obz; }
+        };
+        bool warp_only = false;      // the last level ran in warp 0 alone
+        for (int lv = 1; lv <= m_eff; ++lv) {
+            const int Cn = sh.C[lv];
+            if (Cn == 0) continue;
+            if (Cn <= kWarpLevel) {
+                warp_only = true;
+                if (warp != 0) continue;
+                level_setup(lv);
+                __syncwarp();
+                Perm pk;
+                pk.init(uint32_t(2 * Cn), sh.keys[lv]);
+                for (int c = lane; c < Cn; c += 32) collide_one(lv, c, pk);
+                __syncwarp();
+            } else {
+                if (warp_only) { __syncthreads(); warp_only = false; }
+                if (warp == 0) level_setup(lv);
+                __syncthreads();
+                Perm pk;
+                pk.init(uint32_t(2 * Cn), sh.keys[lv]);
+                for (int c = tid; c < Cn; c += bs) collide_one(lv, c, pk);
+                __syncthreads();
+            }
         }
+        __syncthreads();
 
         // 6. outputs replace the leaves.  What the collisions changed (sum of
         //    output - original over the leaves) and the thermalised set's own
@@ -697,11 +732,13 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
                      int64_t *report, trmc_stats *stats, cudaStream_t s)
 {
     static int configured_smem = -1;
-    // 128-thread CTAs, four per SM: while one cell is in a barrier-bound
-    // serial phase (split, plan), the SM runs the other cells' parallel work
-    const int threads = 128, per_sm_target = 4;
-    const int smem = int(ctx->smem_optin >= 200 * 1024 ? (220 * 1024) / per_sm_target - int(sizeof(Sh<Real>)) - 1024
-                                                        : ctx->smem_optin / 2 - int(sizeof(Sh<Real>)) - 1024);
+    // CTA size and CTAs per SM from the context (default 128 x 4): several
+    // cells per SM overlap one cell's serial phases with the others' work;
+    // the shared-memory budget of an SM is split evenly between them
+    const int threads = ctx->collide_threads, per_sm_target = ctx->collide_ctas_per_sm;
+    const int budget = ctx->smem_optin >= 200 * 1024 ? 220 * 1024 : int(ctx->smem_optin);
+    int smem = budget / per_sm_target - int(sizeof(Sh<Real>)) - 1024;
+    if (smem > int(ctx->smem_optin) - int(sizeof(Sh<Real>))) smem = int(ctx->smem_optin) - int(sizeof(Sh<Real>));
     cudaError_t e;
     if (configured_smem != smem) {
         e = cudaFuncSetAttribute(collide_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

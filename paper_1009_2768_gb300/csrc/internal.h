@@ -24,6 +24,9 @@ struct trmc_ctx {
     int64_t *tr_counts = nullptr;     // [3 * cells] moves -1/0/+1 per old cell
     int64_t *tr_scan = nullptr;       // [cells + 1]
     int tr_cells = 0;
+    // collide launch shape (trmc_set_collide_launch)
+    int collide_threads = 128;
+    int collide_ctas_per_sm = 4;
     std::string last_error;
 };
 

@@ -25,7 +25,7 @@ REPORT_LEN = 16 + 3 * (MCAP + 2)
 REPORT_FIELDS = ["N", "passes", "m_first", "m_last", "m_next", "R_final", "N0", "leaves",
                  "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "reserved"]
 EXPORTS = ["trmc_create", "trmc_destroy", "trmc_last_error", "trmc_check", "trmc_init_cells",
-           "trmc_collide", "trmc_transport", "trmc_moments", "trmc_collide_static"]
+           "trmc_collide", "trmc_transport", "trmc_moments", "trmc_collide_static", "trmc_set_collide_launch"]
 STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -84,6 +84,7 @@ def load():
         lib.trmc_collide.argtypes = [P, C.POINTER(State), C.POINTER(CollideParams), C.c_uint64, P, P, P]
         lib.trmc_transport.argtypes = [P, C.POINTER(State), P, C.c_int32, C.c_double, P, P]
         lib.trmc_moments.argtypes = [P, C.POINTER(State), P, P]
+        lib.trmc_set_collide_launch.argtypes = [P, C.c_int32, C.c_int32]
         lib.trmc_collide_static.argtypes = [C.POINTER(State), C.POINTER(CollideParams), C.c_int32, C.c_uint64,
                                             C.c_uint64, C.c_int32, P, P]
         for f in EXPORTS:
@@ -124,6 +125,10 @@ def trmc_destroy(ctx):
 
 def trmc_check(ctx, stream=None):
     _raise(ctx, load().trmc_check(ctx, _stream(stream)))
+
+
+def trmc_set_collide_launch(ctx, threads, ctas_per_sm):
+    _raise(ctx, load().trmc_set_collide_launch(ctx, threads, ctas_per_sm))
 
 
 def trmc_init_cells(ctx, state, cell_init, stream=None):

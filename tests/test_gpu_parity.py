@@ -282,3 +282,15 @@ def test_shock_tube_chain_parity():
         assert_velocity_parity(st.v[:, :n].cpu().numpy(), vo, cso, tol=1e-11)
         assert np.array_equal(st.m_max.cpu().numpy(), mo)
     T.trmc_destroy(c)
+
+
+def test_collide_parity_deep_continuation_with_tiny_pool():
+    """Deep trees (tau ~ 0.83) from m = 32: the TRMC-RAD continuation to
+    levels 33..64 works on a thermalised pool of a few particles, which
+    cannot supply the leaves; the depth is lowered until the plan fits."""
+    counts = [885, 916, 111, 3000]
+    v, cs = cells(counts, seed=15)
+    p = T.collide_params(dt=1.8, eps=1.0, alpha=0.0, rho_scale=0.0, trunc=T.TRUNC_RAD, m=32, indicator=T.IND_PXX)
+    cp = np.stack([np.ones(4), np.full(4, 1.8), 1.0 / np.array(counts, float), np.zeros(4)], axis=1)
+    g, vo, rep = compare(v, cs, p, step=2, m_state=np.full(4, 32, np.int32), cell_param=cp)
+    assert rep[:, 1].max() >= 2 and rep[:, 11].sum() > 0, "expected continuations with depth reductions"
