@@ -90,6 +90,10 @@ typedef struct trmc_state {
     trmc_cell_param *cell_param;  /* [n_cells] or NULL (then the params scalars)   */
     const uint64_t *cell_key;     /* [n_cells] (problem << 32 | cell in problem) or NULL */
     double *cell_vmax2;           /* [n_cells] max |v|^2 after the last collide, or NULL */
+    double *cell_carry;           /* [n_cells][4] or NULL: momentum (3) and sum |v|^2 that rounding
+                                     the thermalised velocities to the storage precision left over;
+                                     the next step's renormalisation target adds it back, so
+                                     sum(stored) + carry is conserved to FP64 round-off */
     int64_t capacity;             /* length of each particle array                */
     int32_t n_cells;
     uint32_t problem_id;          /* used when cell_key is NULL                   */

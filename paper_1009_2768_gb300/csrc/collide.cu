@@ -39,6 +39,7 @@ namespace {
 
 constexpr int NLEV = kMC + 2;
 constexpr int kWarpLevel = 64;     // levels with at most this many collisions run in one warp
+constexpr int kPreLabels = 16;     // labels per level drawn ahead of the plan
 
 struct Args {
     void *vx, *vy, *vz;
@@ -48,6 +49,7 @@ struct Args {
     const trmc_cell_param *cell_param;
     const uint64_t *cell_key;
     double *cell_vmax2;
+    double *cell_carry;
     uint32_t problem_id;
     uint64_t seed, step;
     trmc_collide_params prm;
@@ -66,11 +68,12 @@ struct Sh {
     int32_t Pn[kMC + 1];
     double uS[NLEV], uP[NLEV];
     U64x4 keys[NLEV];
-    double red[32 * 8];
+    double red[kRedScratch];
+    uint8_t lab[NLEV][kPreLabels];   // labels of the first kPreLabels collisions of each level
     int32_t cell, n, m, lo, m_eff, pass, n0, D0, R, npart, m_next, Dge1;
     int32_t n0_prev, D0_prev;
     int32_t feas, pdrop, psurp, pdrop_tot, psurp_tot, skip, cont, m_top, m_first, n0_first;
-    double q, Sigma, U[3], P[3], E, S_pre, dP[3], dE, dS, Pp[3], Ep, Sp;
+    double q, Sigma, U[3], P[3], E, S_pre, dP[3], dE, dS, Pp[3], Ep, Sp, carry[4], Pt[3], Et;
     double alpha, dt, eps, rho_scale;
     uint64_t problem, lcell;
     U64x4 keyK;
@@ -135,6 +138,55 @@ template <> struct Math<float> {
     }
 };
 
+// Per-thread partial sums of particle quantities.  In FP64 contexts they are
+// plain double sums.  In FP32-mixed contexts they are compensated float sums
+// (TwoSum, with squares split exactly by an FMA), about 48 significant bits,
+// so no per-particle work lands on GB300's FP64 pipe (2 lanes/clk/SM); the
+// partials are combined in FP64 across the warp and the block.
+template <typename Real> struct Sum;
+template <> struct Sum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void add_sq3(double x, double y, double z) { s += x * x + y * y + z * z; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Sum<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = hi + x, bp = t - hi;
+        lo += (hi - (t - bp)) + (x - bp);
+        hi = t;
+    }
+    __device__ __forceinline__ void add_sq(float x)
+    {
+        const float p = x * x;
+        add(p);
+        lo += fmaf(x, x, -p);
+    }
+    __device__ __forceinline__ void sub_sq(float x)
+    {
+        const float p = x * x;
+        add(-p);
+        lo -= fmaf(x, x, -p);
+    }
+    __device__ __forceinline__ void add_sq3(float x, float y, float z) { add_sq(x); add_sq(y); add_sq(z); }
+    __device__ __forceinline__ void sub_sq3(float x, float y, float z) { sub_sq(x); sub_sq(y); sub_sq(z); }
+    __device__ __forceinline__ double get() const { return double(hi) + double(lo); }
+};
+
+// |v|^2 and the adaptive indicator in the working precision
+template <typename Real>
+__device__ __forceinline__ Real indicator_r(Real x, Real y, Real z, Real Ux, int ind)
+{
+    if (ind == TRMC_IND_M4) {
+        const Real e = x * x + y * y + z * z;
+        return e * e;
+    }
+    const Real d = x - Ux;
+    return d * d;
+}
+
 __device__ __forceinline__ double indicator(double x, double y, double z, const double U[3], int ind)
 {
     if (ind == TRMC_IND_M4) {
@@ -179,6 +231,7 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
         sh.feas = sh.pdrop = sh.psurp = sh.pdrop_tot = sh.psurp_tot = 0;
         sh.n0_prev = 0; sh.D0_prev = 0;
         sh.dP[0] = sh.dP[1] = sh.dP[2] = 0.0; sh.dE = 0.0; sh.dS = 0.0;
+        for (int j = 0; j < 4; ++j) sh.carry[j] = a.cell_carry ? a.cell_carry[4 * int64_t(cell) + j] : 0.0;
         // persistent layout: V, flags, inv[2]
         char *smem = reinterpret_cast<char *>(dsm);
         size_t scap = size_t(a.smem_bytes);
@@ -228,27 +281,41 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
 
     // ---- 1. stage + moments -------------------------------------------------
     {
-        double s[5] = {0, 0, 0, 0, 0};
-        for (int i = tid; i < n; i += bs) {
-            const Real x = gx[base + i], y = gy[base + i], z = gz[base + i];
-            Vx[i] = x; Vy[i] = y; Vz[i] = z;
-            const double dx = x, dy = y, dz = z;
-            s[0] += dx; s[1] += dy; s[2] += dz;
-            const double e = dx * dx + dy * dy + dz * dz;
-            s[3] += e;
-            s[4] += e * e;
+        Sum<Real> a0, a1, a2, a3, a4;
+        constexpr int U = 4;      // loads issued together, ahead of the stores they feed
+        for (int i0 = tid; i0 < n; i0 += U * bs) {
+            Real x[U], y[U], z[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * bs;
+                if (i < n) { x[u] = gx[base + i]; y[u] = gy[base + i]; z[u] = gz[base + i]; }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * bs;
+                if (i < n) {
+                    Vx[i] = x[u]; Vy[i] = y[u]; Vz[i] = z[u];
+                    a0.add(x[u]); a1.add(y[u]); a2.add(z[u]);
+                    a3.add_sq3(x[u], y[u], z[u]);
+                    const Real e = x[u] * x[u] + y[u] * y[u] + z[u] * z[u];
+                    a4.add(e * e);
+                }
+            }
         }
+        double s[5] = {a0.get(), a1.get(), a2.get(), a3.get(), a4.get()};
         block_sum<5>(s, sh.red);
         const double U0 = s[0] / double(n), U1 = s[1] / double(n), U2 = s[2] / double(n);
-        double d2 = 0.0, pxx = 0.0;
+        const Real u0 = Real(U0), u1 = Real(U1), u2 = Real(U2);
+        Real d2 = 0;
+        Sum<Real> pxx;
         for (int i = tid; i < n; i += bs) {
-            const double ax = double(Vx[i]) - U0, ay = double(Vy[i]) - U1, az = double(Vz[i]) - U2;
+            const Real ax = Vx[i] - u0, ay = Vy[i] - u1, az = Vz[i] - u2;
             d2 = fmax(d2, ax * ax + ay * ay + az * az);
-            pxx += ax * ax;
+            pxx.add(ax * ax);
         }
-        double t[1] = {pxx};
+        double t[1] = {pxx.get()};
         block_sum<1>(t, sh.red);
-        const double dmax = (sh.alpha != 0.0) ? block_max(d2, sh.red) : 0.0;
+        const double dmax = (sh.alpha != 0.0) ? block_max(double(d2), sh.red) : 0.0;
         if (tid == 0) {
             sh.P[0] = s[0]; sh.P[1] = s[1]; sh.P[2] = s[2]; sh.E = s[3];
             sh.U[0] = U0; sh.U[1] = U1; sh.U[2] = U2;
@@ -286,6 +353,13 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
                 for (int t = lane; t < m; t += 32) {
                     sh.uP[t + 1] = u01(rng.draw(uint64_t(t + 1), 0, uint32_t(pass), TAG_PARITY).w[0]);
                     sh.keys[t + 1] = rng.draw(0, uint64_t(t + 1), uint32_t(pass), TAG_PERMK);
+                }
+                // the first kPreLabels labels of every level, off the plan's critical path
+                for (int t = lane; t < m * (kPreLabels / 4); t += 32) {
+                    const int lv = 1 + t / (kPreLabels / 4), g = t % (kPreLabels / 4);
+                    const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sh.lab[lv][4 * g + j] = uint8_t(below(w.w[j], uint32_t(lv)));
                 }
             }
             __syncwarp();
@@ -337,7 +411,8 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
                     for (int k = lane; k < lv; k += 32) row[k] = 0;
                     __syncwarp();
                     const int Cn = sh.C[lv];
-                    for (int g = lane; g < (Cn + 3) >> 2; g += 32) {
+                    for (int c = lane; c < Cn && c < kPreLabels; c += 32) atomicAdd(&row[sh.lab[lv][c]], 1);
+                    for (int g = kPreLabels / 4 + lane; g < (Cn + 3) >> 2; g += 32) {
                         const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
@@ -535,27 +610,36 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
         //    adaptive indicator from the changed particles only, without
         //    cancelling two sums over the whole cell.
         {
-            double s[5] = {0, 0, 0, 0, 0};
+            Sum<Real> c0, c1, c2, c3, c4;
+            const Real Ux = Real(sh.U[0]);
             for (int jx = tid; jx < D0; jx += bs) {
                 const int sl = inv[n0 + jx];
-                const double ox = Vx[sl], oy = Vy[sl], oz = Vz[sl];
+                const Real ox = Vx[sl], oy = Vy[sl], oz = Vz[sl];
                 const Real x = OBx[jx], y = OBy[jx], z = OBz[jx];
                 Vx[sl] = x; Vy[sl] = y; Vz[sl] = z;
-                const double dx = x, dy = y, dz = z;
-                s[0] += dx - ox; s[1] += dy - oy; s[2] += dz - oz;
-                s[3] += (dx * dx + dy * dy + dz * dz) - (ox * ox + oy * oy + oz * oz);
-                s[4] += indicator(dx, dy, dz, sh.U, prm.indicator) - indicator(ox, oy, oz, sh.U, prm.indicator);
+                if constexpr (sizeof(Real) == 8) {
+                    c0.add(x - ox); c1.add(y - oy); c2.add(z - oz);
+                    c3.add((x * x + y * y + z * z) - (ox * ox + oy * oy + oz * oz));
+                    c4.add(indicator(x, y, z, sh.U, prm.indicator) - indicator(ox, oy, oz, sh.U, prm.indicator));
+                } else {
+                    c0.add(x); c0.add(-ox); c1.add(y); c1.add(-oy); c2.add(z); c2.add(-oz);
+                    c3.add_sq3(x, y, z); c3.sub_sq3(ox, oy, oz);
+                    c4.add(indicator_r(x, y, z, Ux, prm.indicator) - indicator_r(ox, oy, oz, Ux, prm.indicator));
+                }
             }
+            double s[5] = {c0.get(), c1.get(), c2.get(), c3.get(), c4.get()};
             block_sum<5>(s, sh.red);
-            double p[5] = {0, 0, 0, 0, 0};
+            Sum<Real> p0, p1, p2, p3, p4;
             const int pool0 = n0 + D0, R = sh.R;
             for (int t = tid; t < R; t += bs) {
                 const int sl = inv[pool0 + t];
-                const double x = Vx[sl], y = Vy[sl], z = Vz[sl];
-                p[0] += x; p[1] += y; p[2] += z;
-                p[3] += x * x + y * y + z * z;
-                p[4] += indicator(x, y, z, sh.U, prm.indicator);
+                const Real x = Vx[sl], y = Vy[sl], z = Vz[sl];
+                p0.add(x); p1.add(y); p2.add(z);
+                p3.add_sq3(x, y, z);
+                if constexpr (sizeof(Real) == 8) p4.add(indicator(x, y, z, sh.U, prm.indicator));
+                else p4.add(indicator_r(x, y, z, Ux, prm.indicator));
             }
+            double p[5] = {p0.get(), p1.get(), p2.get(), p3.get(), p4.get()};
             block_sum<5>(p, sh.red);
             if (tid == 0) {
                 sh.dP[0] += s[0]; sh.dP[1] += s[1]; sh.dP[2] += s[2]; sh.dE += s[3]; sh.dS += s[4];
@@ -621,50 +705,98 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
     const int32_t *inv = sh.inv[pass & 1];
     const int pool0 = sh.n0 + sh.D0;
     if (R >= 2) {
-        double s[3] = {0, 0, 0};
+        Sum<Real> q0, q1, q2;
         for (int t = tid; t < R; t += bs) {
             Real z0, z1, z2;
             Math<Real>::normals(rng.draw(uint64_t(t), 0, 0, TAG_MAXW), z0, z1, z2);
             const int sl = inv[pool0 + t];
             Vx[sl] = z0; Vy[sl] = z1; Vz[sl] = z2;
-            s[0] += double(z0); s[1] += double(z1); s[2] += double(z2);
+            q0.add(z0); q1.add(z1); q2.add(z2);
         }
+        double s[3] = {q0.get(), q1.get(), q2.get()};
         block_sum<3>(s, sh.red);
         const double zb0 = s[0] / double(R), zb1 = s[1] / double(R), zb2 = s[2] / double(R);
-        double e[1] = {0.0};
+        const Real rz0 = Real(zb0), rz1 = Real(zb1), rz2 = Real(zb2);
+        Sum<Real> qe;
         for (int t = tid; t < R; t += bs) {
             const int sl = inv[pool0 + t];
-            const double a0 = double(Vx[sl]) - zb0, a1 = double(Vy[sl]) - zb1, a2 = double(Vz[sl]) - zb2;
-            e[0] += a0 * a0 + a1 * a1 + a2 * a2;
+            if constexpr (sizeof(Real) == 8) {
+                const double a0 = Vx[sl] - zb0, a1 = Vy[sl] - zb1, a2 = Vz[sl] - zb2;
+                qe.add(a0 * a0 + a1 * a1 + a2 * a2);
+            } else {
+                qe.add_sq3(Vx[sl] - rz0, Vy[sl] - rz1, Vz[sl] - rz2);
+            }
         }
+        double e[1] = {qe.get()};
         block_sum<1>(e, sh.red);
-        const double Pt0 = sh.Pp[0] - sh.dP[0], Pt1 = sh.Pp[1] - sh.dP[1], Pt2 = sh.Pp[2] - sh.dP[2];
-        const double Et = sh.Ep - sh.dE;
+        // target: what the set carried, minus the collisions' round-off change,
+        // plus what earlier steps' rounding to the storage precision left over
+        const double Pt0 = sh.Pp[0] - sh.dP[0] + sh.carry[0], Pt1 = sh.Pp[1] - sh.dP[1] + sh.carry[1],
+                     Pt2 = sh.Pp[2] - sh.dP[2] + sh.carry[2];
+        const double Et = sh.Ep - sh.dE + sh.carry[3];
+        if (tid == 0) { sh.Pt[0] = Pt0; sh.Pt[1] = Pt1; sh.Pt[2] = Pt2; sh.Et = Et; }
         double et = Et - (Pt0 * Pt0 + Pt1 * Pt1 + Pt2 * Pt2) / double(R);
         if (et < 0.0) et = 0.0;
         const double sc = (e[0] > 0.0) ? sqrt(et / e[0]) : 0.0;
         const double u0 = Pt0 / double(R), u1 = Pt1 / double(R), u2 = Pt2 / double(R);
-        for (int t = tid; t < R; t += bs) {
-            const int sl = inv[pool0 + t];
-            Vx[sl] = Real(u0 + sc * (double(Vx[sl]) - zb0));
-            Vy[sl] = Real(u1 + sc * (double(Vy[sl]) - zb1));
-            Vz[sl] = Real(u2 + sc * (double(Vz[sl]) - zb2));
+        if constexpr (sizeof(Real) == 8) {
+            for (int t = tid; t < R; t += bs) {
+                const int sl = inv[pool0 + t];
+                Vx[sl] = u0 + sc * (Vx[sl] - zb0);
+                Vy[sl] = u1 + sc * (Vy[sl] - zb1);
+                Vz[sl] = u2 + sc * (Vz[sl] - zb2);
+            }
+        } else {
+            // FP64 scale and targets, applied in float: the stored result is a
+            // float either way
+            const Real fs = Real(sc), f0 = Real(u0), f1 = Real(u1), f2 = Real(u2);
+            for (int t = tid; t < R; t += bs) {
+                const int sl = inv[pool0 + t];
+                Vx[sl] = f0 + fs * (Vx[sl] - rz0);
+                Vy[sl] = f1 + fs * (Vy[sl] - rz1);
+                Vz[sl] = f2 + fs * (Vz[sl] - rz2);
+            }
         }
     }
     __syncthreads();
+    if (a.cell_carry) {
+        // new carry: what the stored thermalised set misses of its target
+        // (R >= 2), or the collisions' round-off change (R <= 1)
+        if (R >= 2) {
+            Sum<Real> r0, r1, r2, r3;
+            for (int t = tid; t < R; t += bs) {
+                const int sl = inv[pool0 + t];
+                const Real x = Vx[sl], y = Vy[sl], z = Vz[sl];
+                r0.add(x); r1.add(y); r2.add(z);
+                r3.add_sq3(x, y, z);
+            }
+            double r[4] = {r0.get(), r1.get(), r2.get(), r3.get()};
+            block_sum<4>(r, sh.red);
+            if (tid == 0) {
+                sh.carry[0] = sh.Pt[0] - r[0]; sh.carry[1] = sh.Pt[1] - r[1]; sh.carry[2] = sh.Pt[2] - r[2];
+                sh.carry[3] = sh.Et - r[3];
+            }
+        } else if (tid == 0) {
+            sh.carry[0] -= sh.dP[0]; sh.carry[1] -= sh.dP[1]; sh.carry[2] -= sh.dP[2]; sh.carry[3] -= sh.dE;
+        }
+        if (tid == 0)
+            for (int j = 0; j < 4; ++j) a.cell_carry[4 * int64_t(cell) + j] = sh.carry[j];
+    }
 
     // ---- 8. write back the changed particles; cell max |v|^2 ----------------
     {
-        double vm = 0.0;
+        Real vm = 0;
         for (int i = tid; i < n; i += bs) {
             const Real x = Vx[i], y = Vy[i], z = Vz[i];
             if ((sh.flags[i >> 5] >> (i & 31)) & 1u) { gx[base + i] = x; gy[base + i] = y; gz[base + i] = z; }
-            const double dx = x, dy = y, dz = z;
-            vm = fmax(vm, __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+            if constexpr (sizeof(Real) == 8)       // rounded exactly as the CPU reference rounds it
+                vm = fmax(vm, __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+            else
+                vm = fmaxf(vm, __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z)));
         }
         if (a.cell_vmax2) {
-            vm = block_max(vm, sh.red);
-            if (tid == 0) a.cell_vmax2[cell] = vm;
+            const double vmax = block_max(double(vm), sh.red);
+            if (tid == 0) a.cell_vmax2[cell] = vmax;
         }
     }
     if (tid == 0) {
@@ -760,6 +892,7 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     a.cell_param = st->cell_param;
     a.cell_key = st->cell_key;
     a.cell_vmax2 = st->cell_vmax2;
+    a.cell_carry = st->cell_carry;
     a.problem_id = st->problem_id;
     a.seed = ctx->seed;
     a.step = step;
@@ -862,6 +995,7 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
     a.cell_param = st->cell_param;
     a.cell_key = st->cell_key;
     a.cell_vmax2 = st->cell_vmax2;
+    a.cell_carry = st->cell_carry;
     a.problem_id = st->problem_id;
     a.seed = seed;
     a.step = step;

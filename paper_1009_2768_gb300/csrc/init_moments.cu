@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(256) init_kernel(const double *ci_all, const i
                                                    uint32_t problem_id, uint64_t seed, Real *vx, Real *vy, Real *vz,
                                                    Real *x, double *cell_vmax2)
 {
-    __shared__ double red[32];
+    __shared__ double red[kRedScratch];
     const int c = blockIdx.x;
     const double *ci = ci_all + size_t(c) * TRMC_INIT_COLS;
     const int kind = int(ci[0]);
@@ -68,7 +68,7 @@ template <typename Real>
 __global__ void __launch_bounds__(256) moments_kernel(const Real *vx, const Real *vy, const Real *vz, const int64_t *cs,
                                                       const trmc_cell_param *cp, double *out)
 {
-    __shared__ double red[32 * 8];
+    __shared__ double red[kRedScratch];
     const int c = blockIdx.x;
     const int64_t b = cs[c], e = cs[c + 1], n = e - b;
     double *o = out + size_t(c) * TRMC_MOM_COLS;

@@ -103,7 +103,7 @@ __device__ __forceinline__ Mover32 make_mover<float>(const trmc_domain &D, doubl
 __global__ void cfl_kernel(const trmc_domain *doms, int nd, int nc_total, const double *cell_vmax2, double cfl,
                            double *dt, trmc_cell_param *cell_param)
 {
-    __shared__ double red[32];
+    __shared__ double red[kRedScratch];
     const int d = blockIdx.x;
     if (d >= nd) return;
     const trmc_domain D = doms[d];

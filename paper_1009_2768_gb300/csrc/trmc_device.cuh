@@ -127,11 +127,18 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
-// Sum K doubles over the block; every thread gets the totals.  scratch must
-// hold 32*K doubles.  Contains two __syncthreads().
+// Reduction scratch: warp partials at [w*K + j] (w < 32, K <= 8), block_sum
+// totals at [256 + j], the block_max total at [264].
+constexpr int kRedScratch = 272;
+
+// Sum K doubles over the block (K <= 8); every thread gets the totals.
+// scratch holds kRedScratch doubles.  Warp partials are combined by warp 0 alone (lane j
+// sums value j), so the FP64 work beyond the warp trees is K lanes x (warps)
+// adds instead of every thread re-summing every partial.  Two barriers.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double *scratch)
 {
+    static_assert(K >= 1 && K <= 8, "block_sum handles 1..8 values");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int j = 0; j < K; ++j) v[j] = warp_sum(v[j]);
@@ -140,13 +147,14 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double *scratch)
         for (int j = 0; j < K; ++j) scratch[warp * K + j] = v[j];
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
+    if (warp == 0 && lane < K) {
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += scratch[w * K + j];
-        v[j] = s;
+        for (int w = 0; w < nw; ++w) s += scratch[w * K + lane];
+        scratch[256 + lane] = s;
     }
     __syncthreads();
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = scratch[256 + j];
 }
 
 __device__ __forceinline__ double block_max(double v, double *scratch)
@@ -155,10 +163,13 @@ __device__ __forceinline__ double block_max(double v, double *scratch)
     v = warp_max(v);
     if (lane == 0) scratch[warp] = v;
     __syncthreads();
-    double m = scratch[0];
-    for (int w = 1; w < nw; ++w) m = fmax(m, scratch[w]);
+    if (threadIdx.x == 0) {
+        double m = scratch[0];
+        for (int w = 1; w < nw; ++w) m = fmax(m, scratch[w]);
+        scratch[264] = m;
+    }
     __syncthreads();
-    return m;
+    return scratch[264];
 }
 
 }  // namespace trmc

@@ -44,6 +44,7 @@ class State(C.Structure):
                 ("vx_alt", C.c_void_p), ("vy_alt", C.c_void_p), ("vz_alt", C.c_void_p), ("x_alt", C.c_void_p),
                 ("cell_start", C.c_void_p), ("cell_start_alt", C.c_void_p), ("m_max", C.c_void_p),
                 ("cell_param", C.c_void_p), ("cell_key", C.c_void_p), ("cell_vmax2", C.c_void_p),
+                ("cell_carry", C.c_void_p),
                 ("capacity", C.c_int64), ("n_cells", C.c_int32), ("problem_id", C.c_uint32)]
 
 
@@ -174,7 +175,7 @@ class ParticleState:
     *_alt arrays swap; after_transport() keeps the tensors in step."""
 
     def __init__(self, cell_start, capacity=None, precision=FP64, with_x=False, rad=False,
-                 cell_param=None, cell_key=None, problem_id=0, device="cuda"):
+                 cell_param=None, cell_key=None, problem_id=0, carry=False, device="cuda"):
         import torch
         cs = torch.as_tensor(np.asarray(cell_start, dtype=np.int64)).to(device)
         n_cells = cs.numel() - 1
@@ -195,6 +196,7 @@ class ParticleState:
         self.cell_key = None if cell_key is None else torch.as_tensor(
             np.asarray(cell_key, dtype=np.uint64).view(np.int64)).to(device)
         self.cell_vmax2 = torch.zeros(max(n_cells, 1), dtype=torch.float64, device=device)
+        self.cell_carry = torch.zeros((max(n_cells, 1), 4), dtype=torch.float64, device=device) if carry else None
         self.n_cells = n_cells
         self.capacity = n
         self.c = State()
@@ -216,6 +218,7 @@ class ParticleState:
         c.cell_param = self.cell_param.data_ptr() if self.cell_param is not None else None
         c.cell_key = self.cell_key.data_ptr() if self.cell_key is not None else None
         c.cell_vmax2 = self.cell_vmax2.data_ptr()
+        c.cell_carry = self.cell_carry.data_ptr() if self.cell_carry is not None else None
 
     def after_transport(self):
         if self.c.vx == self.v_alt[0].data_ptr():
