@@ -7,6 +7,13 @@ VHS hard-sphere acceptance, Maxwellian renormalisation, TRMC-RAD) over the
 each, CFL 0.5, FP64.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload shock|batched|bkw]
+
+--workload selects the step timed (default shock, the benchmark line):
+  shock   the four-tube FP64 shock-tube step above;
+  batched 4096 independent homogeneous cells, 64..8192 particles log-uniform,
+          bi-Maxwellian, VHS alpha 0.6, eps log-uniform 1e-4..10, FP32-mixed;
+  bkw     one homogeneous cell of 1e5 Maxwell molecules from BKW data, FP64.
 
 N > 1 runs N independent replicas (one per rank, launched by torchrun), each
 on its own problem ids; value is the total over ranks.  --impl reference
@@ -14,6 +21,7 @@ times the CPU oracle (FP64, all host cores) on a bounded sample of the same
 workload.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -32,6 +40,17 @@ WORKLOAD = ("1D Riemann shock tube on [0,1] (rho 1/0.125, T 1/0.8, u 0), hard-sp
             "CFL 0.5, TRMC-RAD (P_xx indicator, delta 0.005/0.01, m0 2); 4 tubes x 400 cells x 500 "
             "particles/cell mean, eps 1e-1/1e-2/1e-3/1e-4, FP64")
 METRIC = "particle-steps/s"
+
+# DRAM traffic per collide launch from `ncu` (dram__bytes_read.sum + dram__bytes_write.sum)
+# of the same command, keyed by the hash of csrc/collide.cu it was taken on; reported as
+# null once the kernel source differs.  See profiles/.
+NCU_TRAFFIC = {
+    "shock": {"collide_sha": "6d2dfbde8b297843", "bytes": 22815744 + 73984},
+}
+
+
+def collide_sha():
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_1009_2768_gb300", "csrc", "collide.cu"), "rb").read()).hexdigest()[:16]
 
 
 def peaks():
@@ -143,6 +162,69 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+WORKLOADS = {
+    "shock": WORKLOAD,
+    "batched": ("batched homogeneous relaxation: 4096 independent cells, 64..8192 particles log-uniform, "
+                "bi-Maxwellian T_par/T_perp in [0.3,3], VHS alpha 0.6, eps log-uniform 1e-4..10, dt 0.05, "
+                "TRMC-RAD, FP32-mixed"),
+    "bkw": "homogeneous Maxwell molecules, one cell of 1e5 particles, BKW K0 0.6, eps 1, dt 0.05, TRMC-RAD (M4), FP64",
+}
+
+
+def make_sim(workload, seed):
+    from paper_1009_2768_gb300 import trmc as T
+    from paper_1009_2768_gb300.workloads import BatchedRelaxation, HomogeneousBKW, ShockTubes
+    if workload == "shock":
+        return ShockTubes(EPS, N_CELLS, MEAN, precision=T.FP64, seed=seed), 8, "f64"
+    if workload == "batched":
+        return BatchedRelaxation(precision=T.FP32_MIXED, seed=seed), 4, "f32 velocities, f64 moments"
+    return HomogeneousBKW(100000, precision=T.FP64, seed=seed), 8, "f64"
+
+
+def time_steps(sim, K, flush, stats=None):
+    """K steps, each bracketed by CUDA events on the current stream, with an
+    L2 flush before each; returns per-step (transport, collide) ms arrays."""
+    import torch
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        sim.step(stats=stats, events=ev[k])
+    torch.cuda.synchronize()
+    tr = np.array([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)])
+    co = np.array([ev[k][1].elapsed_time(ev[k][2]) for k in range(K)])
+    return tr, co
+
+
+def compare_forms(flush, steps=60, warm=5):
+    """The plain single-problem FP64 form (one tube alone) against the batched
+    FP32-mixed form (the four tubes in one launch), on the same GPU, with the
+    moment difference between the forms after the same number of steps."""
+    import torch
+    from paper_1009_2768_gb300 import trmc as T
+    from paper_1009_2768_gb300.workloads import ShockTubes
+    out = {}
+    temps = {}
+    for name, eps, prec in (("fp64_single_tube", (1e-2,), T.FP64), ("fp32_batched_tubes", EPS, T.FP32_MIXED)):
+        sim = ShockTubes(eps, N_CELLS, MEAN, precision=prec, seed=7)
+        for _ in range(warm):
+            sim.step()
+        tr, co = time_steps(sim, steps, flush)
+        T.trmc_check(sim.ctx)
+        out[name] = {"value": sim.n_particles / ((tr + co).mean() / 1e3), "unit": METRIC,
+                     "ms_per_step": float((tr + co).mean()), "particles": sim.n_particles}
+        mom = torch.zeros((sim.state.n_cells, T.MOM_COLS), dtype=torch.float64, device="cuda")
+        T.trmc_moments(sim.ctx, sim.state, mom)
+        temps[name] = mom[:N_CELLS, 5].cpu().numpy()        # the eps = 1e-2 tube's temperature profile
+        if name == "fp32_batched_tubes":
+            temps[name] = mom[N_CELLS:2 * N_CELLS, 5].cpu().numpy()
+        sim.close()
+    a, b = temps["fp64_single_tube"], temps["fp32_batched_tubes"]
+    out["moment_error"] = {"what": "L1 relative difference of the eps=1e-2 tube's temperature profile, FP32-mixed "
+                                   "batched vs FP64 single, same seed and step count (statistical noise included)",
+                           "value": float(np.abs(a - b).sum() / np.abs(a).sum()), "steps": warm + steps}
+    return out
+
+
 def ours(args):
     import torch
     rank, world, local = dist_env()
@@ -154,9 +236,8 @@ def ours(args):
     from paper_1009_2768_gb300 import build
     build.build()
     from paper_1009_2768_gb300 import trmc as T
-    from paper_1009_2768_gb300.workloads import ShockTubes
 
-    sim = ShockTubes(EPS, N_CELLS, MEAN, precision=T.FP64, seed=rank)
+    sim, rb, dtype = make_sim(args.workload, rank)
     n = sim.n_particles
     stats = torch.zeros(len(T.STATS_FIELDS), dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")      # > L2 (129 MB)
@@ -164,7 +245,6 @@ def ours(args):
         sim.step()
     T.trmc_check(sim.ctx)
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     clocks = Clocks(local)
     if dist:
         dist.barrier()
@@ -172,18 +252,13 @@ def ours(args):
     clocks.start()
     time.sleep(0.2)
     t_wall = time.perf_counter()
-    for k in range(K):
-        flush.zero_()
-        sim.step(stats=stats, events=ev[k])
-    torch.cuda.synchronize()
+    tr_ms, co_ms = time_steps(sim, K, flush, stats)
     t_wall = time.perf_counter() - t_wall
     if dist:
         dist.barrier()
     clk = clocks.stop()
     T.trmc_check(sim.ctx)
-    step_ms = np.array([ev[k][0].elapsed_time(ev[k][2]) for k in range(K)])
-    tr_ms = np.array([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)])
-    co_ms = np.array([ev[k][1].elapsed_time(ev[k][2]) for k in range(K)])
+    step_ms = tr_ms + co_ms
     total_ms = float(step_ms.sum())
     if dist:
         t = torch.tensor([total_ms], device="cuda")
@@ -194,44 +269,49 @@ def ours(args):
 
     # roofline of the dominant kernel, from the same events
     peak, peak_kind = peaks()
-    rb = 8  # bytes per velocity component (FP64)
-    collide_bytes = 3 * rb * (n + st["changed"] / K)               # read all, write changed (per launch)
-    transport_bytes = (2 * rb + 8 * rb) * n                        # count: x,vx; scatter: read x,v + write x,v
+    collide_bytes = 3 * rb * (n + st["changed"] / K)               # read every particle, write the changed ones
+    transport_bytes = (2 * rb + 8 * rb) * n                        # count: x, v_x; scatter: read x, v + write x, v
     co_avg, tr_avg = co_ms.mean() / 1e3, tr_ms.mean() / 1e3
     if co_avg >= tr_avg:
-        kern, abytes, dur = "collide_kernel<double>", collide_bytes, co_avg
+        kern, abytes, dur = "collide_kernel", collide_bytes, co_avg
     else:
         kern, abytes, dur = "transport (count+scan+scatter)", transport_bytes, tr_avg
     achieved = abytes / dur / 1e9
+    tr_rec = NCU_TRAFFIC.get(args.workload)
+    traffic = tr_rec["bytes"] if (tr_rec and kern == "collide_kernel" and tr_rec["collide_sha"] == collide_sha()) else None
     roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+            "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
             "collide_ms": float(co_ms.mean()), "transport_ms": float(tr_ms.mean()),
             "algorithmic_bytes_per_launch": abytes}
 
     # end to end: host-resident state, H2D + step + D2H every step
     e2e = None
     if not args.no_e2e:
-        hx = torch.empty_like(sim.state.x, device="cpu").pin_memory()
         hv = torch.empty_like(sim.state.v, device="cpu").pin_memory()
-        hx.copy_(sim.state.x)
         hv.copy_(sim.state.v)
+        hx = None
+        if sim.state.x is not None:
+            hx = torch.empty_like(sim.state.x, device="cpu").pin_memory()
+            hx.copy_(sim.state.x)
         hcs = sim.state.cell_start.cpu().pin_memory()
         Ke = max(1, min(K, 200))
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for k in range(Ke):
-            sim.state.x.copy_(hx, non_blocking=True)
+            if hx is not None:
+                sim.state.x.copy_(hx, non_blocking=True)
             sim.state.v.copy_(hv, non_blocking=True)
             sim.state.cell_start.copy_(hcs, non_blocking=True)
             sim.step()
-            hx.copy_(sim.state.x, non_blocking=True)
+            if hx is not None:
+                hx.copy_(sim.state.x, non_blocking=True)
             hv.copy_(sim.state.v, non_blocking=True)
             hcs.copy_(sim.state.cell_start, non_blocking=True)
         e1.record()
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1)
-        h2d = hx.numel() * hx.element_size() + hv.numel() * hv.element_size() + hcs.numel() * 8
+        h2d = hv.numel() * hv.element_size() + hcs.numel() * 8 + (hx.numel() * hx.element_size() if hx is not None else 0)
         e2e = {"value": n * world * Ke / (e_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": h2d, "steps": Ke}
 
@@ -244,15 +324,20 @@ def ours(args):
         cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
                "sample": f"one full tube (eps 1e-2, {nn} particles), {done} steps in {el:.1f} s"}
 
+    forms = None
+    if rank == 0 and args.workload == "shock" and not args.no_forms:
+        forms = compare_forms(flush)
+
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "particles_per_gpu": n, "cells_per_gpu": N_CELLS * len(EPS),
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "particles_per_gpu": n,
+                       "cells_per_gpu": sim.state.n_cells,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": sim.launches_per_step * K, "clocks": clk,
+            "gpu_launches": sim.launches_per_step * K, "clocks": clk, "forms": forms,
             "step_stats": {k: st[k] / K for k in ("collisions", "dummy", "maxwell", "changed", "passes")},
             "wall_s": t_wall}))
     sim.close()
@@ -268,6 +353,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--workload", default="shock", choices=["shock", "batched", "bkw"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
