@@ -90,6 +90,11 @@ typedef struct trmc_state {
     trmc_cell_param *cell_param;  /* [n_cells] or NULL (then the params scalars)   */
     const uint64_t *cell_key;     /* [n_cells] (problem << 32 | cell in problem) or NULL */
     double *cell_vmax2;           /* [n_cells] max |v|^2 after the last collide, or NULL */
+    uint64_t *step_dev;           /* NULL, or a device step counter: trmc_collide then keys its
+                                     draws with *step_dev (ignoring its step argument) and adds 1 to
+                                     it when done, so a captured CUDA graph advances on replay */
+    const int32_t *cell_order;    /* [n_cells] or NULL: the order in which cells are handed to
+                                     CTAs (e.g. largest first); results do not depend on it */
     double *cell_carry;           /* [n_cells][4] or NULL: momentum (3) and sum |v|^2 that rounding
                                      the thermalised velocities to the storage precision left over;
                                      the next step's renormalisation target adds it back, so

@@ -50,6 +50,8 @@ struct Args {
     const uint64_t *cell_key;
     double *cell_vmax2;
     double *cell_carry;
+    uint64_t *step_dev;
+    const int32_t *cell_order;
     uint32_t problem_id;
     uint64_t seed, step;
     trmc_collide_params prm;
@@ -203,7 +205,7 @@ __device__ __forceinline__ void raise_status(int *status, int code, int cell)
 }
 
 template <typename Real>
-__device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, char *slab, int cell,
+__device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigned char *dsm, char *slab, int cell,
                              double (&cnt)[3])
 {
     const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
@@ -277,7 +279,7 @@ __device__ void process_cell(const Args &a, Sh<Real> &sh, unsigned char *dsm, ch
         return;
     }
     Real *Vx = sh.V, *Vy = sh.V + n, *Vz = sh.V + 2 * n;
-    const CellRng rng{a.seed, sh.problem, sh.lcell, a.step};
+    const CellRng rng{a.seed, sh.problem, sh.lcell, step};
 
     // ---- 1. stage + moments -------------------------------------------------
     {
@@ -817,14 +819,18 @@ __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
     __shared__ Sh<Real> sh;
     __shared__ int s_cell;
     char *slab = a.slabs + size_t(blockIdx.x) * a.slab_bytes;
+    // the device step counter is read before any CTA can finish: it is
+    // advanced only after every CTA of this launch has retired its last cell
+    const uint64_t step = a.step_dev ? *a.step_dev : a.step;
     for (;;) {
         if (threadIdx.x == 0) s_cell = int(atomicAdd(&a.tickets[0], 1u));
         __syncthreads();
-        const int cell = s_cell;
+        const int ticket = s_cell;
         __syncthreads();
-        if (cell >= a.n_cells) break;
+        if (ticket >= a.n_cells) break;
+        const int cell = a.cell_order ? a.cell_order[ticket] : ticket;
         double cnt[3] = {0, 0, 0};   // collisions, dummy, exceed
-        process_cell<Real>(a, sh, dsm, slab, cell, cnt);
+        process_cell<Real>(a, step, sh, dsm, slab, cell, cnt);
         __syncthreads();
         if (a.report || a.stats) {
             block_sum<3>(cnt, sh.red);
@@ -854,6 +860,7 @@ __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
         if (done == gridDim.x - 1) {
             a.tickets[0] = 0u;
             a.tickets[1] = 0u;
+            if (a.step_dev) *a.step_dev = step + 1;
             __threadfence();
         }
     }
@@ -893,6 +900,8 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     a.cell_key = st->cell_key;
     a.cell_vmax2 = st->cell_vmax2;
     a.cell_carry = st->cell_carry;
+    a.step_dev = st->step_dev;
+    a.cell_order = st->cell_order;
     a.problem_id = st->problem_id;
     a.seed = ctx->seed;
     a.step = step;
@@ -996,6 +1005,8 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
     a.cell_key = st->cell_key;
     a.cell_vmax2 = st->cell_vmax2;
     a.cell_carry = st->cell_carry;
+    a.step_dev = st->step_dev;
+    a.cell_order = st->cell_order;
     a.problem_id = st->problem_id;
     a.seed = seed;
     a.step = step;

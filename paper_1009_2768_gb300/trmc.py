@@ -44,7 +44,7 @@ class State(C.Structure):
                 ("vx_alt", C.c_void_p), ("vy_alt", C.c_void_p), ("vz_alt", C.c_void_p), ("x_alt", C.c_void_p),
                 ("cell_start", C.c_void_p), ("cell_start_alt", C.c_void_p), ("m_max", C.c_void_p),
                 ("cell_param", C.c_void_p), ("cell_key", C.c_void_p), ("cell_vmax2", C.c_void_p),
-                ("cell_carry", C.c_void_p),
+                ("step_dev", C.c_void_p), ("cell_order", C.c_void_p), ("cell_carry", C.c_void_p),
                 ("capacity", C.c_int64), ("n_cells", C.c_int32), ("problem_id", C.c_uint32)]
 
 
@@ -197,6 +197,8 @@ class ParticleState:
             np.asarray(cell_key, dtype=np.uint64).view(np.int64)).to(device)
         self.cell_vmax2 = torch.zeros(max(n_cells, 1), dtype=torch.float64, device=device)
         self.cell_carry = torch.zeros((max(n_cells, 1), 4), dtype=torch.float64, device=device) if carry else None
+        self.step_dev = None           # device step counter (use_device_step)
+        self.cell_order = None         # cell processing order (set_cell_order)
         self.n_cells = n_cells
         self.capacity = n
         self.c = State()
@@ -219,6 +221,20 @@ class ParticleState:
         c.cell_key = self.cell_key.data_ptr() if self.cell_key is not None else None
         c.cell_vmax2 = self.cell_vmax2.data_ptr()
         c.cell_carry = self.cell_carry.data_ptr() if self.cell_carry is not None else None
+        c.step_dev = self.step_dev.data_ptr() if self.step_dev is not None else None
+        c.cell_order = self.cell_order.data_ptr() if self.cell_order is not None else None
+
+    def use_device_step(self, start=0):
+        """Key the collision draws with a device counter that each trmc_collide
+        advances, so that captured CUDA graphs step on replay."""
+        import torch
+        self.step_dev = torch.full((1,), start, dtype=torch.int64, device=self.cell_vmax2.device)
+        self._fill()
+
+    def set_cell_order(self, order):
+        import torch
+        self.cell_order = torch.as_tensor(np.asarray(order, dtype=np.int32)).to(self.cell_vmax2.device)
+        self._fill()
 
     def after_transport(self):
         if self.c.vx == self.v_alt[0].data_ptr():

@@ -113,7 +113,8 @@ class HomogeneousBKW:
 
 class BatchedRelaxation:
     def __init__(self, n_cells=4096, lo=64, hi=8192, eps_lo=1e-4, eps_hi=10.0, alpha=0.6, dt=0.05,
-                 precision=T.FP32_MIXED, seed=0, trunc=T.TRUNC_RAD, m_init=2, workspace=1 << 30):
+                 precision=T.FP32_MIXED, seed=0, trunc=T.TRUNC_RAD, m_init=2, workspace=1 << 30,
+                 order="given"):
         g = synth.rng(seed)
         counts = synth.loguniform_ints(n_cells, lo, hi, g=g)
         eps = synth.loguniform(n_cells, eps_lo, eps_hi, g=g)
@@ -134,6 +135,8 @@ class BatchedRelaxation:
         ci[:, 4] = t_par
         ci[:, 5] = t_perp
         T.trmc_init_cells(self.ctx, self.state, _dev(ci))
+        if order == "largest_first":          # cell sizes never change here: order once
+            self.state.set_cell_order(np.argsort(-counts, kind="stable").astype(np.int32))
         self.params = T.collide_params(trunc=trunc, m=m_init, indicator=T.IND_PXX)
         self.step_index = 0
 
