@@ -13,7 +13,9 @@ each, CFL 0.5, FP64.  Prints one JSON line.
   shock   the four-tube FP64 shock-tube step above;
   batched 4096 independent homogeneous cells, 64..8192 particles log-uniform,
           bi-Maxwellian, VHS alpha 0.6, eps log-uniform 1e-4..10, FP32-mixed;
-  bkw     one homogeneous cell of 1e5 Maxwell molecules from BKW data, FP64.
+  bkw     one homogeneous cell of 1e5 Maxwell molecules from BKW data, FP64;
+  stationary  Mach 3 stationary shock, 4000 cells x 2500 particles, reservoirs,
+          FP32-mixed.
 
 N > 1 runs N independent replicas (one per rank, launched by torchrun), each
 on its own problem ids; value is the total over ranks.  --impl reference
@@ -168,12 +170,16 @@ WORKLOADS = {
                 "bi-Maxwellian T_par/T_perp in [0.3,3], VHS alpha 0.6, eps log-uniform 1e-4..10, dt 0.05, "
                 "TRMC-RAD, FP32-mixed"),
     "bkw": "homogeneous Maxwell molecules, one cell of 1e5 particles, BKW K0 0.6, eps 1, dt 0.05, TRMC-RAD (M4), FP64",
+    "stationary": ("1D stationary normal shock, Mach 3, 4000 cells x 2500 particles/cell mean (1e7), hard-sphere "
+                   "VHS, eps 1e-3, Rankine-Hugoniot inflow/outflow reservoirs, CFL 0.5, TRMC-RAD, FP32-mixed"),
 }
 
 
 def make_sim(workload, seed):
     from paper_1009_2768_gb300 import trmc as T
-    from paper_1009_2768_gb300.workloads import BatchedRelaxation, HomogeneousBKW, ShockTubes
+    from paper_1009_2768_gb300.workloads import BatchedRelaxation, HomogeneousBKW, ShockTubes, StationaryShock
+    if workload == "stationary":
+        return StationaryShock(4000, 2500, precision=T.FP32_MIXED, seed=seed), 4, "f32 velocities, f64 moments"
     if workload == "shock":
         return ShockTubes(EPS, N_CELLS, MEAN, precision=T.FP64, seed=seed), 8, "f64"
     if workload == "batched":
@@ -354,7 +360,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--workload", default="shock", choices=["shock", "batched", "bkw"])
+    ap.add_argument("--workload", default="shock", choices=["shock", "batched", "bkw", "stationary"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -115,11 +115,24 @@ typedef struct trmc_collide_params {
     int32_t reserved;                  /* must be 0                                 */
 } trmc_collide_params;
 
-/* One 1D problem for trmc_transport: cells [cell_begin, cell_begin+n_cells)
- * of equal width cover [x_lo, x_hi]; both ends are specular walls. */
+typedef enum trmc_bc {
+    TRMC_BC_SPECULAR = 0,   /* both ends are specular walls: x -> 2 x_wall - x, v_x -> -v_x          */
+    TRMC_BC_RESERVOIR = 1   /* both ends are reservoirs (inflow / outflow), see trmc_transport      */
+} trmc_bc;
+
+/* One 1D problem for trmc_transport: cells [cell_begin, cell_begin+n_cells).
+ * Specular walls: the n_cells cells of equal width cover [x_lo, x_hi].
+ * Reservoirs: the first and the last cell are ghost cells just outside
+ * [x_lo, x_hi) (one cell width each), the n_cells - 2 cells between cover
+ * [x_lo, x_hi); res_lo / res_hi give the reservoir density, mean x velocity
+ * and temperature beyond x_lo / x_hi, particle_mass the mass of one particle. */
 typedef struct trmc_domain {
     int32_t cell_begin, n_cells;
     double x_lo, x_hi;
+    int32_t bc;                       /* trmc_bc */
+    int32_t reserved;                 /* must be 0 */
+    double res_lo[3], res_hi[3];      /* reservoir (rho, u_x, T); unused for walls */
+    double particle_mass;             /* unused for walls */
 } trmc_domain;
 
 /* Step statistics, accumulated with integer atomics (device struct, optional). */
@@ -170,17 +183,25 @@ trmc_status trmc_init_cells(trmc_ctx *ctx, trmc_state *state, const double *cell
 trmc_status trmc_collide(trmc_ctx *ctx, trmc_state *state, const trmc_collide_params *params,
                          uint64_t step, int64_t *report_dev, trmc_stats *stats_dev, void *stream);
 
-/* Free transport x += v_x dt with specular walls, then a stable regrouping
- * of the particles by cell (operator splitting, Sec. 3.1).  domains_dev:
+/* Free transport x += v_x dt, boundaries, then a stable regrouping of the
+ * particles by cell (operator splitting, Sec. 3.1).  domains_dev:
  * [n_domains] trmc_domain on the device.  If cfl > 0, dt_dev[d] receives
  * cfl * dx / max|v| over domain d (from state->cell_vmax2, which must be
  * present) and, when state->cell_param is present, cell_param[c].dt is set
  * for every cell of the domain; otherwise dt_dev[d] is read.  Requires
- * dt * max|v_x| <= dx (a particle moves at most one cell).  The sorted
- * particles land in the *_alt arrays and the state's pointers are swapped,
- * so on return state->vx etc. name the sorted arrays. */
+ * dt * max|v_x| <= dx (a particle moves at most one cell).
+ * Reservoir domains: particles that end outside [x_lo, x_hi) are deleted
+ * (outflow, and ghost particles that did not enter); the survivors keep
+ * their order; each ghost cell is then refilled with Iround(rho dx / mass)
+ * particles of the reservoir's Maxwellian, uniform in the ghost cell
+ * (Philox tag RESERVOIR, keyed by step).  The particle count changes: it is
+ * state->cell_start[n_cells] on the device; a count above state->capacity
+ * is reported as TRMC_ERR_CAPACITY by trmc_check (the overflow is dropped).
+ * step keys the reservoir draws (ignored when state->step_dev is set).
+ * The sorted particles land in the *_alt arrays and the state's pointers
+ * are swapped, so on return state->vx etc. name the sorted arrays. */
 trmc_status trmc_transport(trmc_ctx *ctx, trmc_state *state, const trmc_domain *domains_dev,
-                           int32_t n_domains, double cfl, double *dt_dev, void *stream);
+                           int32_t n_domains, double cfl, double *dt_dev, uint64_t step, void *stream);
 
 /* Per-cell moments [n_cells][TRMC_MOM_COLS] doubles on the device:
  * N, rho = N rho_scale, u (3), T, P_xx, M_4 = <|v|^4>, E = <|v|^2>/2, max |v|^2

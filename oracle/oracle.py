@@ -37,9 +37,24 @@ class CollideParams(C.Structure):
                 ("seed", C.c_uint64)]
 
 
+BC_SPECULAR, BC_RESERVOIR = 0, 1
+TAG_RESERVOIR = 9
+
+
 class Domain(C.Structure):
     _fields_ = [("cell_begin", C.c_int32), ("n_cells", C.c_int32),
-                ("x_lo", C.c_double), ("x_hi", C.c_double)]
+                ("x_lo", C.c_double), ("x_hi", C.c_double), ("bc", C.c_int32), ("reserved", C.c_int32),
+                ("res_lo", C.c_double * 3), ("res_hi", C.c_double * 3), ("particle_mass", C.c_double)]
+
+
+def domain(cell_begin, n_cells, x_lo, x_hi, bc=BC_SPECULAR, res_lo=(0, 0, 0), res_hi=(0, 0, 0), particle_mass=0.0):
+    return Domain(cell_begin, n_cells, x_lo, x_hi, bc, 0, (C.c_double * 3)(*res_lo), (C.c_double * 3)(*res_hi),
+                  particle_mass)
+
+
+def _domains(domains):
+    ds = [d if isinstance(d, Domain) else domain(*d) for d in domains]
+    return (Domain * len(ds))(*ds)
 
 
 _lib = None
@@ -60,7 +75,9 @@ def lib():
         _lib.orc_prp_inv.argtypes = [P, C.c_uint64]; _lib.orc_prp_inv.restype = C.c_uint64
         _lib.orc_collide.argtypes = [P, P, P, P, C.c_int32, P, C.c_uint64, C.c_uint64, P, P, P, P, C.c_int]
         _lib.orc_collide_cell.argtypes = [P, P, P, C.c_int64, C.c_uint64, C.c_uint64, C.c_uint64, P, P, P, P]
-        _lib.orc_transport.argtypes = [P, P, P, P, P, C.c_int32, P, C.c_int32, P, P, P, P, P, P]
+        _lib.orc_transport.argtypes = [P, P, P, P, P, C.c_int32, P, C.c_int32, P, P, C.c_uint64, C.c_uint64,
+                                       C.c_uint64, P, P, P, P, C.c_int64, P]
+        _lib.orc_transport.restype = C.c_int64
         _lib.orc_cfl_dt.argtypes = [P, P, P, P, P, C.c_int32, C.c_double, P]
         _lib.orc_init_cells.argtypes = [P, P, C.c_int32, P, C.c_uint64, C.c_uint64, P, P, P, P]
         _lib.orc_moments.argtypes = [P, P, P, P, C.c_int32, P, P]
@@ -139,7 +156,7 @@ def collide(v, cell_start, prm, step, m_state=None, cell_param=None, cell_key=No
 
 
 def cfl_dt(v, cell_start, domains, cfl):
-    doms = (Domain * len(domains))(*[Domain(*d) for d in domains])
+    doms = _domains(domains)
     out = np.zeros(len(domains), np.float64)
     vx, vy, vz = (_c(v[i], np.float64) for i in range(3))
     lib().orc_cfl_dt(_p(vx), _p(vy), _p(vz), _p(_c(cell_start, np.int64)), doms, len(domains),
@@ -147,22 +164,26 @@ def cfl_dt(v, cell_start, domains, cfl):
     return out
 
 
-def transport(x, v, cell_start, domains, dt_dom):
-    """Free transport + specular walls + stable cell sort.
-    domains: list of (cell_begin, n_cells, x_lo, x_hi).  Returns (x, v, cell_start)."""
+def transport(x, v, cell_start, domains, dt_dom, step=0, seed=0, problem_id=0, cell_key=None, capacity=None):
+    """Free transport + boundaries + stable cell sort.  domains: Domain
+    structs or tuples (cell_begin, n_cells, x_lo, x_hi[, bc, res_lo, res_hi,
+    particle_mass]).  Returns (x, v, cell_start) of the new particle set."""
     x = np.array(x, dtype=np.float64, copy=True)
     v = np.array(v, dtype=np.float64, copy=True)
     cs = np.array(cell_start, dtype=np.int64, copy=True)
     nc = len(cs) - 1
-    np_ = int(cs[-1])
-    doms = (Domain * len(domains))(*[Domain(*d) for d in domains])
+    cap = int(capacity if capacity is not None else 2 * int(cs[-1]) + 100000)
+    doms = _domains(domains)
     dt = _c(dt_dom, np.float64)
+    ck = None if cell_key is None else _c(cell_key, np.uint64)
     vx, vy, vz = (np.ascontiguousarray(v[i]) for i in range(3))
-    xo = np.zeros(np_); vxo = np.zeros(np_); vyo = np.zeros(np_); vzo = np.zeros(np_)
+    xo = np.zeros(cap); vxo = np.zeros(cap); vyo = np.zeros(cap); vzo = np.zeros(cap)
     cso = np.zeros(nc + 1, np.int64)
-    lib().orc_transport(_p(x), _p(vx), _p(vy), _p(vz), _p(cs), nc, doms, len(domains), _p(dt),
-                        _p(xo), _p(vxo), _p(vyo), _p(vzo), _p(cso))
-    return xo, np.stack([vxo, vyo, vzo]), cso
+    n = lib().orc_transport(_p(x), _p(vx), _p(vy), _p(vz), _p(cs), nc, doms, len(doms), _p(dt), _p(ck), problem_id,
+                            seed, step, _p(xo), _p(vxo), _p(vyo), _p(vzo), cap, _p(cso))
+    if n < 0:
+        raise ValueError("oracle transport: particle count exceeds capacity")
+    return xo[:n], np.stack([vxo[:n], vyo[:n], vzo[:n]]), cso
 
 
 def init_cells(cell_init, cell_start, seed, problem_id=0, cell_key=None, with_x=True):

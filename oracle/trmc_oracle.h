@@ -30,7 +30,8 @@ extern "C" {
 
 /* Philox counter tags (the fourth counter word carries step, pass and tag). */
 enum { ORC_TAG_INIT = 1, ORC_TAG_SPLIT = 2, ORC_TAG_PARITY = 3, ORC_TAG_KSEL = 4,
-       ORC_TAG_PERM0 = 5, ORC_TAG_PERMK = 6, ORC_TAG_COLL = 7, ORC_TAG_MAXW = 8 };
+       ORC_TAG_PERM0 = 5, ORC_TAG_PERMK = 6, ORC_TAG_COLL = 7, ORC_TAG_MAXW = 8,
+       ORC_TAG_RESERVOIR = 9 };
 
 /* --- random numbers (Salmon et al., SC'11, Philox4x64-10) --------------- */
 void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
@@ -87,16 +88,23 @@ int orc_collide(double *vx, double *vy, double *vz, const int64_t *cell_start,
                 const orc_cell_param *cell_param, int64_t *reports, int n_threads);
 
 /* --- transport + stable cell sort (operator splitting, Sec. 3.1) -------- */
+enum { ORC_BC_SPECULAR = 0, ORC_BC_RESERVOIR = 1 };
 typedef struct {
-    int32_t cell_begin, n_cells;     /* cells [cell_begin, cell_begin+n_cells) */
-    double x_lo, x_hi;               /* specular walls at both ends          */
+    int32_t cell_begin, n_cells;     /* cells [cell_begin, cell_begin+n_cells); with
+                                        reservoirs the first and last are ghost cells */
+    double x_lo, x_hi;               /* walls, or the reservoirs' faces               */
+    int32_t bc, reserved;
+    double res_lo[3], res_hi[3];     /* reservoir rho, u_x, T                         */
+    double particle_mass;
 } orc_domain;
 
-int orc_transport(double *x, double *vx, double *vy, double *vz,
-                  int64_t *cell_start, int32_t n_cells_total,
-                  const orc_domain *dom, int32_t n_dom, const double *dt_dom,
-                  double *x_out, double *vx_out, double *vy_out, double *vz_out,
-                  int64_t *cell_start_out);
+/* Returns the new particle count, or -1 if it would exceed capacity. */
+int64_t orc_transport(double *x, double *vx, double *vy, double *vz,
+                      int64_t *cell_start, int32_t n_cells_total,
+                      const orc_domain *dom, int32_t n_dom, const double *dt_dom,
+                      const uint64_t *cell_key, uint64_t problem_id, uint64_t seed, uint64_t step,
+                      double *x_out, double *vx_out, double *vy_out, double *vz_out, int64_t capacity,
+                      int64_t *cell_start_out);
 /* CFL time step per domain: cfl * dx / max |v| over the domain's particles. */
 void orc_cfl_dt(const double *vx, const double *vy, const double *vz,
                 const int64_t *cell_start, const orc_domain *dom, int32_t n_dom,

@@ -157,7 +157,7 @@ trmc_status trmc_collide(trmc_ctx *ctx, trmc_state *state, const trmc_collide_pa
 }
 
 trmc_status trmc_transport(trmc_ctx *ctx, trmc_state *state, const trmc_domain *domains_dev, int32_t n_domains,
-                           double cfl, double *dt_dev, void *stream)
+                           double cfl, double *dt_dev, uint64_t step, void *stream)
 {
     if (!ctx) return TRMC_ERR_ARG;
     trmc_status r = check_state(ctx, state);
@@ -169,7 +169,7 @@ trmc_status trmc_transport(trmc_ctx *ctx, trmc_state *state, const trmc_domain *
     if (!dt_dev) return set_error(ctx, TRMC_ERR_ARG, "dt_dev is NULL");
     if (cfl > 1.0) return set_error(ctx, TRMC_ERR_ARG, "cfl > 1 would move particles more than one cell");
     if (cfl > 0.0 && !state->cell_vmax2) return set_error(ctx, TRMC_ERR_ARG, "CFL mode needs state.cell_vmax2");
-    return launch_transport(ctx, state, domains_dev, n_domains, cfl, dt_dev, static_cast<cudaStream_t>(stream));
+    return launch_transport(ctx, state, domains_dev, n_domains, cfl, dt_dev, step, static_cast<cudaStream_t>(stream));
 }
 
 trmc_status trmc_moments(trmc_ctx *ctx, const trmc_state *state, double *out_dev, void *stream)

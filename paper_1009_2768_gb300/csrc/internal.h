@@ -41,7 +41,7 @@ trmc_status cuda_error(trmc_ctx *ctx, cudaError_t e, const char *where);
 trmc_status launch_collide(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *prm,
                            uint64_t step, int64_t *report, trmc_stats *stats, cudaStream_t s);
 trmc_status launch_transport(trmc_ctx *ctx, trmc_state *st, const trmc_domain *domains,
-                             int32_t n_domains, double cfl, double *dt, cudaStream_t s);
+                             int32_t n_domains, double cfl, double *dt, uint64_t step, cudaStream_t s);
 trmc_status launch_init(trmc_ctx *ctx, trmc_state *st, const double *cell_init, cudaStream_t s);
 trmc_status launch_moments(trmc_ctx *ctx, const trmc_state *st, double *out, cudaStream_t s);
 

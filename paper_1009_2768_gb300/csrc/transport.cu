@@ -12,6 +12,11 @@
 // cells are recomputed identically in kernels 1 and 3.  In FP64 contexts
 // the position update uses explicitly rounded operations (no contraction),
 // so cells are bit-identical to the CPU oracle's.
+// Reservoir domains (inflow / outflow, Sec. 5.2): the first and last cell
+// are ghost cells outside [x_lo, x_hi).  A particle that ends outside
+// [x_lo, x_hi) is dropped; a ghost cell's "stay" count slot carries the
+// number of particles its reservoir refills it with (kernel 4), so the scan
+// and the scatter need no special case.
 #include <utility>
 
 #include "internal.h"
@@ -21,34 +26,40 @@ namespace trmc {
 namespace {
 
 constexpr int kTT = 256;   // threads per CTA
+constexpr double kTwoPi = 6.283185307179586;
 
-// Position update and new cell (relative to the domain's first cell), double.
+// Position update and new cell (relative to the domain's first cell, -1 if
+// the particle leaves through a reservoir face), double.
 struct Mover64 {
     double lo, hi, dx, dt;
-    int nc;
+    int nc, res;          // interior cells; reservoir domain (ghost cell first)
     __device__ __forceinline__ int move(double &x, double &vx) const
     {
         double xn = __dadd_rn(x, __dmul_rn(vx, dt));
-        if (xn < lo) { xn = __dsub_rn(__dmul_rn(2.0, lo), xn); vx = -vx; }
+        if (res) {
+            if (xn < lo || xn >= hi) return -1;
+        } else if (xn < lo) { xn = __dsub_rn(__dmul_rn(2.0, lo), xn); vx = -vx; }
         else if (xn > hi) { xn = __dsub_rn(__dmul_rn(2.0, hi), xn); vx = -vx; }
         x = xn;
         const double f = floor(__ddiv_rn(__dsub_rn(xn, lo), dx));
         int c = (f < 0.0) ? 0 : (f > double(nc - 1) ? nc - 1 : int(f));
-        return c;
+        return c + res;
     }
 };
 struct Mover32 {
     float lo, hi, inv_dx, dt;
-    int nc;
+    int nc, res;
     __device__ __forceinline__ int move(float &x, float &vx) const
     {
         float xn = x + vx * dt;
-        if (xn < lo) { xn = 2.0f * lo - xn; vx = -vx; }
+        if (res) {
+            if (xn < lo || xn >= hi) return -1;
+        } else if (xn < lo) { xn = 2.0f * lo - xn; vx = -vx; }
         else if (xn > hi) { xn = 2.0f * hi - xn; vx = -vx; }
         x = xn;
         const float f = floorf((xn - lo) * inv_dx);
         int c = (f < 0.0f) ? 0 : (f > float(nc - 1) ? nc - 1 : int(f));
-        return c;
+        return c + res;
     }
 };
 template <typename Real> struct MoverT;
@@ -62,7 +73,13 @@ struct CellDom {
 
 __device__ __forceinline__ bool domain_ok(const trmc_domain &D, int nc_total)
 {
-    return D.n_cells >= 1 && D.cell_begin >= 0 && D.cell_begin <= nc_total - D.n_cells && D.x_hi > D.x_lo;
+    const bool res = D.bc == TRMC_BC_RESERVOIR;
+    return D.n_cells >= (res ? 3 : 1) && D.cell_begin >= 0 && D.cell_begin <= nc_total - D.n_cells &&
+           D.x_hi > D.x_lo && (D.bc == TRMC_BC_SPECULAR || (res && D.particle_mass > 0.0));
+}
+__device__ __forceinline__ int interior_cells(const trmc_domain &D)
+{
+    return D.bc == TRMC_BC_RESERVOIR ? D.n_cells - 2 : D.n_cells;
 }
 
 // Domain of cell c (first valid match); malformed domains are ignored and
@@ -86,16 +103,17 @@ template <>
 __device__ __forceinline__ Mover64 make_mover<double>(const trmc_domain &D, double dt)
 {
     Mover64 m;
-    m.lo = D.x_lo; m.hi = D.x_hi; m.nc = D.n_cells; m.dt = dt;
-    m.dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(D.n_cells));
+    m.lo = D.x_lo; m.hi = D.x_hi; m.nc = interior_cells(D); m.dt = dt; m.res = D.bc == TRMC_BC_RESERVOIR;
+    m.dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(m.nc));
     return m;
 }
 template <>
 __device__ __forceinline__ Mover32 make_mover<float>(const trmc_domain &D, double dt)
 {
     Mover32 m;
-    m.lo = float(D.x_lo); m.hi = float(D.x_hi); m.nc = D.n_cells; m.dt = float(dt);
-    m.inv_dx = float(double(D.n_cells) / (D.x_hi - D.x_lo));
+    m.lo = float(D.x_lo); m.hi = float(D.x_hi); m.nc = interior_cells(D); m.dt = float(dt);
+    m.res = D.bc == TRMC_BC_RESERVOIR;
+    m.inv_dx = float(double(m.nc) / (D.x_hi - D.x_lo));
     return m;
 }
 
@@ -114,7 +132,7 @@ __global__ void cfl_kernel(const trmc_domain *doms, int nd, int nc_total, const 
     double vm = 0.0;
     for (int c = threadIdx.x; c < D.n_cells; c += blockDim.x) vm = fmax(vm, cell_vmax2[D.cell_begin + c]);
     vm = block_max(vm, red);
-    const double dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(D.n_cells));
+    const double dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(interior_cells(D)));
     const double h = (vm > 0.0) ? __ddiv_rn(__dmul_rn(cfl, dx), __dsqrt_rn(vm)) : 0.0;
     if (threadIdx.x == 0) dt[d] = h;
     if (cell_param)
@@ -122,10 +140,28 @@ __global__ void cfl_kernel(const trmc_domain *doms, int nd, int nc_total, const 
 }
 
 // Kernel 1: per old cell, how many particles go left / stay / go right.
+// Particles a ghost cell is refilled with: Iround(rho dx / mass), one
+// uniform (Philox tag RESERVOIR, reserved index).
+__device__ __forceinline__ int64_t refill_count(const trmc_domain &D, int c, const uint64_t *cell_key,
+                                                uint32_t problem_id, uint64_t seed, uint64_t step)
+{
+    const bool lo_side = c == D.cell_begin;
+    const double *r = lo_side ? D.res_lo : D.res_hi;
+    const double dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(D.n_cells - 2));
+    CellRng rng{seed, problem_id, uint64_t(c), step};
+    if (cell_key) { rng.problem = cell_key[c] >> 32; rng.cell = cell_key[c] & 0xFFFFFFFFull; }
+    const double want = __ddiv_rn(__dmul_rn(r[0], dx), D.particle_mass);
+    const double fl = floor(want);
+    const U64x4 w = rng.draw(0xFFFFFFFFull, 2, 0, TAG_RESERVOIR);
+    return int64_t(fl) + ((u01(w.w[0]) < __dsub_rn(want, fl)) ? 1 : 0);
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(kTT) count_kernel(const Real *x, const Real *vx, const int64_t *cs,
                                                     const trmc_domain *doms, int nd, int nc_total, const double *dt,
-                                                    int64_t *counts, int *status)
+                                                    int64_t *counts, int *status, const uint64_t *cell_key,
+                                                    uint32_t problem_id, uint64_t seed, uint64_t step,
+                                                    const uint64_t *step_dev)
 {
     __shared__ CellDom sd;
     __shared__ unsigned long long tot[3];
@@ -139,15 +175,21 @@ __global__ void __launch_bounds__(kTT) count_kernel(const Real *x, const Real *v
         if (threadIdx.x == 0) { counts[3 * c] = 0; counts[3 * c + 1] = e - b; counts[3 * c + 2] = 0; }
         return;
     }
-    const auto mv = make_mover<Real>(doms[sd.d], dt[sd.d]);
+    const trmc_domain D = doms[sd.d];
+    const auto mv = make_mover<Real>(D, dt[sd.d]);
     const int local = c - sd.first;
+    const bool ghost = D.bc == TRMC_BC_RESERVOIR && (local == 0 || local == D.n_cells - 1);
     bool bad = false;
     for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
         Real xi = x[i], vi = vx[i];
-        int d = mv.move(xi, vi) - local;
-        if (d < -1 || d > 1) { bad = true; d = d < 0 ? -1 : 1; }
+        const int nl = mv.move(xi, vi);
+        if (nl < 0) continue;                       // left through a reservoir face
+        int d = nl - local;
+        if (d < -1 || d > 1 || (ghost && d == 0)) { bad = true; d = d < 0 ? -1 : 1; }
         n3[d + 1]++;
     }
+    if (ghost && threadIdx.x == 0)                  // the refill takes the "stay" slot
+        n3[1] = (unsigned long long)refill_count(D, c, cell_key, problem_id, seed, step_dev ? *step_dev : step);
     if (bad) { if (atomicCAS(status, 0, TRMC_ERR_STATE) == 0) status[1] = c; }
     for (int j = 0; j < 3; ++j) {
         unsigned long long v = n3[j];
@@ -164,7 +206,8 @@ __global__ void __launch_bounds__(kTT) count_kernel(const Real *x, const Real *v
 }
 
 // Kernel 2: new cell starts (single CTA, exclusive scan of the new counts).
-__global__ void __launch_bounds__(1024) scan_kernel(const int64_t *counts, int nc, int64_t *new_start)
+__global__ void __launch_bounds__(1024) scan_kernel(const int64_t *counts, int nc, int64_t *new_start,
+                                                    int64_t capacity, int *status)
 {
     __shared__ int64_t wsum[32];
     __shared__ int64_t carry;
@@ -203,7 +246,49 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int64_t *counts, int n
         if (threadIdx.x == blockDim.x - 1) carry = before + incl;
         __syncthreads();
     }
-    if (threadIdx.x == 0) new_start[nc] = carry;
+    if (threadIdx.x == 0) {
+        new_start[nc] = carry;
+        if (carry > capacity && atomicCAS(status, 0, TRMC_ERR_CAPACITY) == 0) status[1] = -1;
+    }
+}
+
+// Kernel 4: refill the ghost cells of reservoir domains from their
+// Maxwellians (one CTA per ghost cell), uniform positions in the cell.
+template <typename Real>
+__global__ void __launch_bounds__(kTT) refill_kernel(const trmc_domain *doms, int nd, int nc_total,
+                                                     const int64_t *new_start, const uint64_t *cell_key,
+                                                     uint32_t problem_id, uint64_t seed, uint64_t step,
+                                                     const uint64_t *step_dev, Real *xo, Real *vxo, Real *vyo,
+                                                     Real *vzo, int64_t capacity, double *cell_vmax2)
+{
+    __shared__ double red[kRedScratch];
+    const int d = blockIdx.x >> 1, side = blockIdx.x & 1;
+    if (d >= nd) return;
+    const trmc_domain D = doms[d];
+    if (D.bc != TRMC_BC_RESERVOIR || !domain_ok(D, nc_total)) return;
+    const int g = side == 0 ? D.cell_begin : D.cell_begin + D.n_cells - 1;
+    const double *r = side == 0 ? D.res_lo : D.res_hi;
+    const double dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(D.n_cells - 2));
+    const double x0 = side == 0 ? __dsub_rn(D.x_lo, dx) : D.x_hi;
+    const double sT = sqrt(r[2]);
+    const uint64_t stp = step_dev ? *step_dev : step;
+    CellRng rng{seed, problem_id, uint64_t(g), stp};
+    if (cell_key) { rng.problem = cell_key[g] >> 32; rng.cell = cell_key[g] & 0xFFFFFFFFull; }
+    const int64_t b = new_start[g], n = new_start[g + 1] - b;
+    double vm = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const U64x4 w = rng.draw(uint64_t(j), 0, 0, TAG_RESERVOIR);
+        const U64x4 w2 = rng.draw(uint64_t(j), 1, 0, TAG_RESERVOIR);
+        const double r1 = sqrt(-2.0 * log(u01_open(w.w[0]))), a1 = kTwoPi * u01(w.w[1]);
+        const double r2 = sqrt(-2.0 * log(u01_open(w.w[2]))), a2 = kTwoPi * u01(w.w[3]);
+        const Real v0 = Real(r[1] + sT * (r1 * cos(a1))), v1 = Real(sT * (r1 * sin(a1))), v2 = Real(sT * (r2 * cos(a2)));
+        const Real xx = Real(__dadd_rn(x0, __dmul_rn(dx, u01(w2.w[0]))));
+        if (b + j < capacity) { xo[b + j] = xx; vxo[b + j] = v0; vyo[b + j] = v1; vzo[b + j] = v2; }
+        const double e0 = v0, e1 = v1, e2 = v2;
+        vm = fmax(vm, __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)));
+    }
+    vm = block_max(vm, red);
+    if (threadIdx.x == 0 && cell_vmax2) cell_vmax2[g] = vm;
 }
 
 // Kernel 3: stable scatter of one old cell into the new order.
@@ -212,7 +297,8 @@ __global__ void __launch_bounds__(kTT) scatter_kernel(const Real *x, const Real 
                                                       const int64_t *cs, const trmc_domain *doms, int nd,
                                                       const double *dt, const int64_t *counts,
                                                       const int64_t *new_start, int nc_total,
-                                                      Real *xo, Real *vxo, Real *vyo, Real *vzo, int *status)
+                                                      Real *xo, Real *vxo, Real *vyo, Real *vzo, int *status,
+                                                      int64_t capacity)
 {
     __shared__ CellDom sd;
     __shared__ int64_t dest[3];
@@ -234,13 +320,15 @@ __global__ void __launch_bounds__(kTT) scatter_kernel(const Real *x, const Real 
     if (sd.d >= 0) { mv = make_mover<Real>(doms[sd.d], dt[sd.d]); local = c - sd.first; }
     for (int64_t chunk = b; chunk < e; chunk += blockDim.x) {
         const int64_t i = chunk + threadIdx.x;
-        const bool live = i < e;
+        bool live = i < e;
         Real xi = 0, vi = 0, yi = 0, zi = 0;
         int d = 0;
         if (live) {
             xi = x[i]; vi = vx[i]; yi = vy[i]; zi = vz[i];
             if (sd.d >= 0) {
-                d = mv.move(xi, vi) - local;
+                const int nl = mv.move(xi, vi);
+                if (nl < 0) live = false;           // left through a reservoir face
+                d = nl - local;
                 d = d < -1 ? -1 : (d > 1 ? 1 : d);
             }
         }
@@ -257,7 +345,7 @@ __global__ void __launch_bounds__(kTT) scatter_kernel(const Real *x, const Real 
             int64_t pos = dest[g];
             for (int w = 0; w < warp; ++w) pos += wcnt[g][w];
             pos += __popc(bal[g] & ((1u << lane) - 1u));
-            xo[pos] = xi; vxo[pos] = vi; vyo[pos] = yi; vzo[pos] = zi;
+            if (pos < capacity) { xo[pos] = xi; vxo[pos] = vi; vyo[pos] = yi; vzo[pos] = zi; }
         }
         __syncthreads();
         if (threadIdx.x < 3) {
@@ -271,7 +359,7 @@ __global__ void __launch_bounds__(kTT) scatter_kernel(const Real *x, const Real 
 
 template <typename Real>
 trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_domain *doms, int32_t nd, double cfl,
-                     double *dt, cudaStream_t s)
+                     double *dt, uint64_t step, cudaStream_t s)
 {
     const int nc = st->n_cells;
     if (ctx->tr_cells < nc) {
@@ -286,13 +374,18 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_domain *doms, int
         cfl_kernel<<<nd, 256, 0, s>>>(doms, nd, nc, st->cell_vmax2, cfl, dt, st->cell_param);
     }
     const Real *x = static_cast<const Real *>(st->x), *vx = static_cast<const Real *>(st->vx);
-    count_kernel<Real><<<nc, kTT, 0, s>>>(x, vx, st->cell_start, doms, nd, nc, dt, ctx->tr_counts, ctx->status);
-    scan_kernel<<<1, 1024, 0, s>>>(ctx->tr_counts, nc, st->cell_start_alt);
+    count_kernel<Real><<<nc, kTT, 0, s>>>(x, vx, st->cell_start, doms, nd, nc, dt, ctx->tr_counts, ctx->status,
+                                          st->cell_key, st->problem_id, ctx->seed, step, st->step_dev);
+    scan_kernel<<<1, 1024, 0, s>>>(ctx->tr_counts, nc, st->cell_start_alt, st->capacity, ctx->status);
     scatter_kernel<Real><<<nc, kTT, 0, s>>>(x, vx, static_cast<const Real *>(st->vy), static_cast<const Real *>(st->vz),
                                             st->cell_start, doms, nd, dt, ctx->tr_counts, st->cell_start_alt, nc,
                                             static_cast<Real *>(st->x_alt), static_cast<Real *>(st->vx_alt),
                                             static_cast<Real *>(st->vy_alt), static_cast<Real *>(st->vz_alt),
-                                            ctx->status);
+                                            ctx->status, st->capacity);
+    refill_kernel<Real><<<2 * nd, kTT, 0, s>>>(doms, nd, nc, st->cell_start_alt, st->cell_key, st->problem_id, ctx->seed,
+                                               step, st->step_dev, static_cast<Real *>(st->x_alt),
+                                               static_cast<Real *>(st->vx_alt), static_cast<Real *>(st->vy_alt),
+                                               static_cast<Real *>(st->vz_alt), st->capacity, st->cell_vmax2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "transport launch");
     std::swap(st->x, st->x_alt);
@@ -306,10 +399,10 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_domain *doms, int
 }  // namespace
 
 trmc_status launch_transport(trmc_ctx *ctx, trmc_state *st, const trmc_domain *doms, int32_t nd, double cfl,
-                             double *dt, cudaStream_t s)
+                             double *dt, uint64_t step, cudaStream_t s)
 {
-    if (ctx->precision == TRMC_FP64) return launch_t<double>(ctx, st, doms, nd, cfl, dt, s);
-    return launch_t<float>(ctx, st, doms, nd, cfl, dt, s);
+    if (ctx->precision == TRMC_FP64) return launch_t<double>(ctx, st, doms, nd, cfl, dt, step, s);
+    return launch_t<float>(ctx, st, doms, nd, cfl, dt, step, s);
 }
 
 }  // namespace trmc

@@ -17,7 +17,7 @@ namespace trmc {
 
 enum Tag : uint32_t {
     TAG_INIT = 1, TAG_SPLIT = 2, TAG_PARITY = 3, TAG_KSEL = 4,
-    TAG_PERM0 = 5, TAG_PERMK = 6, TAG_COLL = 7, TAG_MAXW = 8
+    TAG_PERM0 = 5, TAG_PERMK = 6, TAG_COLL = 7, TAG_MAXW = 8, TAG_RESERVOIR = 9
 };
 
 struct U64x4 { uint64_t w[4]; };

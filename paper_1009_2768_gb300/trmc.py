@@ -54,8 +54,31 @@ class CollideParams(C.Structure):
                 ("m_min", C.c_int32), ("m_cap", C.c_int32), ("indicator", C.c_int32), ("reserved", C.c_int32)]
 
 
+BC_SPECULAR, BC_RESERVOIR = 0, 1
+
+
 class Domain(C.Structure):
-    _fields_ = [("cell_begin", C.c_int32), ("n_cells", C.c_int32), ("x_lo", C.c_double), ("x_hi", C.c_double)]
+    _fields_ = [("cell_begin", C.c_int32), ("n_cells", C.c_int32), ("x_lo", C.c_double), ("x_hi", C.c_double),
+                ("bc", C.c_int32), ("reserved", C.c_int32), ("res_lo", C.c_double * 3), ("res_hi", C.c_double * 3),
+                ("particle_mass", C.c_double)]
+
+
+def domains_tensor(domains, device="cuda"):
+    """Device array of trmc_domain from Domain structs or tuples
+    (cell_begin, n_cells, x_lo, x_hi[, bc, res_lo, res_hi, particle_mass])."""
+    import torch
+    arr = (Domain * len(domains))()
+    for i, d in enumerate(domains):
+        if isinstance(d, Domain):
+            arr[i] = d
+            continue
+        bc = d[4] if len(d) > 4 else BC_SPECULAR
+        rlo = d[5] if len(d) > 5 else (0.0, 0.0, 0.0)
+        rhi = d[6] if len(d) > 6 else (0.0, 0.0, 0.0)
+        mass = d[7] if len(d) > 7 else 0.0
+        arr[i] = Domain(d[0], d[1], d[2], d[3], bc, 0, (C.c_double * 3)(*rlo), (C.c_double * 3)(*rhi), mass)
+    raw = np.frombuffer(bytes(arr), dtype=np.uint8).copy()
+    return torch.as_tensor(raw).to(device)
 
 
 class Stats(C.Structure):
@@ -83,7 +106,7 @@ def load():
         lib.trmc_check.argtypes = [P, P]
         lib.trmc_init_cells.argtypes = [P, C.POINTER(State), P, P]
         lib.trmc_collide.argtypes = [P, C.POINTER(State), C.POINTER(CollideParams), C.c_uint64, P, P, P]
-        lib.trmc_transport.argtypes = [P, C.POINTER(State), P, C.c_int32, C.c_double, P, P]
+        lib.trmc_transport.argtypes = [P, C.POINTER(State), P, C.c_int32, C.c_double, P, C.c_uint64, P]
         lib.trmc_moments.argtypes = [P, C.POINTER(State), P, P]
         lib.trmc_set_collide_launch.argtypes = [P, C.c_int32, C.c_int32]
         lib.trmc_collide_static.argtypes = [C.POINTER(State), C.POINTER(CollideParams), C.c_int32, C.c_uint64,
@@ -141,8 +164,9 @@ def trmc_collide(ctx, state, params, step, report=None, stats=None, stream=None)
                                     _stream(stream)))
 
 
-def trmc_transport(ctx, state, domains, n_domains, cfl, dt, stream=None):
-    code = load().trmc_transport(ctx, C.byref(state.c), _ptr(domains), n_domains, cfl, _ptr(dt), _stream(stream))
+def trmc_transport(ctx, state, domains, n_domains, cfl, dt, step=0, stream=None):
+    code = load().trmc_transport(ctx, C.byref(state.c), _ptr(domains), n_domains, cfl, _ptr(dt), step,
+                                 _stream(stream))
     state.after_transport()
     _raise(ctx, code)
 

@@ -16,9 +16,6 @@ import numpy as np
 from . import synth
 from . import trmc as T
 
-DOMAIN_DTYPE = np.dtype([("b", "i4"), ("n", "i4"), ("lo", "f8"), ("hi", "f8")])
-
-
 def _dev(a):
     import torch
     return torch.as_tensor(np.ascontiguousarray(a)).cuda()
@@ -54,8 +51,7 @@ class ShockTubes:
             self.state.m_max.fill_(m_init)
         self.ctx = T.trmc_create(precision, seed, workspace)
         T.trmc_init_cells(self.ctx, self.state, _dev(ci))
-        doms = np.array([(t * n_cells, n_cells, 0.0, 1.0) for t in range(self.n_tubes)], DOMAIN_DTYPE)
-        self.domains = _dev(doms.view(np.uint8))
+        self.domains = T.domains_tensor([(t * n_cells, n_cells, 0.0, 1.0) for t in range(self.n_tubes)])
         self.dt = torch.zeros(self.n_tubes, dtype=torch.float64, device="cuda")
         self.cfl = cfl
         self.params = T.collide_params(trunc=trunc, m=m_init, indicator=T.IND_PXX)
@@ -67,7 +63,7 @@ class ShockTubes:
         between transport and collide, and after collide."""
         if events:
             events[0].record()
-        T.trmc_transport(self.ctx, self.state, self.domains, self.n_tubes, self.cfl, self.dt)
+        T.trmc_transport(self.ctx, self.state, self.domains, self.n_tubes, self.cfl, self.dt, self.step_index)
         if events:
             events[1].record()
         T.trmc_collide(self.ctx, self.state, self.params, self.step_index, stats=stats)
@@ -75,7 +71,7 @@ class ShockTubes:
             events[2].record()
         self.step_index += 1
 
-    launches_per_step = 5     # cfl, count, scan, scatter, collide
+    launches_per_step = 6     # cfl, count, scan, scatter, refill (no-op for walls), collide
 
     def close(self):
         T.trmc_destroy(self.ctx)
@@ -150,6 +146,77 @@ class BatchedRelaxation:
         self.step_index += 1
 
     launches_per_step = 1
+
+    def close(self):
+        T.trmc_destroy(self.ctx)
+
+
+def rankine_hugoniot(mach, rho_l=1.0, t_l=1.0, gamma=5.0 / 3.0):
+    """Downstream state of a normal shock from the Rankine-Hugoniot relations
+    (Sec. 5.2) for an upstream state moving at Mach `mach` (p = rho T)."""
+    u_l = mach * np.sqrt(gamma * t_l)
+    m2 = mach * mach
+    rho_r = rho_l * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    u_r = rho_l * u_l / rho_r
+    p_r = rho_l * t_l * (2.0 * gamma * m2 - (gamma - 1.0)) / (gamma + 1.0)
+    return (rho_l, u_l, t_l), (rho_r, u_r, p_r / rho_r)
+
+
+class StationaryShock:
+    """1D stationary normal shock on [0,1] (Sec. 5.2): upstream Rankine-
+    Hugoniot state on the left flowing in through a reservoir, downstream
+    state on the right flowing out through the other, initial step at 0.5;
+    hard-sphere VHS, CFL time step, ghost cells at both ends (not collided)."""
+
+    def __init__(self, n_cells=4000, mean_per_cell=2500, mach=3.0, eps=1e-3, precision=T.FP32_MIXED, seed=0,
+                 alpha=1.0, trunc=T.TRUNC_RAD, m_init=2, cfl=0.5, workspace=1 << 30, headroom=1.25):
+        import torch
+        left, right = rankine_hugoniot(mach)
+        self.left, self.right = left, right
+        dx = 1.0 / n_cells
+        n_total = n_cells * mean_per_cell
+        mass = (0.5 * left[0] + 0.5 * right[0]) / n_total           # particle mass
+        self.particle_mass = mass
+        nc = n_cells + 2
+        counts = np.empty(nc, np.int64)
+        ci = np.zeros((nc, T.INIT_COLS))
+        for c in range(nc):
+            xc = (c - 1 + 0.5) * dx
+            rho, u, Tm = left if xc < 0.5 else right
+            counts[c] = int(round(rho * dx / mass))
+            ci[c] = [T.INIT_MAXWELL, u, 0, 0, Tm, 0, 0, (c - 1) * dx, c * dx]
+        cs = synth.starts(counts)
+        self.n_particles = int(cs[-1])
+        cp = np.zeros((nc, 4))
+        cp[:, 0] = eps
+        cp[[0, -1], 0] = 1e300                 # ghost cells: reservoir particles, never collided
+        cp[:, 2] = mass / dx
+        cp[:, 3] = alpha
+        cap = int(headroom * self.n_particles) + 4 * mean_per_cell
+        self.state = T.ParticleState(cs, capacity=cap, precision=precision, with_x=True, rad=trunc == T.TRUNC_RAD,
+                                     cell_param=cp, carry=precision == T.FP32_MIXED)
+        if trunc == T.TRUNC_RAD:
+            self.state.m_max.fill_(m_init)
+        self.ctx = T.trmc_create(precision, seed, workspace)
+        T.trmc_init_cells(self.ctx, self.state, _dev(ci))
+        self.domains = T.domains_tensor([(0, nc, 0.0, 1.0, T.BC_RESERVOIR, left, right, mass)])
+        self.dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        self.cfl = cfl
+        self.params = T.collide_params(trunc=trunc, m=m_init, indicator=T.IND_PXX)
+        self.step_index = 0
+
+    def step(self, stats=None, events=None):
+        if events:
+            events[0].record()
+        T.trmc_transport(self.ctx, self.state, self.domains, 1, self.cfl, self.dt, self.step_index)
+        if events:
+            events[1].record()
+        T.trmc_collide(self.ctx, self.state, self.params, self.step_index, stats=stats)
+        if events:
+            events[2].record()
+        self.step_index += 1
+
+    launches_per_step = 6     # cfl, count, scan, scatter, refill, collide
 
     def close(self):
         T.trmc_destroy(self.ctx)

@@ -50,6 +50,6 @@ def test_struct_layouts_match_header():
     from paper_1009_2768_gb300 import trmc
     assert ctypes.sizeof(trmc.State) == 17 * 8 + 8 + 4 + 4
     assert ctypes.sizeof(trmc.CollideParams) == 6 * 8 + 6 * 4
-    assert ctypes.sizeof(trmc.Domain) == 24
+    assert ctypes.sizeof(trmc.Domain) == 88
     assert ctypes.sizeof(trmc.CellParam) == 32
     assert ctypes.sizeof(trmc.Stats) == 80

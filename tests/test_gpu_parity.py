@@ -164,8 +164,7 @@ def gpu_transport(x, v, cs, doms, dt=None, cfl=0.0, vmax2=None):
     st.set_positions(x)
     if vmax2 is not None:
         st.cell_vmax2.copy_(torch.as_tensor(vmax2))
-    dd = torch.as_tensor(np.array([tuple(d) for d in doms],
-                                  dtype=[("b", "i4"), ("n", "i4"), ("lo", "f8"), ("hi", "f8")]).view(np.uint8)).cuda()
+    dd = T.domains_tensor(doms)
     dtt = torch.as_tensor(np.asarray(dt if dt is not None else np.zeros(len(doms)), np.float64)).cuda()
     c = ctx()
     T.trmc_transport(c, st, dd, len(doms), cfl, dtt)
@@ -261,8 +260,7 @@ def test_shock_tube_chain_parity():
     cso = cs.copy()
     mo = np.full(n_cells, 2, np.int32)
     doms = [(0, n_cells, 0.0, 1.0)]
-    dd = torch.as_tensor(np.array([tuple(d) for d in doms],
-                                  dtype=[("b", "i4"), ("n", "i4"), ("lo", "f8"), ("hi", "f8")]).view(np.uint8)).cuda()
+    dd = T.domains_tensor(doms)
     dtt = torch.zeros(1, dtype=torch.float64, device="cuda")
     p = T.collide_params(trunc=T.TRUNC_RAD, m=2)
     po = oracle_params(O, p)
@@ -294,3 +292,68 @@ def test_collide_parity_deep_continuation_with_tiny_pool():
     cp = np.stack([np.ones(4), np.full(4, 1.8), 1.0 / np.array(counts, float), np.zeros(4)], axis=1)
     g, vo, rep = compare(v, cs, p, step=2, m_state=np.full(4, 32, np.int32), cell_param=cp)
     assert rep[:, 1].max() >= 2 and rep[:, 11].sum() > 0, "expected continuations with depth reductions"
+
+
+# ---------------------------------------------------------------- reservoirs
+def shock_state(n_int, mean, seed):
+    from paper_1009_2768_gb300.workloads import rankine_hugoniot
+    left, right = rankine_hugoniot(3.0)
+    dx = 1.0 / n_int
+    mass = (0.5 * left[0] + 0.5 * right[0]) / (n_int * mean)
+    nc = n_int + 2
+    counts = np.array([int(round((left if (c - 0.5) * dx < 0.5 else right)[0] * dx / mass)) for c in range(nc)])
+    cs = synth.starts(counts)
+    ci = np.zeros((nc, T.INIT_COLS))
+    for c in range(nc):
+        rho, u, Tm = left if (c - 0.5) * dx < 0.5 else right
+        ci[c] = [T.INIT_MAXWELL, u, 0, 0, Tm, 0, 0, (c - 1) * dx, c * dx]
+    dom = (0, nc, 0.0, 1.0, T.BC_RESERVOIR, left, right, mass)
+    return cs, ci, dom, mass
+
+
+def test_reservoir_transport_parity():
+    need_gpu()
+    cs, ci, dom, mass = shock_state(40, 300, seed=16)
+    xo0, vo0 = O.init_cells(ci, cs, 21)
+    cap = int(cs[-1] * 1.5)
+    st = T.ParticleState(cs, capacity=cap, precision=T.FP64, with_x=True)
+    st.set_velocities(vo0)
+    st.set_positions(xo0)
+    c = T.trmc_create(T.FP64, 21, 1 << 20)
+    dd = T.domains_tensor([dom])
+    dt = O.cfl_dt(vo0, cs, [O.domain(*dom)], 0.5)
+    dtt = torch.as_tensor(dt).cuda()
+    T.trmc_transport(c, st, dd, 1, 0.0, dtt, 9)
+    T.trmc_check(c)
+    xo, vo, cso = O.transport(xo0, vo0, cs, [O.domain(*dom)], dt, step=9, seed=21, capacity=cap)
+    n = int(cso[-1])
+    assert np.array_equal(st.cell_start.cpu().numpy(), cso)
+    assert np.array_equal(st.x[:n].cpu().numpy(), xo)
+    g0, g1 = cso[1], cso[-2]                       # refilled ghosts: [0, g0) and [g1, n)
+    vg = st.v[:, :n].cpu().numpy()
+    assert np.array_equal(vg[:, g0:g1], vo[:, g0:g1])                       # moved particles: exact
+    assert np.allclose(vg[:, :g0], vo[:, :g0], rtol=1e-12, atol=1e-12)      # Maxwellian draws: ulps
+    assert np.allclose(vg[:, g1:], vo[:, g1:], rtol=1e-12, atol=1e-12)
+    T.trmc_destroy(c)
+
+
+def test_stationary_shock_keeps_rankine_hugoniot_end_states():
+    """Mach 3 stationary shock (Sec. 5.2): after 300 steps the upstream and
+    downstream thirds still carry the Rankine-Hugoniot states (density ratio
+    3, temperature ratio 11/3, velocity ratio 1/3)."""
+    need_gpu()
+    from paper_1009_2768_gb300.workloads import StationaryShock
+    sim = StationaryShock(n_cells=200, mean_per_cell=400, eps=1e-3, precision=T.FP32_MIXED, seed=2)
+    for _ in range(300):
+        sim.step()
+    T.trmc_check(sim.ctx)
+    mom = torch.zeros((sim.state.n_cells, T.MOM_COLS), dtype=torch.float64, device="cuda")
+    T.trmc_moments(sim.ctx, sim.state, mom)
+    m = mom.cpu().numpy()[1:-1]
+    up, down = m[10:60], m[140:190]
+    (rl, ul, tl), (rr, ur, tr) = sim.left, sim.right
+    assert abs(rr / rl - 3.0) < 1e-12 and abs(tr / tl - 11.0 / 3.0) < 1e-12 and abs(ur / ul - 1.0 / 3.0) < 1e-12
+    assert abs(up[:, 1].mean() / rl - 1) < 0.03 and abs(down[:, 1].mean() / rr - 1) < 0.03
+    assert abs(up[:, 5].mean() / tl - 1) < 0.03 and abs(down[:, 5].mean() / tr - 1) < 0.03
+    assert abs(up[:, 2].mean() / ul - 1) < 0.03 and abs(down[:, 2].mean() / ur - 1) < 0.05
+    sim.close()

@@ -122,3 +122,58 @@ def test_moments_hand_example():
     # |v-U|^2 = 2.75, 0.75, 0.75, 2.75 -> T = 7/12; (v_x-U_x)^2 = 2.25, .25, .25, .25 -> Pxx = 3/4;
     # |v|^2 = 4, 0, 1, 5 -> M4 = 42/4, E = 10/8, max |v|^2 = 5
     assert np.allclose(m[1], [4, 1.0, 0.5, 0.5, 0.5, 7 / 12, 0.75, 10.5, 1.25, 5.0], rtol=1e-15, atol=0)
+
+
+# ---------------------------------------------------------------- reservoirs
+def res_domain(n_int, lo=0.0, hi=1.0, rlo=(1.0, 0.5, 1.0), rhi=(2.0, -0.3, 0.5), mass=1e-3):
+    return O.domain(0, n_int + 2, lo, hi, O.BC_RESERVOIR, rlo, rhi, mass)
+
+
+def test_reservoir_hand_example():
+    # 2 interior cells on [0,1] (dx 0.5) + ghosts [-0.5,0) and [1,1.5); dt = 1
+    d = res_domain(2, rlo=(0.0, 0.0, 1.0), rhi=(0.0, 0.0, 1.0), mass=1.0)    # empty reservoirs: no refill
+    x = np.array([-0.2, -0.4, 0.1, 0.6, 0.9, 1.2])
+    v = np.array([[0.3, 0.1, -0.2, 0.1, 0.2, -0.4], [1, 2, 3, 4, 5, 6], [0, 0, 0, 0, 0, 0.0]])
+    cs = np.array([0, 2, 3, 5, 6])
+    xo, vo, cso = O.transport(x, v, cs, [d], [1.0])
+    # -0.2+0.3=0.1 enters cell 1; -0.4+0.1=-0.3 stays in the ghost: removed; 0.1-0.2=-0.1 leaves: removed;
+    # 0.6+0.1=0.7 and 0.9+0.2=1.1 (leaves: removed); 1.2-0.4=0.8 enters cell 2
+    assert np.array_equal(cso, [0, 0, 1, 3, 3])
+    assert np.allclose(xo, [0.1, 0.7, 0.8], atol=1e-15)
+    assert np.array_equal(vo[1], [1, 4, 6])
+
+
+def test_reservoir_refill_counts_and_law():
+    d = res_domain(4, rlo=(1.0, 0.5, 2.0), rhi=(3.0, -1.0, 0.5), mass=1e-4)   # dx 0.25: 2500 and 7500 expected
+    cs = np.zeros(7, np.int64)
+    xs, vs = [], []
+    for step in range(40):
+        xo, vo, cso = O.transport(np.zeros(0), np.zeros((3, 0)), cs, [d], [0.0], step=step, seed=3)
+        g_lo, g_hi = cso[1] - cso[0], cso[6] - cso[5]
+        assert abs(g_lo - 2500) <= 1 and abs(g_hi - 7500) <= 1      # Iround(rho dx / mass)
+        assert np.all((xo[:g_lo] >= -0.25) & (xo[:g_lo] < 0.0)) and np.all((xo[g_lo:] >= 1.0) & (xo[g_lo:] < 1.25))
+        xs.append(xo[:g_lo]); vs.append(vo[:, :g_lo])
+    v = np.concatenate(vs, axis=1)
+    assert stats.kstest((v[0] - 0.5) / np.sqrt(2.0), "norm").pvalue > 1e-4
+    assert stats.kstest(v[1] / np.sqrt(2.0), "norm").pvalue > 1e-4
+    assert stats.kstest((np.concatenate(xs) + 0.25) / 0.25, "uniform").pvalue > 1e-4
+
+
+def test_reservoir_inflow_is_the_half_range_flux():
+    """Particles entering from a reservoir (rho, u, T) per step: (rho/mass)
+    dt E[max(v_x, 0)] with E[v_x^+] = u Phi(u/sqrt T) + sqrt T phi(u/sqrt T)
+    (uniform positions in the ghost cell, v dt < dx)."""
+    rho, u, T, mass, dt = 1.0, 0.4, 1.0, 2e-5, 0.01
+    d = res_domain(4, rlo=(rho, u, T), rhi=(0.0, 0.0, 1.0), mass=mass)
+    cs = np.zeros(7, np.int64)
+    x, v, cs = O.transport(np.zeros(0), np.zeros((3, 0)), cs, [d], [0.0], step=0, seed=5)    # fill the ghost
+    entered = []
+    for step in range(1, 121):
+        x2, v2, cs2 = O.transport(x, v, cs, [d], [dt], step=step, seed=5)
+        entered.append(cs2[5] - cs2[1])          # interior particles now (the interior started empty)
+        x, v, cs = x2[:cs2[1]], v2[:, :cs2[1]], np.array([0, cs2[1], cs2[1], cs2[1], cs2[1], cs2[1], cs2[1]])
+    s = u / np.sqrt(T)
+    flux = u * stats.norm.cdf(s) + np.sqrt(T) * stats.norm.pdf(s)
+    expect = rho / mass * dt * flux
+    e = np.array(entered, float)
+    assert abs(e.mean() - expect) <= 4 * e.std(ddof=1) / np.sqrt(len(e)), (e.mean(), expect)
