@@ -7,7 +7,7 @@ VHS hard-sphere acceptance, Maxwellian renormalisation, TRMC-RAD) over the
 each, CFL 0.5, FP64.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload shock|batched|bkw]
+                  [--workload shock|batched|bkw|stationary|serving]
 
 --workload selects the step timed (default shock, the benchmark line):
   shock   the four-tube FP64 shock-tube step above;
@@ -15,7 +15,12 @@ each, CFL 0.5, FP64.  Prints one JSON line.
           bi-Maxwellian, VHS alpha 0.6, eps log-uniform 1e-4..10, FP32-mixed;
   bkw     one homogeneous cell of 1e5 Maxwell molecules from BKW data, FP64;
   stationary  Mach 3 stationary shock, 4000 cells x 2500 particles, reservoirs,
-          FP32-mixed.
+          FP32-mixed;
+  serving a stream of solve requests (shock tubes and homogeneous relaxations,
+          1e5..2e7 particles log-uniform, eps 1e-4..1 log-uniform, FP32-mixed)
+          arriving as a Poisson process, swept over --rates requests/s,
+          admitted against a 150 GB HBM budget; reports p50/p99 latency and
+          particle-steps/s per rate (value: the highest rate's throughput).
 
 N > 1 runs N independent replicas (one per rank, launched by torchrun), each
 on its own problem ids; value is the total over ranks.  --impl reference
@@ -172,6 +177,9 @@ WORKLOADS = {
     "bkw": "homogeneous Maxwell molecules, one cell of 1e5 particles, BKW K0 0.6, eps 1, dt 0.05, TRMC-RAD (M4), FP64",
     "stationary": ("1D stationary normal shock, Mach 3, 4000 cells x 2500 particles/cell mean (1e7), hard-sphere "
                    "VHS, eps 1e-3, Rankine-Hugoniot inflow/outflow reservoirs, CFL 0.5, TRMC-RAD, FP32-mixed"),
+    "serving": ("serving stream: Poisson arrivals of shock-tube (500 particles/cell, specular walls) and homogeneous-"
+                "relaxation (cells 64..8192 log-uniform, bi-Maxwellian) solves, 1e5..2e7 particles log-uniform, eps "
+                "1e-4..1 log-uniform, state resident on the device, 150 GB HBM budget, TRMC-RAD, FP32-mixed"),
 }
 
 
@@ -351,6 +359,72 @@ def ours(args):
         dist.destroy_process_group()
 
 
+def serving_bench(args):
+    """Rate sweep of the continuous-batching serving loop.  Every request's
+    latency runs from its arrival to its moments table landing in host
+    memory: set-up of its cell tables (host -> device), its steps, the
+    moments kernel and the copy back."""
+    import torch
+    from paper_1009_2768_gb300 import build, synth
+    from paper_1009_2768_gb300 import trmc as T
+    from paper_1009_2768_gb300.serving import GpuEngine, ServingLoop, requests_from, summary
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    budget = int(args.budget_gb * (1 << 30))
+    eng = GpuEngine(n_slots=args.slots, precision=T.FP32_MIXED, seed=rank, workspace_bytes=512 << 20,
+                    chunk=args.chunk, depth=2)
+    rates = [float(r) for r in args.rates.split(",")]
+    # warm-up: a few small requests through the same engine (allocator, module load, pinned pool)
+    warm = requests_from(synth.poisson_requests(max(args.warmup, 3), 1e4, n_hi=1_000_000, g=synth.rng(99)),
+                         steps=args.req_steps, first_id=1 << 20)
+    ServingLoop(eng, budget - eng.fixed_bytes).run(warm)
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.2)
+    sweep, rid = [], 0
+    t_wall = time.perf_counter()
+    for i, rate in enumerate(rates):
+        n_req = args.requests or int(min(48, max(8, 8 * rate)))
+        reqs = requests_from(synth.poisson_requests(n_req, rate, g=synth.rng(1000 * rank + i)), steps=args.req_steps,
+                             first_id=rid)
+        rid += n_req
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        loop = ServingLoop(eng, budget - eng.fixed_bytes)
+        out = loop.run(reqs)
+        s = summary(out)
+        s.update(rate=rate, requests=n_req, resident_peak_gb=(loop.peak_bytes + eng.fixed_bytes) / 2 ** 30,
+                 torch_peak_gb=torch.cuda.max_memory_allocated() / 2 ** 30,
+                 mean_particles=float(np.mean([r.particles for r in out])),
+                 errors=[r.error for r in out if r.error][:3])
+        sweep.append(s)
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    eng.close()
+    top = sweep[-1]
+    value = top.get("particle_steps_per_s") or 0.0
+    peak, peak_kind = peaks()
+    achieved = value * (12 + 12) / 1e9          # FP32: read v, write (at most) every particle, per particle-step
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.req_steps,
+            "warmup": len(warm), "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 velocities, f64 moments", "data": "synthetic",
+            "config": {"workload": WORKLOADS["serving"], "rates_per_s": rates, "steps_per_request": args.req_steps,
+                       "slots": args.slots, "chunk": args.chunk, "budget_gb": args.budget_gb,
+                       "l2": "requests far larger than L2 on average (mean 3.8e6 particles)",
+                       "parallelism": f"replicas x{world}"},
+            "serving": sweep,
+            "roofline": {"bound": "hbm", "kernel": "all kernels of the served mix", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": None},
+            "cpu_baseline": None,
+            "e2e": {"value": value, "unit": METRIC, "note": "serving is timed end to end (tables in, moments out)",
+                    "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+            "clocks": clk, "wall_s": t_wall}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,12 +434,20 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--workload", default="shock", choices=["shock", "batched", "bkw", "stationary"])
+    ap.add_argument("--workload", default="shock", choices=["shock", "batched", "bkw", "stationary", "serving"])
+    ap.add_argument("--rates", default="1,10,50,200", help="serving: arrival rates (requests/s) to sweep")
+    ap.add_argument("--requests", type=int, default=0, help="serving: requests per rate (default 8*rate in [8, 48])")
+    ap.add_argument("--req-steps", type=int, default=20, help="serving: time steps per request")
+    ap.add_argument("--slots", type=int, default=8, help="serving: concurrent requests (contexts + streams)")
+    ap.add_argument("--chunk", type=int, default=4, help="serving: steps issued per chunk")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: HBM budget (GiB)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "serving":
+        serving_bench(args)
     else:
         ours(args)
 

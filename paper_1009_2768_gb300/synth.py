@@ -67,3 +67,20 @@ def shock_tube_counts(n_cells, mean_per_cell, rho_l=1.0, rho_r=0.125):
     counts[:half] = int(round(w * rho_l))
     counts[half:] = int(round(w * rho_r))
     return counts
+
+
+def poisson_requests(n, rate, n_lo=100_000, n_hi=20_000_000, eps_lo=1e-4, eps_hi=1.0, kinds=("shock", "relax"),
+                     g=None):
+    """A stream of n solve requests: Poisson arrivals at `rate` per second
+    (exponential gaps, first arrival at 0), kind drawn uniformly from
+    `kinds`, particle count log-uniform in [n_lo, n_hi], Knudsen number
+    log-uniform in [eps_lo, eps_hi].  Returns a list of dicts."""
+    g = g or rng(0)
+    gaps = g.exponential(1.0 / rate, n)
+    gaps[0] = 0.0
+    t = np.cumsum(gaps)
+    kind = g.integers(0, len(kinds), n)
+    npart = loguniform_ints(n, n_lo, n_hi, g=g)
+    eps = loguniform(n, eps_lo, eps_hi, g=g)
+    return [dict(arrival=float(t[i]), kind=kinds[kind[i]], n_particles=int(npart[i]), eps=float(eps[i]))
+            for i in range(n)]

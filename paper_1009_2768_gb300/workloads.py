@@ -24,7 +24,7 @@ def _dev(a):
 class ShockTubes:
     def __init__(self, eps_list=(1e-1, 1e-2, 1e-3, 1e-4), n_cells=400, mean_per_cell=500,
                  precision=T.FP64, seed=0, alpha=1.0, trunc=T.TRUNC_RAD, m_init=2, cfl=0.5,
-                 workspace=512 << 20):
+                 workspace=512 << 20, ctx=None, problem_base=0):
         import torch
         self.n_tubes = len(eps_list)
         self.n_cells_tube = n_cells
@@ -39,17 +39,22 @@ class ShockTubes:
         cp[:, 0] = np.repeat(np.asarray(eps_list, float), n_cells)
         cp[:, 2] = rho_scale
         cp[:, 3] = alpha
-        keys = np.array([(t << 32) | c for t in range(self.n_tubes) for c in range(n_cells)], np.uint64)
+        tube = np.repeat(np.arange(self.n_tubes, dtype=np.uint64), n_cells)
+        keys = ((np.uint64(problem_base) + tube) << np.uint64(32)) | np.tile(np.arange(n_cells, dtype=np.uint64),
+                                                                             self.n_tubes)
         ci = np.zeros((nc, T.INIT_COLS))
-        for t in range(self.n_tubes):
-            for c in range(n_cells):
-                ci[t * n_cells + c] = [T.INIT_MAXWELL, 0, 0, 0, 1.0 if c < n_cells // 2 else 0.8, 0, 0,
-                                       c / n_cells, (c + 1) / n_cells]
-        self.state = T.ParticleState(cs, precision=precision, with_x=True, rad=trunc == T.TRUNC_RAD,
-                                     cell_param=cp, cell_key=keys)
+        c = np.tile(np.arange(n_cells), self.n_tubes)
+        ci[:, 0] = T.INIT_MAXWELL
+        ci[:, 4] = np.where(c < n_cells // 2, 1.0, 0.8)
+        ci[:, 7] = c / n_cells
+        ci[:, 8] = (c + 1) / n_cells
+        self.state = T.ParticleState(cs, capacity=self.n_particles, precision=precision, with_x=True,
+                                     rad=trunc == T.TRUNC_RAD, cell_param=cp, cell_key=keys,
+                                     carry=precision == T.FP32_MIXED)
         if trunc == T.TRUNC_RAD:
             self.state.m_max.fill_(m_init)
-        self.ctx = T.trmc_create(precision, seed, workspace)
+        self.own_ctx = ctx is None
+        self.ctx = T.trmc_create(precision, seed, workspace) if ctx is None else ctx
         T.trmc_init_cells(self.ctx, self.state, _dev(ci))
         self.domains = T.domains_tensor([(t * n_cells, n_cells, 0.0, 1.0) for t in range(self.n_tubes)])
         self.dt = torch.zeros(self.n_tubes, dtype=torch.float64, device="cuda")
@@ -74,7 +79,8 @@ class ShockTubes:
     launches_per_step = 6     # cfl, count, scan, scatter, refill (no-op for walls), collide
 
     def close(self):
-        T.trmc_destroy(self.ctx)
+        if self.own_ctx:
+            T.trmc_destroy(self.ctx)
 
 
 class HomogeneousBKW:
@@ -110,9 +116,12 @@ class HomogeneousBKW:
 class BatchedRelaxation:
     def __init__(self, n_cells=4096, lo=64, hi=8192, eps_lo=1e-4, eps_hi=10.0, alpha=0.6, dt=0.05,
                  precision=T.FP32_MIXED, seed=0, trunc=T.TRUNC_RAD, m_init=2, workspace=1 << 30,
-                 order="given"):
+                 order="given", ctx=None, problem_base=0, problem_per_cell=True, counts=None):
         g = synth.rng(seed)
-        counts = synth.loguniform_ints(n_cells, lo, hi, g=g)
+        if counts is None:
+            counts = synth.loguniform_ints(n_cells, lo, hi, g=g)
+        counts = np.asarray(counts, np.int64)
+        n_cells = len(counts)
         eps = synth.loguniform(n_cells, eps_lo, eps_hi, g=g)
         ratio = g.uniform(0.3, 3.0, n_cells)          # T_par / T_perp with T = (T_par + 2 T_perp)/3 = 1
         t_perp = 3.0 / (ratio + 2.0)
@@ -120,12 +129,17 @@ class BatchedRelaxation:
         cs = synth.starts(counts)
         self.n_particles = int(cs[-1])
         cp = np.stack([eps, np.full(n_cells, dt), 1.0 / counts, np.full(n_cells, alpha)], axis=1)
-        keys = np.array([(c << 32) for c in range(n_cells)], np.uint64)     # every cell its own problem
-        self.state = T.ParticleState(cs, precision=precision, rad=trunc == T.TRUNC_RAD, cell_param=cp,
-                                     cell_key=keys)
+        c = np.arange(n_cells, dtype=np.uint64)
+        if problem_per_cell:                  # every cell its own problem
+            keys = (np.uint64(problem_base) + c) << np.uint64(32)
+        else:                                 # one problem, cells numbered within it
+            keys = (np.uint64(problem_base) << np.uint64(32)) | c
+        self.state = T.ParticleState(cs, capacity=self.n_particles, precision=precision, rad=trunc == T.TRUNC_RAD,
+                                     cell_param=cp, cell_key=keys, carry=precision == T.FP32_MIXED)
         if trunc == T.TRUNC_RAD:
             self.state.m_max.fill_(m_init)
-        self.ctx = T.trmc_create(precision, seed, workspace)
+        self.own_ctx = ctx is None
+        self.ctx = T.trmc_create(precision, seed, workspace) if ctx is None else ctx
         ci = np.zeros((n_cells, T.INIT_COLS))
         ci[:, 0] = T.INIT_BIMAXWELL
         ci[:, 4] = t_par
@@ -148,7 +162,8 @@ class BatchedRelaxation:
     launches_per_step = 1
 
     def close(self):
-        T.trmc_destroy(self.ctx)
+        if self.own_ctx:
+            T.trmc_destroy(self.ctx)
 
 
 def rankine_hugoniot(mach, rho_l=1.0, t_l=1.0, gamma=5.0 / 3.0):
