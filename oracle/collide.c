@@ -6,7 +6,8 @@
  * collision sets with Iround), Algorithms 4.3/4.4 (recursive collision trees
  * for Maxwell / VHS molecules, binary collision Eq. Maxwell_coll with sigma
  * from Eq. n3d), the conservative Maxwellian resampling (end of Sec. 4.2) and
- * the adaptive truncation TRMC-RAD (Sec. 4.3).
+ * the adaptive truncation TRMC-RAD (Sec. 4.3) and the shape-dependent
+ * truncation TRMC-WB (Sec. 4.4, Eqs. def:1-3, Algorithms 4.5/4.6).
  *
  * Algorithm 4.3 processes the levels n = m..1 and, whenever a level-n
  * collision needs a sample of f_k (k = 1..n-1), either takes a stored sibling
@@ -189,8 +190,45 @@ static void binary_collision(vec3 a, vec3 b, const uint64_t w[4], double alpha, 
     *accepted = 1;
 }
 
+/* ---- tree lengths (Sec. 4.4) --------------------------------------------- */
+/* Length of a tree of root size k = j + h + 1 from the lengths of its two
+ * subtrees: Eq. def:1 counts the collisions, Eq. def:2 takes 1 + the shorter
+ * subtree, Eq. def:3 1 + their mean.  A sample of f_0 (an original particle)
+ * has length 0. */
+static double tree_len(int def, double Lj, double Lh)
+{
+    if (def == ORC_LEN_K) return 1.0 + Lj + Lh;
+    if (def == ORC_LEN_MIN) return 1.0 + (Lj < Lh ? Lj : Lh);
+    return 1.0 + 0.5 * (Lj + Lh);
+}
+
+/* Algorithm 4.5 read back: the list holds k, then (j, h) of every node in
+ * pre-order; the length is evaluated recursively from the leaves. */
+static double path_len(const int32_t *path, int64_t len, int64_t *idx, int32_t k, int def)
+{
+    if (k == 0) return 0.0;
+    if (*idx + 2 > len) return -1.0;
+    int32_t j = path[*idx], h = path[*idx + 1];
+    *idx += 2;
+    if (j < 0 || h < 0 || j + h + 1 != k) return -1.0;
+    double Lj = path_len(path, len, idx, j, def);
+    if (Lj < 0.0) return -1.0;
+    double Lh = path_len(path, len, idx, h, def);
+    if (Lh < 0.0) return -1.0;
+    return tree_len(def, Lj, Lh);
+}
+
+double orc_tree_length(const int32_t *path, int64_t len, int def)
+{
+    if (len < 1 || path[0] < 0 || def < ORC_LEN_K || def > ORC_LEN_MEAN) return -1.0;
+    int64_t idx = 1;
+    double L = path_len(path, len, &idx, path[0], def);
+    return (L >= 0.0 && idx == len) ? L : -1.0;
+}
+
 typedef struct {
     int64_t coll, dummy, exceed;
+    int64_t wbrej;           /* TRMC-WB: outputs whose tree was too long       */
     /* what the collisions changed: sum over this pass's leaves of
      * (output - original) for v, |v|^2 and the adaptive indicator */
     double dP[3], dE, dS;
@@ -205,7 +243,7 @@ static double indicator(vec3 v, const double U[3], int ind);
 static void run_pass(const plan_t *pl, const keyctx *k, uint32_t pass,
                      const int64_t *part, int64_t n_total, const vec3 *vin, vec3 *vfin,
                      int64_t *pool, double alpha, double Sigma, const double U[3], int ind,
-                     counters_t *cnt)
+                     int wb_def, int wb_mmax, counters_t *cnt)
 {
     int m = pl->m_eff;
     /* Roles: a uniform permutation of the participants (READING: the paper
@@ -228,10 +266,12 @@ static void run_pass(const plan_t *pl, const keyctx *k, uint32_t pass,
     vec3 *prod[MC + 1];
     int64_t *feeder[MC + 1];
     int64_t *outp[MC + 1];
-    for (int n = 0; n <= MC; ++n) { prod[n] = NULL; feeder[n] = NULL; outp[n] = NULL; }
+    double *Lc[MC + 1];      /* TRMC-WB: length of the tree of collision c of level n */
+    for (int n = 0; n <= MC; ++n) { prod[n] = NULL; feeder[n] = NULL; outp[n] = NULL; Lc[n] = NULL; }
     for (int n = 1; n <= m; ++n) {
         int64_t P = 2 * pl->C[n];
         prod[n] = (vec3 *)malloc(sizeof(vec3) * (size_t)(P > 0 ? P : 1));
+        if (wb_def) Lc[n] = (double *)malloc(sizeof(double) * (size_t)(pl->C[n] > 0 ? pl->C[n] : 1));
         feeder[n] = (int64_t *)malloc(sizeof(int64_t) * (size_t)(pl->D[n] > 0 ? pl->D[n] : 1));
         outp[n] = (int64_t *)malloc(sizeof(int64_t) * (size_t)(pl->out[n] > 0 ? pl->out[n] : 1));
         uint64_t kk[4];
@@ -245,16 +285,23 @@ static void run_pass(const plan_t *pl, const keyctx *k, uint32_t pass,
         }
     }
     /* Collision waves, level 1 first: every input of a level-n collision
-     * is either a leaf (k = 0) or a product of a lower level. */
+     * is either a leaf (k = 0) or a product of a lower level.  For TRMC-WB
+     * the length of each collision's tree follows from its inputs' trees
+     * (both products of a collision share the tree). */
     for (int n = 1; n <= m; ++n) {
         for (int64_t c = 0; c < pl->C[n]; ++c) {
             vec3 in[2];
+            double Lin[2];
             for (int s = 0; s < 2; ++s) {
                 int a = (s == 0) ? pl->label[n][c] : (n - 1 - pl->label[n][c]);
                 int64_t sl = pl->slot[s][n][c];
-                if (a == 0) in[s] = vin[leaf[sl]];
-                else in[s] = prod[a][feeder[a][sl]];
+                if (a == 0) { in[s] = vin[leaf[sl]]; Lin[s] = 0.0; }
+                else {
+                    in[s] = prod[a][feeder[a][sl]];
+                    Lin[s] = wb_def ? Lc[a][feeder[a][sl] >> 1] : 0.0;
+                }
             }
+            if (wb_def) Lc[n][c] = tree_len(wb_def, Lin[0], Lin[1]);
             uint64_t w[4];
             draw(k, (uint64_t)c, (uint64_t)n, pass, ORC_TAG_COLL, w);
             int acc, exc;
@@ -264,17 +311,37 @@ static void run_pass(const plan_t *pl, const keyctx *k, uint32_t pass,
             cnt->exceed += exc;
         }
     }
+    /* TRMC-WB (Algorithm 4.6): an output whose tree is longer than m_max is
+     * not kept; the particle it would replace joins the thermalised set,
+     * after the set's own members, in output order.  READING: the trees are
+     * the ones the plan actually built (the plan is fixed before any
+     * collision, so the lengths are known "without performing collisions").
+     * A lone rejected output with no thermalised set is kept: the only
+     * Maxwellian sample with its momentum and energy is the output itself. */
+    int64_t nrej = 0;
+    unsigned char *rej = NULL;
+    if (wb_def) {
+        rej = (unsigned char *)calloc((size_t)(pl->leaves > 0 ? pl->leaves : 1), 1);
+        int64_t jj = 0;
+        for (int n = 1; n <= m; ++n)
+            for (int64_t o = 0; o < pl->out[n]; ++o, ++jj)
+                if (Lc[n][outp[n][o] >> 1] > (double)wb_mmax) { rej[jj] = 1; nrej++; }
+        if (pl->R == 0 && nrej == 1) { memset(rej, 0, (size_t)(pl->leaves > 0 ? pl->leaves : 1)); nrej = 0; }
+    }
+    cnt->wbrej += nrej;
     /* Output j (levels 1..m in order, then by rank) replaces leaf j. */
-    int64_t j = 0;
+    int64_t j = 0, r = 0;
     for (int n = 1; n <= m; ++n)
         for (int64_t o = 0; o < pl->out[n]; ++o) {
+            if (rej && rej[j]) { pool[pl->R + r++] = leaf[j++]; continue; }
             vec3 nv = prod[n][outp[n][o]], ov = vin[leaf[j]];
             cnt->dP[0] += nv.x - ov.x; cnt->dP[1] += nv.y - ov.y; cnt->dP[2] += nv.z - ov.z;
             cnt->dE += (nv.x * nv.x + nv.y * nv.y + nv.z * nv.z) - (ov.x * ov.x + ov.y * ov.y + ov.z * ov.z);
             cnt->dS += indicator(nv, U, ind) - indicator(ov, U, ind);
             vfin[leaf[j++]] = nv;
         }
-    for (int n = 0; n <= MC; ++n) { free(prod[n]); free(feeder[n]); free(outp[n]); }
+    for (int n = 0; n <= MC; ++n) { free(prod[n]); free(feeder[n]); free(outp[n]); free(Lc[n]); }
+    free(rej);
     free(leaf);
 }
 
@@ -345,7 +412,8 @@ int orc_collide_cell(double *vx, double *vy, double *vz, int64_t n,
     int64_t *pool = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     for (int64_t i = 0; i < n; ++i) part[i] = i;
     int64_t n_part = n;
-    counters_t cnt = { 0, 0, 0, { 0.0, 0.0, 0.0 }, 0.0, 0.0 };
+    counters_t cnt = { 0, 0, 0, 0, { 0.0, 0.0, 0.0 }, 0.0, 0.0 };
+    const int wb_def = (prm->trunc == ORC_TRUNC_WB) ? prm->wb_length : 0;
     int m = m0, lo = 0, m_next = m0;
     uint32_t pass = 0;
     int64_t R = 0, leaves_total = 0;
@@ -370,9 +438,10 @@ int orc_collide_cell(double *vx, double *vy, double *vz, int64_t n,
             report[ORC_R_PDROP] += pl.pdrop;
             report[ORC_R_PSURP] += pl.psurp;
         }
-        run_pass(&pl, &k, pass, part, n_part, vin, vfin, pool, alpha, Sigma, U, prm->indicator, &cnt);
+        run_pass(&pl, &k, pass, part, n_part, vin, vfin, pool, alpha, Sigma, U, prm->indicator,
+                 wb_def, prm->m_fixed, &cnt);
         leaves_total += pl.leaves;
-        R = pl.R;
+        R = pl.R + cnt.wbrej;
         plan_free(&pl);
         if (prm->trunc != ORC_TRUNC_RAD) { m_next = m; break; }
 
@@ -484,6 +553,7 @@ int orc_collide_cell(double *vx, double *vy, double *vz, int64_t n,
         report[ORC_R_COLL] = cnt.coll;
         report[ORC_R_DUMMY] = cnt.dummy;
         report[ORC_R_EXCEED] = cnt.exceed;
+        report[ORC_R_WBREJ] = cnt.wbrej;
     }
     free(vin); free(vfin); free(part); free(pool);
     return 0;
@@ -525,6 +595,8 @@ int orc_collide(double *vx, double *vy, double *vz, const int64_t *cell_start,
 {
     if (prm->trunc == ORC_TRUNC_RAD && !m_state) return 1;
     if (prm->m_cap < 1 || prm->m_cap > MC) return 1;
+    if (prm->trunc == ORC_TRUNC_WB &&
+        (prm->wb_length < ORC_LEN_K || prm->wb_length > ORC_LEN_MEAN || prm->m_fixed < 0)) return 1;
     if (n_threads < 1) n_threads = 1;
     job_t *jobs = (job_t *)malloc(sizeof(job_t) * (size_t)n_threads);
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);

@@ -13,7 +13,8 @@ import numpy as np
 from .build import build_oracle
 
 TAG_INIT, TAG_SPLIT, TAG_PARITY, TAG_KSEL, TAG_PERM0, TAG_PERMK, TAG_COLL, TAG_MAXW = range(1, 9)
-TRUNC_FIXED, TRUNC_RAD, TRUNC_UNLIMITED = 0, 1, 2
+TRUNC_FIXED, TRUNC_RAD, TRUNC_UNLIMITED, TRUNC_WB = 0, 1, 2, 3
+LEN_K, LEN_MIN, LEN_MEAN = 1, 2, 3          # tree-length definitions, Eqs. def:1-3
 IND_PXX, IND_M4 = 0, 1
 INIT_MAXWELL, INIT_BIMAXWELL, INIT_BKW = 0, 1, 2
 MCAP = 64
@@ -22,7 +23,7 @@ MOM_COLS = 10
 
 # report layout (int64 per cell)
 R_FIELDS = ["N", "passes", "m_first", "m_last", "m_next", "R_final", "N0", "leaves",
-            "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "reserved"]
+            "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "wbrej"]
 R_NK = 16
 R_CK = 16 + MCAP + 2
 R_DK = 16 + 2 * (MCAP + 2)
@@ -33,7 +34,7 @@ class CollideParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("eps", C.c_double), ("alpha", C.c_double),
                 ("rho_scale", C.c_double), ("delta1", C.c_double), ("delta2", C.c_double),
                 ("trunc", C.c_int32), ("m_fixed", C.c_int32), ("m_min", C.c_int32),
-                ("m_cap", C.c_int32), ("indicator", C.c_int32), ("pad_", C.c_int32),
+                ("m_cap", C.c_int32), ("indicator", C.c_int32), ("wb_length", C.c_int32),
                 ("seed", C.c_uint64)]
 
 
@@ -81,6 +82,8 @@ def lib():
         _lib.orc_cfl_dt.argtypes = [P, P, P, P, P, C.c_int32, C.c_double, P]
         _lib.orc_init_cells.argtypes = [P, P, C.c_int32, P, C.c_uint64, C.c_uint64, P, P, P, P]
         _lib.orc_moments.argtypes = [P, P, P, P, C.c_int32, P, P]
+        _lib.orc_tree_length.argtypes = [P, C.c_int64, C.c_int]
+        _lib.orc_tree_length.restype = C.c_double
     return _lib
 
 
@@ -131,9 +134,20 @@ def prp_table(n, key, inverse=False):
 
 
 def collide_params(dt=0.0, eps=1.0, alpha=0.0, rho_scale=1.0, trunc=TRUNC_FIXED, m=2, m_min=1,
-                   m_cap=MCAP, delta1=0.005, delta2=0.01, indicator=IND_PXX, seed=0):
+                   m_cap=MCAP, delta1=0.005, delta2=0.01, indicator=IND_PXX, seed=0, wb_length=0):
+    """For trunc=TRUNC_WB, m is the shape threshold m_max and wb_length one of LEN_*."""
     return CollideParams(dt, eps, alpha, rho_scale, delta1, delta2, trunc, m, m_min, m_cap,
-                         indicator, 0, seed)
+                         indicator, wb_length, seed)
+
+
+def tree_length(path, definition):
+    """Length of the collision tree stored as Algorithm 4.5's list (k, then
+    (j, h) of every node in pre-order) under definition LEN_K/LEN_MIN/LEN_MEAN."""
+    a = _c(path, np.int32)
+    L = lib().orc_tree_length(_p(a), len(a), definition)
+    if L < 0:
+        raise ValueError("malformed tree list")
+    return L
 
 
 def collide(v, cell_start, prm, step, m_state=None, cell_param=None, cell_key=None,

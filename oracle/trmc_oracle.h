@@ -48,14 +48,16 @@ uint64_t orc_prp_fwd(const orc_prp *p, uint64_t x);
 uint64_t orc_prp_inv(const orc_prp *p, uint64_t y);
 
 /* --- collision step ------------------------------------------------------ */
-enum { ORC_TRUNC_FIXED = 0, ORC_TRUNC_RAD = 1, ORC_TRUNC_UNLIMITED = 2 };
+enum { ORC_TRUNC_FIXED = 0, ORC_TRUNC_RAD = 1, ORC_TRUNC_UNLIMITED = 2, ORC_TRUNC_WB = 3 };
+/* Tree-length definitions of Sec. 4.4: Eq. def:1 (L = k), def:2 (1 + min), def:3 (1 + mean). */
+enum { ORC_LEN_K = 1, ORC_LEN_MIN = 2, ORC_LEN_MEAN = 3 };
 enum { ORC_IND_PXX = 0, ORC_IND_M4 = 1 };
 
 typedef struct {
     double dt, eps, alpha, rho_scale;   /* rho_c = N_c * rho_scale */
     double delta1, delta2;              /* adaptive thresholds (Sec. 4.3) */
     int32_t trunc, m_fixed, m_min, m_cap, indicator;
-    int32_t pad_;
+    int32_t wb_length;                  /* TRMC-WB: ORC_LEN_*; m_fixed is then m_max */
     uint64_t seed;
 } orc_collide_params;
 
@@ -66,12 +68,18 @@ typedef struct { double eps, dt, rho_scale, alpha; } orc_cell_param;
 enum {
     ORC_R_N = 0, ORC_R_PASSES, ORC_R_MFIRST, ORC_R_MLAST, ORC_R_MNEXT, ORC_R_RFINAL,
     ORC_R_N0, ORC_R_LEAVES, ORC_R_COLL, ORC_R_DUMMY, ORC_R_EXCEED, ORC_R_FEAS,
-    ORC_R_PDROP, ORC_R_PSURP, ORC_R_MEFF0, ORC_R_RESERVED,
+    ORC_R_PDROP, ORC_R_PSURP, ORC_R_MEFF0, ORC_R_WBREJ,
     ORC_R_NK = 16,                    /* pass-0 split quotas N_0..N_{MCAP+1}   */
     ORC_R_CK = 16 + ORC_MCAP + 2,     /* pass-0 collisions per level C_0..C_MCAP+1 */
     ORC_R_DK = 16 + 2 * (ORC_MCAP + 2),
     ORC_R_LEN = 16 + 3 * (ORC_MCAP + 2)
 };
+
+/* Length of one collision tree given as the list `path` of Algorithm 4.5:
+ * path[0] = k, then for every node with k > 0, in pre-order, the sizes (j, h)
+ * of its two subtrees (j + h = k - 1).  def is ORC_LEN_*.  Returns -1 if the
+ * list is malformed. */
+double orc_tree_length(const int32_t *path, int64_t len, int def);
 
 /* One cell: v* are the cell's N particles (updated in place). */
 int orc_collide_cell(double *vx, double *vy, double *vz, int64_t n,
