@@ -51,12 +51,22 @@ typedef enum trmc_precision {
                                level probabilities and the renormalisation in double */
 } trmc_precision;
 
-/* Tree truncation (Sec. 4.1 fixed order m, Sec. 4.3 adaptive TRMC-RAD). */
+/* Tree truncation (Sec. 4.1 fixed order m, Sec. 4.3 adaptive TRMC-RAD,
+ * Sec. 4.4 shape-dependent TRMC-WB). */
 typedef enum trmc_trunc {
     TRMC_TRUNC_FIXED = 0,     /* m = params.m_fixed                              */
     TRMC_TRUNC_RAD = 1,       /* m per cell in state.m_max, adapted each step     */
-    TRMC_TRUNC_UNLIMITED = 2  /* m = params.m_cap (depth limited only by N)       */
+    TRMC_TRUNC_UNLIMITED = 2, /* m = params.m_cap (depth limited only by N)       */
+    TRMC_TRUNC_WB = 3         /* split to params.m_cap; an output whose collision tree has
+                                 length L > params.m_fixed (= m_max) is resampled from the
+                                 Maxwellian instead (Alg. 4.6), L per params.wb_length */
 } trmc_trunc;
+
+/* Length of a collision tree of k = j + h + 1 collisions (Sec. 4.4): Eq. def:1
+ * L = k, Eq. def:2 L = 1 + min(L_j, L_h), Eq. def:3 L = 1 + (L_j + L_h) / 2,
+ * with L = 0 for an original particle.  The trees are the ones the step's
+ * plan builds; their lengths are known before any collision is performed. */
+typedef enum trmc_length { TRMC_LEN_K = 1, TRMC_LEN_MIN = 2, TRMC_LEN_MEAN = 3 } trmc_length;
 
 typedef enum trmc_indicator { TRMC_IND_PXX = 0, TRMC_IND_M4 = 1 } trmc_indicator;
 
@@ -109,10 +119,10 @@ typedef struct trmc_collide_params {
     double dt, eps, alpha, rho_scale;  /* for cells without a trmc_cell_param      */
     double delta1, delta2;             /* TRMC-RAD thresholds (Sec. 4.3)            */
     int32_t trunc;                     /* trmc_trunc                                */
-    int32_t m_fixed;                   /* order for TRMC_TRUNC_FIXED                */
+    int32_t m_fixed;                   /* order for TRMC_TRUNC_FIXED; m_max >= 0 for TRMC_TRUNC_WB */
     int32_t m_min, m_cap;              /* TRMC-RAD bounds, 1 <= m_min <= m_cap <= TRMC_MCAP */
     int32_t indicator;                 /* trmc_indicator for TRMC-RAD               */
-    int32_t reserved;                  /* must be 0                                 */
+    int32_t wb_length;                 /* trmc_length for TRMC_TRUNC_WB, else 0       */
 } trmc_collide_params;
 
 typedef enum trmc_bc {
@@ -147,6 +157,7 @@ typedef struct trmc_stats {
     unsigned long long capacity_skips; /* cells skipped: larger than the workspace     */
     unsigned long long changed;      /* particles whose velocity was rewritten         */
     unsigned long long particles;    /* particles in the processed cells               */
+    unsigned long long wb_rejected;  /* TRMC-WB: outputs resampled for a too-long tree  */
 } trmc_stats;
 
 typedef struct trmc_ctx trmc_ctx;
@@ -175,7 +186,8 @@ trmc_status trmc_set_collide_launch(trmc_ctx *ctx, int32_t threads, int32_t ctas
 trmc_status trmc_init_cells(trmc_ctx *ctx, trmc_state *state, const double *cell_init_dev, void *stream);
 
 /* One homogeneous collision step in every cell (Sec. 3.1 splitting, Eq. WST,
- * Alg. 4.2-4.4, conservative Maxwellian resampling, TRMC-RAD of Sec. 4.3).
+ * Alg. 4.2-4.4, conservative Maxwellian resampling, TRMC-RAD of Sec. 4.3,
+ * TRMC-WB of Sec. 4.4).
  * The cell's mass, momentum and energy are conserved to round-off.
  * step keys the random draws.  report_dev (optional) receives
  * [n_cells][TRMC_REPORT_LEN] int64 per-cell plan records; stats_dev

@@ -135,8 +135,14 @@ trmc_status trmc_collide(trmc_ctx *ctx, trmc_state *state, const trmc_collide_pa
     trmc_status r = check_state(ctx, state);
     if (r != TRMC_OK) return r;
     if (!p) return set_error(ctx, TRMC_ERR_ARG, "params is NULL");
-    if (p->reserved != 0) return set_error(ctx, TRMC_ERR_ARG, "params.reserved must be 0");
-    if (p->trunc < TRMC_TRUNC_FIXED || p->trunc > TRMC_TRUNC_UNLIMITED) return set_error(ctx, TRMC_ERR_ARG, "bad trunc");
+    if (p->trunc < TRMC_TRUNC_FIXED || p->trunc > TRMC_TRUNC_WB) return set_error(ctx, TRMC_ERR_ARG, "bad trunc");
+    if (p->trunc == TRMC_TRUNC_WB) {
+        if (p->wb_length < TRMC_LEN_K || p->wb_length > TRMC_LEN_MEAN)
+            return set_error(ctx, TRMC_ERR_ARG, "TRMC-WB needs wb_length in {TRMC_LEN_K, TRMC_LEN_MIN, TRMC_LEN_MEAN}");
+        if (p->m_fixed < 0) return set_error(ctx, TRMC_ERR_ARG, "TRMC-WB needs m_fixed (m_max) >= 0");
+    } else if (p->wb_length != 0) {
+        return set_error(ctx, TRMC_ERR_ARG, "params.wb_length must be 0 unless trunc is TRMC_TRUNC_WB");
+    }
     if (p->m_cap < 1 || p->m_cap > TRMC_MCAP) return set_error(ctx, TRMC_ERR_ARG, "m_cap outside [1, TRMC_MCAP]");
     if (p->trunc == TRMC_TRUNC_FIXED && (p->m_fixed < 1 || p->m_fixed > p->m_cap))
         return set_error(ctx, TRMC_ERR_ARG, "m_fixed outside [1, m_cap]");

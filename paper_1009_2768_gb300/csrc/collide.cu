@@ -22,6 +22,9 @@
 //      change of the indicator with the analytic Maxwellian part and, if
 //      it is too large, continues the split with levels m+1..2m on the
 //      thermalised set, keeping every collision already done;
+//      TRMC-WB (Sec. 4.4) instead splits to m_cap, carries the length of
+//      every product's tree through the waves (Eqs. def:1-3) and sends an
+//      output whose tree is longer than m_max to the thermalised set;
 //   7. the thermalised particles are resampled from the local Maxwellian
 //      and renormalised to the exact momentum and energy they carried;
 //   8. changed particles are written back (coalesced, predicated).
@@ -74,6 +77,7 @@ struct Sh {
     uint8_t lab[NLEV][kPreLabels];   // labels of the first kPreLabels collisions of each level
     int32_t cell, n, m, lo, m_eff, pass, n0, D0, R, npart, m_next, Dge1;
     int32_t n0_prev, D0_prev;
+    int32_t scan[33], nrej;
     int32_t feas, pdrop, psurp, pdrop_tot, psurp_tot, skip, cont, m_top, m_first, n0_first;
     double q, Sigma, U[3], P[3], E, S_pre, dP[3], dE, dS, Pp[3], Ep, Sp, carry[4], Pt[3], Et;
     double alpha, dt, eps, rho_scale;
@@ -84,6 +88,8 @@ struct Sh {
     int32_t *inv[2];
     int32_t *Mt, *St;
     Real *IBuf, *OBuf;
+    double *ILBuf, *OLBuf;           // TRMC-WB: tree length of every consumer slot / output
+    int32_t *ext;                    // TRMC-WB: slots of rejected outputs, appended to the pool
     char *smem_rest, *slab_rest;
     size_t smem_rest_cap, slab_rest_cap;
     char *pass_smem, *pass_slab;
@@ -100,6 +106,30 @@ __device__ __forceinline__ void *take(char *&smem, size_t &scap, char *&slab, si
     if (bytes <= scap) { void *p = smem; smem += bytes; scap -= bytes; return p; }
     if (bytes <= gcap) { void *p = slab; slab += bytes; gcap -= bytes; return p; }
     return nullptr;
+}
+
+// Exclusive prefix count of a per-thread flag over the CTA, in thread order;
+// returns the CTA total.  Every thread of the CTA must call it.
+__device__ __forceinline__ int block_flag_scan(bool flag, int &excl, int32_t *scratch)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const unsigned b = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) scratch[warp] = __popc(b);
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < nw ? scratch[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane < nw) scratch[lane] = v;
+    }
+    __syncthreads();
+    excl = (warp ? scratch[warp - 1] : 0) + __popc(b & ((1u << lane) - 1u));
+    const int total = scratch[nw - 1];
+    __syncthreads();
+    return total;
 }
 
 template <typename Real> struct Math;
@@ -231,7 +261,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         if (m0 > prm.m_cap) m0 = prm.m_cap;
         sh.m = m0; sh.m_next = m0; sh.m_first = m0; sh.lo = 0; sh.pass = 0; sh.npart = n; sh.skip = 0;
         sh.feas = sh.pdrop = sh.psurp = sh.pdrop_tot = sh.psurp_tot = 0;
-        sh.n0_prev = 0; sh.D0_prev = 0;
+        sh.n0_prev = 0; sh.D0_prev = 0; sh.nrej = 0;
         sh.dP[0] = sh.dP[1] = sh.dP[2] = 0.0; sh.dE = 0.0; sh.dS = 0.0;
         for (int j = 0; j < 4; ++j) sh.carry[j] = a.cell_carry ? a.cell_carry[4 * int64_t(cell) + j] : 0.0;
         // persistent layout: V, flags, inv[2]
@@ -469,6 +499,16 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 sh.OBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
                                                    3 * size_t(sh.D0 + 1) * sizeof(Real)));
                 if (!sh.IBuf || !sh.OBuf) sh.skip = 1;
+                sh.ILBuf = sh.OLBuf = nullptr; sh.ext = nullptr;
+                if (prm.trunc == TRMC_TRUNC_WB) {
+                    sh.ILBuf = static_cast<double *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                                                          8 * size_t(sh.Dge1 + 1)));
+                    sh.OLBuf = static_cast<double *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                                                          8 * size_t(sh.D0 + 1)));
+                    sh.ext = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                                                         4 * size_t(sh.D0 + 1)));
+                    if (!sh.ILBuf || !sh.OLBuf || !sh.ext) sh.skip = 1;
+                }
                 // invariants of a consistent plan; a violation would index the
                 // buffers out of range, so the cell is left unchanged instead
                 bool ok = sh.n0 >= 0 && sh.D0 >= 0 && sh.R >= 0 && sh.n0 + sh.D0 + sh.R == npart &&
@@ -519,6 +559,8 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         Real *IBx = sh.IBuf, *IBy = sh.IBuf + (Dge1 + 1), *IBz = sh.IBuf + 2 * (Dge1 + 1);
         Real *OBx = sh.OBuf, *OBy = sh.OBuf + (D0 + 1), *OBz = sh.OBuf + 2 * (D0 + 1);
         const Real alpha = Real(sh.alpha), Sigma = Real(sh.Sigma);
+        const int wb = prm.trunc == TRMC_TRUNC_WB ? prm.wb_length : 0;
+        double *IL = sh.ILBuf, *OL = sh.OLBuf;
         auto level_setup = [&](int lv) {          // warp 0: label prefix and product key
             const int32_t *row = sh.Mt + tri(lv);
             int a0 = lane < lv ? row[lane] : 0, a1 = lane + 32 < lv ? row[lane + 32] : 0;
@@ -580,6 +622,19 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             else { const int q = On + t0 - Dn; OBx[q] = oax; OBy[q] = oay; OBz[q] = oaz; }
             if (t1 < Dn) { const int q = IBn + t1; IBx[q] = obx; IBy[q] = oby; IBz[q] = obz; }
             else { const int q = On + t1 - Dn; OBx[q] = obx; OBy[q] = oby; OBz[q] = obz; }
+            if (wb) {
+                // length of this collision's tree (both products share it), from
+                // its inputs' trees; an original particle has length 0
+                double L;
+                if (wb == TRMC_LEN_K) {
+                    L = double(lv);
+                } else {
+                    const double La = k == 0 ? 0.0 : IL[sh.IB[k] + s0], Lb = j == 0 ? 0.0 : IL[sh.IB[j] + s1];
+                    L = wb == TRMC_LEN_MIN ? 1.0 + (La < Lb ? La : Lb) : __dadd_rn(1.0, __dmul_rn(0.5, __dadd_rn(La, Lb)));
+                }
+                if (t0 < Dn) IL[IBn + t0] = L; else OL[On + t0 - Dn] = L;
+                if (t1 < Dn) IL[IBn + t1] = L; else OL[On + t1 - Dn] = L;
+            }
         };
         bool warp_only = false;      // the last level ran in warp 0 alone
         for (int lv = 1; lv <= m_eff; ++lv) {
@@ -614,7 +669,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         {
             Sum<Real> c0, c1, c2, c3, c4;
             const Real Ux = Real(sh.U[0]);
-            for (int jx = tid; jx < D0; jx += bs) {
+            auto place = [&](int jx) {
                 const int sl = inv[n0 + jx];
                 const Real ox = Vx[sl], oy = Vy[sl], oz = Vz[sl];
                 const Real x = OBx[jx], y = OBy[jx], z = OBz[jx];
@@ -628,13 +683,40 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     c3.add_sq3(x, y, z); c3.sub_sq3(ox, oy, oz);
                     c4.add(indicator_r(x, y, z, Ux, prm.indicator) - indicator_r(ox, oy, oz, Ux, prm.indicator));
                 }
+            };
+            int nrej = 0;
+            if (prm.trunc == TRMC_TRUNC_WB) {
+                // TRMC-WB (Alg. 4.6): an output whose tree is longer than m_max
+                // is not placed; its leaf joins the thermalised set, after the
+                // set's own members, in output order.  A lone rejected output
+                // with no thermalised set is kept: its only Maxwellian
+                // resample with the same momentum and energy is itself.
+                const double mmax = double(prm.m_fixed);
+                const double *OL = sh.OLBuf;
+                bool keep_all = false;
+                if (sh.R == 0) {
+                    int tot = 0;
+                    for (int j0 = 0; j0 < D0; j0 += bs) tot += __syncthreads_count(j0 + tid < D0 && OL[j0 + tid] > mmax);
+                    keep_all = tot == 1;
+                }
+                for (int j0 = 0; j0 < D0; j0 += bs) {
+                    const int jx = j0 + tid;
+                    const bool rj = !keep_all && jx < D0 && OL[jx] > mmax;
+                    int ex;
+                    const int tot = block_flag_scan(rj, ex, sh.scan);
+                    if (rj) sh.ext[nrej + ex] = inv[n0 + jx];
+                    else if (jx < D0) place(jx);
+                    nrej += tot;
+                }
+            } else {
+                for (int jx = tid; jx < D0; jx += bs) place(jx);
             }
             double s[5] = {c0.get(), c1.get(), c2.get(), c3.get(), c4.get()};
             block_sum<5>(s, sh.red);
             Sum<Real> p0, p1, p2, p3, p4;
-            const int pool0 = n0 + D0, R = sh.R;
-            for (int t = tid; t < R; t += bs) {
-                const int sl = inv[pool0 + t];
+            const int pool0 = n0 + D0, R = sh.R, Rx = R + nrej;
+            for (int t = tid; t < Rx; t += bs) {
+                const int sl = t < R ? inv[pool0 + t] : sh.ext[t - R];
                 const Real x = Vx[sl], y = Vy[sl], z = Vz[sl];
                 p0.add(x); p1.add(y); p2.add(z);
                 p3.add_sq3(x, y, z);
@@ -646,6 +728,8 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             if (tid == 0) {
                 sh.dP[0] += s[0]; sh.dP[1] += s[1]; sh.dP[2] += s[2]; sh.dE += s[3]; sh.dS += s[4];
                 sh.Pp[0] = p[0]; sh.Pp[1] = p[1]; sh.Pp[2] = p[2]; sh.Ep = p[3]; sh.Sp = p[4];
+                sh.nrej = nrej;
+                sh.R = Rx;
             }
         }
         // TRMC-RAD test (Sec. 4.3)
@@ -703,15 +787,17 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
     }
 
     // ---- 7. Maxwellian resampling of the thermalised set + renormalisation --
-    const int pass = sh.pass, R = sh.R;
+    const int pass = sh.pass, R = sh.R, R0 = sh.R - sh.nrej;
     const int32_t *inv = sh.inv[pass & 1];
     const int pool0 = sh.n0 + sh.D0;
+    const int32_t *ext = sh.ext;
+    auto pslot = [&](int t) { return t < R0 ? inv[pool0 + t] : ext[t - R0]; };
     if (R >= 2) {
         Sum<Real> q0, q1, q2;
         for (int t = tid; t < R; t += bs) {
             Real z0, z1, z2;
             Math<Real>::normals(rng.draw(uint64_t(t), 0, 0, TAG_MAXW), z0, z1, z2);
-            const int sl = inv[pool0 + t];
+            const int sl = pslot(t);
             Vx[sl] = z0; Vy[sl] = z1; Vz[sl] = z2;
             q0.add(z0); q1.add(z1); q2.add(z2);
         }
@@ -721,7 +807,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         const Real rz0 = Real(zb0), rz1 = Real(zb1), rz2 = Real(zb2);
         Sum<Real> qe;
         for (int t = tid; t < R; t += bs) {
-            const int sl = inv[pool0 + t];
+            const int sl = pslot(t);
             if constexpr (sizeof(Real) == 8) {
                 const double a0 = Vx[sl] - zb0, a1 = Vy[sl] - zb1, a2 = Vz[sl] - zb2;
                 qe.add(a0 * a0 + a1 * a1 + a2 * a2);
@@ -743,7 +829,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         const double u0 = Pt0 / double(R), u1 = Pt1 / double(R), u2 = Pt2 / double(R);
         if constexpr (sizeof(Real) == 8) {
             for (int t = tid; t < R; t += bs) {
-                const int sl = inv[pool0 + t];
+                const int sl = pslot(t);
                 Vx[sl] = u0 + sc * (Vx[sl] - zb0);
                 Vy[sl] = u1 + sc * (Vy[sl] - zb1);
                 Vz[sl] = u2 + sc * (Vz[sl] - zb2);
@@ -753,7 +839,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             // float either way
             const Real fs = Real(sc), f0 = Real(u0), f1 = Real(u1), f2 = Real(u2);
             for (int t = tid; t < R; t += bs) {
-                const int sl = inv[pool0 + t];
+                const int sl = pslot(t);
                 Vx[sl] = f0 + fs * (Vx[sl] - rz0);
                 Vy[sl] = f1 + fs * (Vy[sl] - rz1);
                 Vz[sl] = f2 + fs * (Vz[sl] - rz2);
@@ -767,7 +853,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         if (R >= 2) {
             Sum<Real> r0, r1, r2, r3;
             for (int t = tid; t < R; t += bs) {
-                const int sl = inv[pool0 + t];
+                const int sl = pslot(t);
                 const Real x = Vx[sl], y = Vy[sl], z = Vz[sl];
                 r0.add(x); r1.add(y); r2.add(z);
                 r3.add_sq3(x, y, z);
@@ -806,8 +892,8 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         if (a.report) {
             int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
             r[0] = n; r[1] = sh.pass + 1; r[2] = sh.m_first; r[3] = sh.m; r[4] = sh.m_next; r[5] = R;
-            r[7] = int64_t(n) - r[6] - int64_t(R);
-            r[11] = sh.feas; r[12] = sh.pdrop_tot; r[13] = sh.psurp_tot; r[15] = 0;
+            r[7] = int64_t(n) - r[6] - int64_t(R - sh.nrej);
+            r[11] = sh.feas; r[12] = sh.pdrop_tot; r[13] = sh.psurp_tot; r[15] = sh.nrej;
         }
     }
 }
@@ -849,6 +935,7 @@ __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
                     atomicAdd(&a.stats->cells, 1ull);
                     atomicAdd(&a.stats->changed, (unsigned long long)(sh.n - sh.n0_first));
                     atomicAdd(&a.stats->particles, (unsigned long long)sh.n);
+                    if (sh.nrej) atomicAdd(&a.stats->wb_rejected, (unsigned long long)sh.nrej);
                 }
             }
             __syncthreads();
@@ -957,13 +1044,16 @@ StaticDevice g_static_dev[kMaxDevices];
 
 // Working-set bound of one cell of n particles in the overflow slab: the
 // staged velocities, flags and role tables, the triangular plan tables at the
-// deepest level, and product buffers for up to 4n consumers and n outputs.
-size_t static_cell_bytes(int64_t n, size_t real)
+// deepest level, and product buffers for up to 4n consumers and n outputs
+// (with TRMC-WB also their tree lengths and the rejected outputs' slots).
+size_t static_cell_bytes(int64_t n, size_t real, bool wb)
 {
     auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
     const size_t N = size_t(n), T = size_t(TRMC_MCAP) * (TRMC_MCAP + 1) / 2 + 1;
-    return a16(3 * N * real) + a16(4 * ((N + 31) / 32)) + 2 * a16(4 * N) + 2 * a16(4 * T) +
-           a16(3 * (3 * N + 1) * real) + a16(3 * (N + 1) * real) + 256;
+    size_t b = a16(3 * N * real) + a16(4 * ((N + 31) / 32)) + 2 * a16(4 * N) + 2 * a16(4 * T) +
+               a16(3 * (3 * N + 1) * real) + a16(3 * (N + 1) * real) + 256;
+    if (wb) b += a16(8 * (3 * N + 1)) + a16(8 * (N + 1)) + a16(4 * (N + 1));
+    return b;
 }
 
 template <typename Real>
@@ -990,7 +1080,7 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
     if (cudaFuncSetAttribute(collide_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return TRMC_ERR_CUDA;
     const size_t avail = size_t(TRMC_STATIC_SCRATCH_BYTES) - kStaticControl;
-    const size_t need = static_cell_bytes(max_cell, sizeof(Real));
+    const size_t need = static_cell_bytes(max_cell, sizeof(Real), prm->trunc == TRMC_TRUNC_WB);
     int grid = int(std::min<size_t>(avail / need, size_t(D.num_sms) * per_sm_target));
     if (grid < 1) return TRMC_ERR_CAPACITY;       // a cell of max_cell particles cannot fit the scratch
     if (grid > st->n_cells) grid = st->n_cells;
@@ -1035,7 +1125,10 @@ extern "C" trmc_status trmc_collide_static(trmc_state *state, const trmc_collide
     if (state->n_cells < 0 || (state->n_cells > 0 && (!state->vx || !state->vy || !state->vz || !state->cell_start)))
         return TRMC_ERR_ARG;
     if (max_cell_particles < 0) return TRMC_ERR_ARG;
-    if (p->reserved != 0 || p->trunc < TRMC_TRUNC_FIXED || p->trunc > TRMC_TRUNC_UNLIMITED) return TRMC_ERR_ARG;
+    if (p->trunc < TRMC_TRUNC_FIXED || p->trunc > TRMC_TRUNC_WB) return TRMC_ERR_ARG;
+    if (p->trunc == TRMC_TRUNC_WB ? (p->wb_length < TRMC_LEN_K || p->wb_length > TRMC_LEN_MEAN || p->m_fixed < 0)
+                                  : p->wb_length != 0)
+        return TRMC_ERR_ARG;
     if (p->m_cap < 1 || p->m_cap > TRMC_MCAP) return TRMC_ERR_ARG;
     if (p->trunc == TRMC_TRUNC_FIXED && (p->m_fixed < 1 || p->m_fixed > p->m_cap)) return TRMC_ERR_ARG;
     if (p->trunc == TRMC_TRUNC_RAD && (!state->m_max || p->m_min < 1 || p->m_min > p->m_cap ||

@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(_PKG, "libtrmc.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_CAPACITY, ERR_TIMEOUT, ERR_STATE = range(7)
 FP64, FP32_MIXED = 0, 1
-TRUNC_FIXED, TRUNC_RAD, TRUNC_UNLIMITED = 0, 1, 2
+TRUNC_FIXED, TRUNC_RAD, TRUNC_UNLIMITED, TRUNC_WB = 0, 1, 2, 3
+LEN_K, LEN_MIN, LEN_MEAN = 1, 2, 3
 IND_PXX, IND_M4 = 0, 1
 INIT_MAXWELL, INIT_BIMAXWELL, INIT_BKW = 0, 1, 2
 MCAP = 64
@@ -23,7 +24,7 @@ INIT_COLS = 9
 MOM_COLS = 10
 REPORT_LEN = 16 + 3 * (MCAP + 2)
 REPORT_FIELDS = ["N", "passes", "m_first", "m_last", "m_next", "R_final", "N0", "leaves",
-                 "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "reserved"]
+                 "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "wbrej"]
 EXPORTS = ["trmc_create", "trmc_destroy", "trmc_last_error", "trmc_check", "trmc_init_cells",
            "trmc_collide", "trmc_transport", "trmc_moments", "trmc_collide_static", "trmc_set_collide_launch"]
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -51,7 +52,7 @@ class State(C.Structure):
 class CollideParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("eps", C.c_double), ("alpha", C.c_double), ("rho_scale", C.c_double),
                 ("delta1", C.c_double), ("delta2", C.c_double), ("trunc", C.c_int32), ("m_fixed", C.c_int32),
-                ("m_min", C.c_int32), ("m_cap", C.c_int32), ("indicator", C.c_int32), ("reserved", C.c_int32)]
+                ("m_min", C.c_int32), ("m_cap", C.c_int32), ("indicator", C.c_int32), ("wb_length", C.c_int32)]
 
 
 BC_SPECULAR, BC_RESERVOIR = 0, 1
@@ -84,7 +85,7 @@ def domains_tensor(domains, device="cuda"):
 class Stats(C.Structure):
     _fields_ = [(f, C.c_ulonglong) for f in
                 ("collisions", "dummy", "maxwell", "exceed", "passes", "feas", "cells", "capacity_skips",
-                 "changed", "particles")]
+                 "changed", "particles", "wb_rejected")]
 
 
 STATS_FIELDS = [f for f, _ in Stats._fields_]
@@ -189,8 +190,9 @@ def trmc_collide_static(state, params, precision, seed, step, max_cell_particles
 
 # ---------------------------------------------------------------- helpers
 def collide_params(dt=0.0, eps=1.0, alpha=0.0, rho_scale=1.0, trunc=TRUNC_FIXED, m=2, m_min=1, m_cap=MCAP,
-                   delta1=0.005, delta2=0.01, indicator=IND_PXX):
-    return CollideParams(dt, eps, alpha, rho_scale, delta1, delta2, trunc, m, m_min, m_cap, indicator, 0)
+                   delta1=0.005, delta2=0.01, indicator=IND_PXX, wb_length=0):
+    """trunc=TRUNC_WB: m is the shape threshold m_max and wb_length one of LEN_*."""
+    return CollideParams(dt, eps, alpha, rho_scale, delta1, delta2, trunc, m, m_min, m_cap, indicator, wb_length)
 
 
 class ParticleState:

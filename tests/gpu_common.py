@@ -55,7 +55,7 @@ def gpu_collide(v, cell_start, params, step, precision=T.FP64, seed=0, m_state=N
 def oracle_params(O, p):
     return O.collide_params(dt=p.dt, eps=p.eps, alpha=p.alpha, rho_scale=p.rho_scale, trunc=p.trunc, m=p.m_fixed,
                             m_min=p.m_min, m_cap=p.m_cap, delta1=p.delta1, delta2=p.delta2, indicator=p.indicator,
-                            seed=0)
+                            seed=0, wb_length=p.wb_length)
 
 
 def assert_velocity_parity(v_gpu, v_orc, cell_start, tol=TOL_V):

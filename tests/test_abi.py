@@ -52,4 +52,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(trmc.CollideParams) == 6 * 8 + 6 * 4
     assert ctypes.sizeof(trmc.Domain) == 88
     assert ctypes.sizeof(trmc.CellParam) == 32
-    assert ctypes.sizeof(trmc.Stats) == 80
+    assert ctypes.sizeof(trmc.Stats) == 88

@@ -57,6 +57,33 @@ def test_collide_parity(alpha, eps, trunc, m):
     compare(v, cs, p, step=7, m_state=ms)
 
 
+@pytest.mark.parametrize("length", [T.LEN_K, T.LEN_MIN, T.LEN_MEAN])
+@pytest.mark.parametrize("m_max", [0, 1, 2, 5])
+@pytest.mark.parametrize("alpha,eps", [(0.0, 1e-3), (1.0, 0.05), (0.6, 1.0), (1.0, 1e-4)])
+def test_collide_parity_wb(length, m_max, alpha, eps):
+    """TRMC-WB (Sec. 4.4): same tree lengths, same rejected outputs, same
+    extended thermalised set as the oracle."""
+    v, cs = cells(COUNTS, seed=40 + 7 * length + m_max)
+    p = T.collide_params(dt=0.05, eps=eps, alpha=alpha, rho_scale=1.0 / 500, trunc=T.TRUNC_WB, m=m_max,
+                         wb_length=length)
+    g, vo, rep = compare(v, cs, p, step=5)
+    if m_max == 0:      # every output is rejected but a lone one with no thermalised set
+        lone = (rep[:, 5] - rep[:, 15] == 0) & (rep[:, 7] == 1)
+        assert np.array_equal(rep[:, 15], np.where(lone, 0, rep[:, 7]))
+
+
+def test_collide_parity_wb_large_cells():
+    """Deep trees (q near 1/2 over many levels) in cells that run from the
+    overflow slab; enough rejections under every definition."""
+    counts = [20000, 9000, 30000]
+    v, cs = cells(counts, seed=44)
+    for length, m_max in ((T.LEN_MIN, 2), (T.LEN_MEAN, 2), (T.LEN_K, 3)):
+        p = T.collide_params(dt=0.7, eps=1.0, alpha=0.0, rho_scale=1.0 / np.array(counts).mean(), trunc=T.TRUNC_WB,
+                             m=m_max, wb_length=length)
+        g, vo, rep = compare(v, cs, p, step=2, workspace=512 << 20)
+        assert rep[:, 15].sum() > 50
+
+
 def test_collide_parity_rad_continuations():
     # far from equilibrium and a long step: several TRMC-RAD passes per cell
     v, cs = cells([300, 1200, 3000], seed=3)
