@@ -78,6 +78,8 @@ struct Sh {
     int32_t cell, n, m, lo, m_eff, pass, n0, D0, R, npart, m_next, Dge1;
     int32_t n0_prev, D0_prev;
     int32_t scan[33], nrej;
+    uint32_t coin[3];                // parity coin of level lv: bit lv (uP[lv] < 1/2)
+    int32_t cand[4], cand_ok[4], cand_next;
     int32_t feas, pdrop, psurp, pdrop_tot, psurp_tot, skip, cont, m_top, m_first, n0_first;
     double q, Sigma, U[3], P[3], E, S_pre, dP[3], dE, dS, Pp[3], Ep, Sp, carry[4], Pt[3], Et;
     double alpha, dt, eps, rho_scale;
@@ -89,6 +91,14 @@ struct Sh {
     int32_t *Mt, *St;
     Real *IBuf, *OBuf;
     double *ILBuf, *OLBuf;           // TRMC-WB: tree length of every consumer slot / output
+    // deep levels (at most kWarpLevel collisions) in ascending order, the
+    // offset of their collisions in the per-collision records, and the records:
+    // exclusive label prefix per level (triangular rows), input and output
+    // locations, acceptance threshold xi*Sigma and scattering direction
+    int32_t WL[NLEV], WB[NLEV + 1], nWL;
+    int32_t *LP;
+    int2 *psrc, *pdst;
+    Real *prnd;
     int32_t *ext;                    // TRMC-WB: slots of rejected outputs, appended to the pool
     char *smem_rest, *slab_rest;
     size_t smem_rest_cap, slab_rest_cap;
@@ -373,54 +383,14 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         int32_t *fwd = sh.inv[1];                       // pass 0: pi(i) of every slot, for the change flags
         const int poolp = sh.n0_prev + sh.D0_prev;
 
-        // 2-3. Warp 0 draws the split (Alg. 4.2) and builds the tree plan with
-        //      warp-level synchronisation only; warps 1.. meanwhile compute the
-        //      role permutation of the participants, which the plan does not
-        //      change (only where its ranks are cut into roles).
-        if (warp == 0) {
-            {
-                const int lo = sh.lo, m = sh.m;
-                for (int t = lane; t <= m - lo; t += 32)
-                    sh.uS[lo + t] = u01(rng.draw(uint64_t(lo + t), 0, uint32_t(pass), TAG_SPLIT).w[0]);
-                for (int t = lane; t < m; t += 32) {
-                    sh.uP[t + 1] = u01(rng.draw(uint64_t(t + 1), 0, uint32_t(pass), TAG_PARITY).w[0]);
-                    sh.keys[t + 1] = rng.draw(0, uint64_t(t + 1), uint32_t(pass), TAG_PERMK);
-                }
-                // the first kPreLabels labels of every level, off the plan's critical path
-                for (int t = lane; t < m * (kPreLabels / 4); t += 32) {
-                    const int lv = 1 + t / (kPreLabels / 4), g = t % (kPreLabels / 4);
-                    const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) sh.lab[lv][4 * g + j] = uint8_t(below(w.w[j], uint32_t(lv)));
-                }
-            }
-            __syncwarp();
-            if (lane == 0) {
-                for (int j = 0; j < NLEV; ++j) sh.Nq[j] = 0;
-                int rem = npart, m_eff = sh.m;
-                for (int lv = sh.lo; lv <= sh.m; ++lv) {
-                    const double x = sh.q * double(rem);
-                    const double fl = floor(x);
-                    const int c = int(fl) + ((sh.uS[lv] < x - fl) ? 1 : 0);
-                    sh.Nq[lv] = c;
-                    rem -= c;
-                    if (rem == 0) { m_eff = lv; break; }
-                }
-                if (rem > 0) sh.Nq[sh.m + 1] = rem;
-                sh.m_eff = m_eff;
-                sh.m_top = m_eff;
-                sh.pass_smem = sh.smem_rest; sh.pass_smem_cap = sh.smem_rest_cap;
-                sh.pass_slab = sh.slab_rest; sh.pass_slab_cap = sh.slab_rest_cap;
-                const size_t T = size_t(tri(m_eff + 1));
-                sh.Mt = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
-                sh.St = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
-                if (!sh.Mt || !sh.St) sh.skip = 1;
-            }
-            __syncwarp();
+        // One attempt of the tree plan (warp 0) on depth sh.m_top, then, if the
+        // trees find enough leaves, the layout of the pass's buffers; otherwise
+        // sh.cont is set and sh.m_top holds the next depth to try.
+        auto plan_attempt = [&]() {
             // Tree plan, top level first, with the leaf-feasibility loop.  Levels
             // with neither quota nor demand have no collision and are skipped;
             // Nn is read-only below because every lane reads it to skip.
-            while (!sh.skip) {
+            if (!sh.skip) {
                 for (int j = lane; j < NLEV; j += 32) {
                     sh.D[j] = 0; sh.C[j] = 0; sh.out[j] = 0;
                     sh.Nn[j] = (j <= sh.m_top) ? sh.Nq[j] : 0;
@@ -434,7 +404,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     if (lane == 0) {
                         int T = sh.Nn[lv] + sh.D[lv];
                         if (T & 1) {
-                            if (sh.Nn[lv] >= 1 && sh.uP[lv] < 0.5) { T -= 1; sh.pdrop++; }
+                            if (sh.Nn[lv] >= 1 && ((sh.coin[lv >> 5] >> (lv & 31)) & 1u)) { T -= 1; sh.pdrop++; }
                             else { T += 1; sh.psurp++; }
                         }
                         sh.C[lv] = T >> 1;
@@ -483,10 +453,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     }
                 }
                 __syncwarp();
-                if (!sh.cont) break;
             }
             // layout of the product buffers; output / input offsets
-            if (lane == 0 && !sh.skip) {
+            if (lane == 0 && !sh.skip && !sh.cont) {
                 const int m = sh.m_top;
                 sh.pdrop_tot += sh.pdrop;
                 sh.psurp_tot += sh.psurp;
@@ -509,6 +478,27 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                                                          4 * size_t(sh.D0 + 1)));
                     if (!sh.ILBuf || !sh.OLBuf || !sh.ext) sh.skip = 1;
                 }
+                // records of the deep levels' collisions; without room for them
+                // the waves compute everything in place (same results)
+                int w = 0;
+                sh.nWL = 0;
+                for (int lv = 1; lv <= m; ++lv)
+                    if (sh.C[lv] > 0 && sh.C[lv] <= kWarpLevel) { sh.WL[sh.nWL] = lv; sh.WB[sh.nWL++] = w; w += sh.C[lv]; }
+                sh.WB[sh.nWL] = w;
+                if (w > 0) {
+                    char *s0 = sh.pass_smem, *g0 = sh.pass_slab;
+                    const size_t sc0 = sh.pass_smem_cap, gc0 = sh.pass_slab_cap;
+                    sh.LP = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                                                        4 * size_t(tri(m + 1) + 1)));
+                    sh.psrc = static_cast<int2 *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 8 * size_t(w)));
+                    sh.pdst = static_cast<int2 *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 8 * size_t(w)));
+                    sh.prnd = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                                                       4 * size_t(w) * sizeof(Real)));
+                    if (!sh.LP || !sh.psrc || !sh.pdst || !sh.prnd) {
+                        sh.pass_smem = s0; sh.pass_slab = g0; sh.pass_smem_cap = sc0; sh.pass_slab_cap = gc0;
+                        sh.nWL = 0;
+                    }
+                }
                 // invariants of a consistent plan; a violation would index the
                 // buffers out of range, so the cell is left unchanged instead
                 bool ok = sh.n0 >= 0 && sh.D0 >= 0 && sh.R >= 0 && sh.n0 + sh.D0 + sh.R == npart &&
@@ -527,6 +517,60 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     }
                 }
             }
+            __syncwarp();
+        };
+        // 2-3. Warp 0 draws the split (Alg. 4.2) and builds the tree plan with
+        //      warp-level synchronisation only; warps 1.. meanwhile compute the
+        //      role permutation of the participants, which the plan does not
+        //      change (only where its ranks are cut into roles).
+        if (warp == 0) {
+            {
+                const int lo = sh.lo, m = sh.m;
+                for (int t = lane; t <= m - lo; t += 32)
+                    sh.uS[lo + t] = u01(rng.draw(uint64_t(lo + t), 0, uint32_t(pass), TAG_SPLIT).w[0]);
+                for (int t = lane; t < m; t += 32) {
+                    sh.uP[t + 1] = u01(rng.draw(uint64_t(t + 1), 0, uint32_t(pass), TAG_PARITY).w[0]);
+                    sh.keys[t + 1] = rng.draw(0, uint64_t(t + 1), uint32_t(pass), TAG_PERMK);
+                }
+                // the first kPreLabels labels of every level, off the plan's critical path
+                for (int t = lane; t < m * (kPreLabels / 4); t += 32) {
+                    const int lv = 1 + t / (kPreLabels / 4), g = t % (kPreLabels / 4);
+                    const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sh.lab[lv][4 * g + j] = uint8_t(below(w.w[j], uint32_t(lv)));
+                }
+            }
+            __syncwarp();
+            // the parity coins as bits: the plan then needs no FP64 compare
+            for (int t0 = 0; t0 < NLEV; t0 += 32) {
+                const int lv = t0 + lane;
+                const unsigned b = __ballot_sync(0xffffffffu, lv >= 1 && lv <= sh.m && sh.uP[lv] < 0.5);
+                if (lane == 0) sh.coin[t0 >> 5] = b;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                for (int j = 0; j < NLEV; ++j) sh.Nq[j] = 0;
+                int rem = npart, m_eff = sh.m;
+                for (int lv = sh.lo; lv <= sh.m; ++lv) {
+                    const double x = sh.q * double(rem);
+                    const double fl = floor(x);
+                    const int c = int(fl) + ((sh.uS[lv] < x - fl) ? 1 : 0);
+                    sh.Nq[lv] = c;
+                    rem -= c;
+                    if (rem == 0) { m_eff = lv; break; }
+                }
+                if (rem > 0) sh.Nq[sh.m + 1] = rem;
+                sh.m_eff = m_eff;
+                sh.m_top = m_eff;
+                sh.pass_smem = sh.smem_rest; sh.pass_smem_cap = sh.smem_rest_cap;
+                sh.pass_slab = sh.slab_rest; sh.pass_slab_cap = sh.slab_rest_cap;
+                const size_t T = size_t(tri(m_eff + 1));
+                sh.Mt = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
+                sh.St = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
+                if (!sh.Mt || !sh.St) sh.skip = 1;
+            }
+            __syncwarp();
+            plan_attempt();
         }
         // 4. roles: a permutation of the participants (warps 1.., or warp 0
         //    afterwards when the CTA is a single warp)
@@ -541,6 +585,75 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             }
         }
         __syncthreads();
+        if (!sh.skip && sh.cont) {
+            // The first plan needs more leaves than the participants can give.
+            // The rule then lowers the depth to just below one quota level
+            // after another; those depths follow from the quotas alone, so up
+            // to four warps test the next ones at once (feasibility only), and
+            // warp 0 then plans the first feasible one in full.
+            const int nsw = (bs >> 5) < 4 ? (bs >> 5) : 4;
+            auto feasible_at = [&](int ct) -> bool {
+                int32_t *Dw = reinterpret_cast<int32_t *>(sh.red) + warp * 130, *rw = Dw + NLEV;
+                for (int j = lane; j < NLEV; j += 32) Dw[j] = 0;
+                __syncwarp();
+                int lv = ct;
+                while (lv >= 1 && sh.Nq[lv] + Dw[lv] == 0) --lv;
+                while (lv >= 1) {
+                    int T = sh.Nq[lv] + Dw[lv];
+                    if (T & 1) T += (sh.Nq[lv] >= 1 && ((sh.coin[lv >> 5] >> (lv & 31)) & 1u)) ? -1 : 1;
+                    const int Cn = T >> 1;
+                    for (int k = lane; k < lv; k += 32) rw[k] = 0;
+                    __syncwarp();
+                    for (int c = lane; c < Cn && c < kPreLabels; c += 32) atomicAdd(&rw[sh.lab[lv][c]], 1);
+                    for (int g = kPreLabels / 4 + lane; g < (Cn + 3) >> 2; g += 32) {
+                        const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (4 * g + j < Cn) atomicAdd(&rw[below(w.w[j], uint32_t(lv))], 1);
+                    }
+                    __syncwarp();
+                    for (int k = lane; k < lv; k += 32) Dw[k] += rw[k] + rw[lv - 1 - k];
+                    __syncwarp();
+                    --lv;
+                    while (lv >= 1 && sh.Nq[lv] + Dw[lv] == 0) --lv;
+                }
+                const int n0q = sh.Nq[0], A = npart - n0q, d0 = Dw[0];
+                return d0 <= A || d0 - A <= n0q;
+            };
+            while (sh.cont) {
+                if (tid == 0) {
+                    int c = sh.m_top;
+                    for (int w = 0; w < nsw; ++w) sh.cand[w] = -1;
+                    for (int w = 0; w < nsw; ++w) {
+                        sh.cand[w] = c;
+                        if (c == 0) break;                 // depth 0 needs no leaf: always feasible
+                        int h = c;
+                        while (h >= 1 && sh.Nq[h] == 0) --h;
+                        c = (h >= 1 ? h : 1) - 1;
+                    }
+                    sh.cand_next = c;
+                }
+                __syncthreads();
+                if (warp < nsw) {
+                    const int ct = sh.cand[warp];
+                    const bool ok = ct >= 0 && feasible_at(ct);
+                    if (lane == 0) sh.cand_ok[warp] = ok ? 1 : 0;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    int chosen = -1;
+                    for (int w = 0; w < nsw; ++w)
+                        if (sh.cand[w] >= 0 && sh.cand_ok[w]) { chosen = sh.cand[w]; break; }
+                    const int next = chosen >= 0 ? chosen : sh.cand_next;
+                    sh.feas += sh.m_top - next;
+                    sh.m_top = next;
+                    sh.cont = chosen >= 0 ? 0 : 1;
+                }
+                __syncthreads();
+            }
+            if (warp == 0) plan_attempt();
+            __syncthreads();
+        }
         if (sh.skip) break;
         const int m_eff = sh.m_eff, n0 = sh.n0, D0 = sh.D0, Dge1 = sh.Dge1;
         if (pass == 0) {
@@ -636,13 +749,127 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 if (t1 < Dn) IL[IBn + t1] = L; else OL[On + t1 - Dn] = L;
             }
         };
+        // 5a. The deep levels run one after the other in warp 0, mostly with a
+        //     few collisions each, so their latency is the cell's critical
+        //     path.  Everything of their collisions that does not depend on
+        //     the inputs -- label, input and output locations, the draw, the
+        //     acceptance threshold and the scattering direction -- is computed
+        //     first by the whole CTA; a deep level then only loads its inputs,
+        //     collides and stores.
+        const int nWL = sh.nWL;
+        if (nWL > 0) {
+            const int nw = bs >> 5;
+            for (int jl = warp; jl < nWL; jl += nw) {
+                const int lv = sh.WL[jl];
+                const int32_t *row = sh.Mt + tri(lv);
+                int32_t *pr = sh.LP + tri(lv);
+                const int r0 = lane < lv ? row[lane] : 0, r1 = lane + 32 < lv ? row[lane + 32] : 0;
+                int a0 = r0, a1 = r1;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t0 = __shfl_up_sync(0xffffffffu, a0, o), t1 = __shfl_up_sync(0xffffffffu, a1, o);
+                    if (lane >= o) { a0 += t0; a1 += t1; }
+                }
+                a1 += __shfl_sync(0xffffffffu, a0, 31);
+                if (lane < lv) pr[lane] = a0 - r0;
+                if (lane + 32 < lv) pr[lane + 32] = a1 - r1;
+            }
+            __syncthreads();
+            const int W = sh.WB[nWL];
+            for (int i = tid; i < W; i += bs) {
+                int lo_ = 0, hi_ = nWL - 1;
+                while (lo_ < hi_) {
+                    const int mid = (lo_ + hi_ + 1) >> 1;
+                    if (sh.WB[mid] <= i) lo_ = mid; else hi_ = mid - 1;
+                }
+                const int lv = sh.WL[lo_], c = i - sh.WB[lo_];
+                const int32_t *row = sh.Mt + tri(lv), *srow = sh.St + tri(lv), *pr = sh.LP + tri(lv);
+                int ka = 0, kb = lv - 1;
+                while (ka < kb) {
+                    const int mid = (ka + kb + 1) >> 1;
+                    if (pr[mid] <= c) ka = mid; else kb = mid - 1;
+                }
+                const int k = ka, j = lv - 1 - k, off = c - pr[k];
+                const int s0 = srow[k] + off, s1 = srow[j] + row[j] + off;
+                int2 sr, ds;
+                sr.x = k == 0 ? ~inv[n0 + s0] : sh.IB[k] + s0;
+                sr.y = j == 0 ? ~inv[n0 + s1] : sh.IB[j] + s1;
+                Perm pk;
+                pk.init(uint32_t(2 * sh.C[lv]), sh.keys[lv]);
+                const int t0 = int(pk.fwd(uint32_t(2 * c))), t1 = int(pk.fwd(uint32_t(2 * c + 1)));
+                const int Dn = sh.D[lv];
+                ds.x = t0 < Dn ? sh.IB[lv] + t0 : ~(sh.O[lv] + t0 - Dn);
+                ds.y = t1 < Dn ? sh.IB[lv] + t1 : ~(sh.O[lv] + t1 - Dn);
+                const U64x4 w = rng.draw(uint64_t(c), uint64_t(lv), uint32_t(pass), TAG_COLL);
+                const Real xs = alpha != Real(0) ? Math<Real>::uni(w.w[0]) * Sigma : Real(0);
+                const Real ct = Real(2) * Math<Real>::uni(w.w[1]) - Real(1);
+                const Real st = Math<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
+                Real sp, cp;
+                Math<Real>::angle(Math<Real>::uni(w.w[2]), sp, cp);
+                sh.psrc[i] = sr;
+                sh.pdst[i] = ds;
+                Real *rr = sh.prnd + 4 * size_t(i);
+                rr[0] = xs; rr[1] = cp * st; rr[2] = sp * st; rr[3] = ct;
+            }
+            __syncthreads();
+        }
+        auto collide_pre = [&](int i, int lv) {
+            const int2 sr = sh.psrc[i], ds = sh.pdst[i];
+            const Real *rr = sh.prnd + 4 * size_t(i);
+            const Real xs = rr[0], sx = rr[1], sy = rr[2], sz = rr[3];
+            Real ax, ay, az, bx, by, bz;
+            if (sr.x >= 0) { ax = IBx[sr.x]; ay = IBy[sr.x]; az = IBz[sr.x]; }
+            else { const int sl = ~sr.x; ax = Vx[sl]; ay = Vy[sl]; az = Vz[sl]; }
+            if (sr.y >= 0) { bx = IBx[sr.y]; by = IBy[sr.y]; bz = IBz[sr.y]; }
+            else { const int sl = ~sr.y; bx = Vx[sl]; by = Vy[sl]; bz = Vz[sl]; }
+            const Real dx = ax - bx, dy = ay - by, dz = az - bz;
+            const Real g = Math<Real>::sqrt_(dx * dx + dy * dy + dz * dz);
+            bool acc = true;
+            if (alpha != Real(0)) {
+                const Real ga = (alpha == Real(1)) ? g : Math<Real>::pow_(g, alpha);
+                if (ga > Sigma) cnt[2] += 1.0;
+                acc = xs < ga;
+            }
+            Real oax = ax, oay = ay, oaz = az, obx = bx, oby = by, obz = bz;
+            if (acc) {
+                const Real h = Real(0.5) * g;
+                const Real cx = Real(0.5) * (ax + bx), cy = Real(0.5) * (ay + by), cz = Real(0.5) * (az + bz);
+                oax = cx + h * sx; oay = cy + h * sy; oaz = cz + h * sz;
+                obx = cx - h * sx; oby = cy - h * sy; obz = cz - h * sz;
+                cnt[0] += 1.0;
+            } else {
+                cnt[1] += 1.0;
+            }
+            if (ds.x >= 0) { IBx[ds.x] = oax; IBy[ds.x] = oay; IBz[ds.x] = oaz; }
+            else { const int q = ~ds.x; OBx[q] = oax; OBy[q] = oay; OBz[q] = oaz; }
+            if (ds.y >= 0) { IBx[ds.y] = obx; IBy[ds.y] = oby; IBz[ds.y] = obz; }
+            else { const int q = ~ds.y; OBx[q] = obx; OBy[q] = oby; OBz[q] = obz; }
+            if (wb) {
+                double L;
+                if (wb == TRMC_LEN_K) {
+                    L = double(lv);
+                } else {
+                    const double La = sr.x >= 0 ? IL[sr.x] : 0.0, Lb = sr.y >= 0 ? IL[sr.y] : 0.0;
+                    L = wb == TRMC_LEN_MIN ? 1.0 + (La < Lb ? La : Lb) : __dadd_rn(1.0, __dmul_rn(0.5, __dadd_rn(La, Lb)));
+                }
+                if (ds.x >= 0) IL[ds.x] = L; else OL[~ds.x] = L;
+                if (ds.y >= 0) IL[ds.y] = L; else OL[~ds.y] = L;
+            }
+        };
         bool warp_only = false;      // the last level ran in warp 0 alone
+        int jw = 0;                  // next deep level in WL
         for (int lv = 1; lv <= m_eff; ++lv) {
             const int Cn = sh.C[lv];
             if (Cn == 0) continue;
             if (Cn <= kWarpLevel) {
                 warp_only = true;
+                const int base = nWL > 0 ? sh.WB[jw++] : 0;
                 if (warp != 0) continue;
+                if (nWL > 0) {
+                    for (int c = lane; c < Cn; c += 32) collide_pre(base + c, lv);
+                    __syncwarp();
+                    continue;
+                }
                 level_setup(lv);
                 __syncwarp();
                 Perm pk;
