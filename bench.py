@@ -187,11 +187,12 @@ def make_sim(workload, seed):
     from paper_1009_2768_gb300 import trmc as T
     from paper_1009_2768_gb300.workloads import BatchedRelaxation, HomogeneousBKW, ShockTubes, StationaryShock
     if workload == "stationary":
-        return StationaryShock(4000, 2500, precision=T.FP32_MIXED, seed=seed), 4, "f32 velocities, f64 moments"
+        return (StationaryShock(4000, 2500, precision=T.FP32_MIXED, seed=seed, order="adaptive"), 4,
+                "f32 velocities, f64 moments")
     if workload == "shock":
-        return ShockTubes(EPS, N_CELLS, MEAN, precision=T.FP64, seed=seed), 8, "f64"
+        return ShockTubes(EPS, N_CELLS, MEAN, precision=T.FP64, seed=seed, order="adaptive"), 8, "f64"
     if workload == "batched":
-        return BatchedRelaxation(precision=T.FP32_MIXED, seed=seed), 4, "f32 velocities, f64 moments"
+        return BatchedRelaxation(precision=T.FP32_MIXED, seed=seed, order="adaptive"), 4, "f32 velocities, f64 moments"
     return HomogeneousBKW(100000, precision=T.FP64, seed=seed), 8, "f64"
 
 

@@ -103,12 +103,16 @@ typedef struct trmc_state {
     uint64_t *step_dev;           /* NULL, or a device step counter: trmc_collide then keys its
                                      draws with *step_dev (ignoring its step argument) and adds 1 to
                                      it when done, so a captured CUDA graph advances on replay */
-    const int32_t *cell_order;    /* [n_cells] or NULL: the order in which cells are handed to
-                                     CTAs (e.g. largest first); results do not depend on it */
+    int32_t *cell_order;          /* [n_cells] or NULL: the order in which cells are handed to
+                                     CTAs (e.g. largest first); results do not depend on it.  With
+                                     cell_cost also set, trmc_collide rewrites it before each launch:
+                                     longest cells first, by the times the previous launch measured */
     double *cell_carry;           /* [n_cells][4] or NULL: momentum (3) and sum |v|^2 that rounding
                                      the thermalised velocities to the storage precision left over;
                                      the next step's renormalisation target adds it back, so
                                      sum(stored) + carry is conserved to FP64 round-off */
+    uint32_t *cell_cost;          /* [n_cells] or NULL: trmc_collide writes the time each cell took
+                                     (SM clock cycles / 16, saturated); start it at zero */
     int64_t capacity;             /* length of each particle array                */
     int32_t n_cells;
     uint32_t problem_id;          /* used when cell_key is NULL                   */

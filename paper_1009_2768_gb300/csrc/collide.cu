@@ -55,6 +55,7 @@ struct Args {
     double *cell_carry;
     uint64_t *step_dev;
     const int32_t *cell_order;
+    uint32_t *cell_cost;
     uint32_t problem_id;
     uint64_t seed, step;
     trmc_collide_params prm;
@@ -1143,7 +1144,12 @@ __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
         if (ticket >= a.n_cells) break;
         const int cell = a.cell_order ? a.cell_order[ticket] : ticket;
         double cnt[3] = {0, 0, 0};   // collisions, dummy, exceed
+        const long long t_start = clock64();
         process_cell<Real>(a, step, sh, dsm, slab, cell, cnt);
+        if (a.cell_cost && threadIdx.x == 0) {
+            const unsigned long long dt = (unsigned long long)(clock64() - t_start) >> 4;
+            a.cell_cost[cell] = dt > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(dt);
+        }
         __syncthreads();
         if (a.report || a.stats) {
             block_sum<3>(cnt, sh.red);
@@ -1178,6 +1184,34 @@ __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
             __threadfence();
         }
     }
+}
+
+// Order of the next collide launch: longest cells first, by the times the
+// previous launch measured (a counting sort over 64 buckets, two per octave;
+// the order within a bucket is arbitrary, and results do not depend on it).
+__device__ __forceinline__ int cost_bucket(uint32_t c)
+{
+    if (c == 0) return 0;
+    const int l = 31 - __clz(c);
+    const int half = l > 0 ? int((c >> (l - 1)) & 1u) : 0;
+    const int b = 2 * l + half + 1;
+    return b > 63 ? 63 : b;
+}
+
+__global__ void __launch_bounds__(1024) order_kernel(const uint32_t *cost, int n, int32_t *order)
+{
+    __shared__ int cnt[64];
+    const int tid = threadIdx.x;
+    if (tid < 64) cnt[tid] = 0;
+    __syncthreads();
+    for (int c = tid; c < n; c += blockDim.x) atomicAdd(&cnt[cost_bucket(cost[c])], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int s = 0;
+        for (int b = 63; b >= 0; --b) { const int t = cnt[b]; cnt[b] = s; s += t; }
+    }
+    __syncthreads();
+    for (int c = tid; c < n; c += blockDim.x) order[atomicAdd(&cnt[cost_bucket(cost[c])], 1)] = c;
 }
 
 template <typename Real>
@@ -1216,6 +1250,7 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     a.cell_carry = st->cell_carry;
     a.step_dev = st->step_dev;
     a.cell_order = st->cell_order;
+    a.cell_cost = st->cell_cost;
     a.problem_id = st->problem_id;
     a.seed = ctx->seed;
     a.step = step;
@@ -1227,6 +1262,7 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     a.slabs = ctx->slabs;
     a.slab_bytes = (ctx->slabs_bytes / size_t(grid)) & ~size_t(255);
     a.smem_bytes = smem;
+    if (st->cell_cost && st->cell_order) order_kernel<<<1, 1024, 0, s>>>(st->cell_cost, st->n_cells, st->cell_order);
     collide_kernel<Real><<<grid, threads, smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "collide launch");
@@ -1324,6 +1360,7 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
     a.cell_carry = st->cell_carry;
     a.step_dev = st->step_dev;
     a.cell_order = st->cell_order;
+    a.cell_cost = nullptr;
     a.problem_id = st->problem_id;
     a.seed = seed;
     a.step = step;

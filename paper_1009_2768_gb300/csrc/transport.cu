@@ -31,7 +31,7 @@ constexpr double kTwoPi = 6.283185307179586;
 // Position update and new cell (relative to the domain's first cell, -1 if
 // the particle leaves through a reservoir face), double.
 struct Mover64 {
-    double lo, hi, dx, dt;
+    double lo, hi, dx, inv_dx, dt;
     int nc, res;          // interior cells; reservoir domain (ghost cell first)
     __device__ __forceinline__ int move(double &x, double &vx) const
     {
@@ -41,7 +41,16 @@ struct Mover64 {
         } else if (xn < lo) { xn = __dsub_rn(__dmul_rn(2.0, lo), xn); vx = -vx; }
         else if (xn > hi) { xn = __dsub_rn(__dmul_rn(2.0, hi), xn); vx = -vx; }
         x = xn;
-        const double f = floor(__ddiv_rn(__dsub_rn(xn, lo), dx));
+        // floor of the correctly rounded quotient (xn - lo) / dx, mostly without
+        // the FP64 division: the product with the rounded reciprocal is within
+        // |q| * 3.4e-16 of that quotient, so below 2^20 cells their floors agree
+        // unless the product lies within 1e-9 of an integer; there the
+        // division is done
+        const double a = __dsub_rn(xn, lo);
+        const double qa = __dmul_rn(a, inv_dx);
+        double f = floor(qa);
+        const double fr = __dsub_rn(qa, f);
+        if (fr < 1e-9 || fr > 1.0 - 1e-9 || qa >= 1048576.0) f = floor(__ddiv_rn(a, dx));
         int c = (f < 0.0) ? 0 : (f > double(nc - 1) ? nc - 1 : int(f));
         return c + res;
     }
@@ -105,6 +114,7 @@ __device__ __forceinline__ Mover64 make_mover<double>(const trmc_domain &D, doub
     Mover64 m;
     m.lo = D.x_lo; m.hi = D.x_hi; m.nc = interior_cells(D); m.dt = dt; m.res = D.bc == TRMC_BC_RESERVOIR;
     m.dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(m.nc));
+    m.inv_dx = __ddiv_rn(1.0, m.dx);
     return m;
 }
 template <>

@@ -33,7 +33,7 @@ class GraphStepper:
     def __init__(self, sim, steps_per_graph=2, warmup=2):
         import torch
         self.sim = sim
-        transports = getattr(sim, "launches_per_step", 1) > 1
+        transports = getattr(sim, "transports", False)
         if transports and steps_per_graph % 2:
             raise ValueError("a transporting workload needs an even number of steps per graph")
         if sim.state.step_dev is None:

@@ -45,7 +45,7 @@ class State(C.Structure):
                 ("vx_alt", C.c_void_p), ("vy_alt", C.c_void_p), ("vz_alt", C.c_void_p), ("x_alt", C.c_void_p),
                 ("cell_start", C.c_void_p), ("cell_start_alt", C.c_void_p), ("m_max", C.c_void_p),
                 ("cell_param", C.c_void_p), ("cell_key", C.c_void_p), ("cell_vmax2", C.c_void_p),
-                ("step_dev", C.c_void_p), ("cell_order", C.c_void_p), ("cell_carry", C.c_void_p),
+                ("step_dev", C.c_void_p), ("cell_order", C.c_void_p), ("cell_carry", C.c_void_p), ("cell_cost", C.c_void_p),
                 ("capacity", C.c_int64), ("n_cells", C.c_int32), ("problem_id", C.c_uint32)]
 
 
@@ -225,6 +225,7 @@ class ParticleState:
         self.cell_carry = torch.zeros((max(n_cells, 1), 4), dtype=torch.float64, device=device) if carry else None
         self.step_dev = None           # device step counter (use_device_step)
         self.cell_order = None         # cell processing order (set_cell_order)
+        self.cell_cost = None          # measured per-cell time (use_adaptive_order)
         self.n_cells = n_cells
         self.capacity = n
         self.c = State()
@@ -249,12 +250,22 @@ class ParticleState:
         c.cell_carry = self.cell_carry.data_ptr() if self.cell_carry is not None else None
         c.step_dev = self.step_dev.data_ptr() if self.step_dev is not None else None
         c.cell_order = self.cell_order.data_ptr() if self.cell_order is not None else None
+        c.cell_cost = self.cell_cost.data_ptr() if self.cell_cost is not None else None
 
     def use_device_step(self, start=0):
         """Key the collision draws with a device counter that each trmc_collide
         advances, so that captured CUDA graphs step on replay."""
         import torch
         self.step_dev = torch.full((1,), start, dtype=torch.int64, device=self.cell_vmax2.device)
+        self._fill()
+
+    def use_adaptive_order(self):
+        """Let every collide launch hand out the cells longest first, by the
+        times the previous launch measured (identity order at the start)."""
+        import torch
+        dev = self.cell_vmax2.device
+        self.cell_cost = torch.zeros(max(self.n_cells, 1), dtype=torch.int32, device=dev)
+        self.cell_order = torch.arange(max(self.n_cells, 1), dtype=torch.int32, device=dev)
         self._fill()
 
     def set_cell_order(self, order):

@@ -22,9 +22,10 @@ def _dev(a):
 
 
 class ShockTubes:
+    transports = True
     def __init__(self, eps_list=(1e-1, 1e-2, 1e-3, 1e-4), n_cells=400, mean_per_cell=500,
                  precision=T.FP64, seed=0, alpha=1.0, trunc=T.TRUNC_RAD, m_init=2, cfl=0.5,
-                 workspace=512 << 20, ctx=None, problem_base=0):
+                 workspace=512 << 20, ctx=None, problem_base=0, order="given"):
         import torch
         self.n_tubes = len(eps_list)
         self.n_cells_tube = n_cells
@@ -53,6 +54,9 @@ class ShockTubes:
                                      carry=precision == T.FP32_MIXED)
         if trunc == T.TRUNC_RAD:
             self.state.m_max.fill_(m_init)
+        if order == "adaptive":
+            self.state.use_adaptive_order()
+        self.launches_per_step = 6 + (order == "adaptive")   # cfl, count, scan, scatter, refill, [order], collide
         self.own_ctx = ctx is None
         self.ctx = T.trmc_create(precision, seed, workspace) if ctx is None else ctx
         T.trmc_init_cells(self.ctx, self.state, _dev(ci))
@@ -76,14 +80,13 @@ class ShockTubes:
             events[2].record()
         self.step_index += 1
 
-    launches_per_step = 6     # cfl, count, scan, scatter, refill (no-op for walls), collide
-
     def close(self):
         if self.own_ctx:
             T.trmc_destroy(self.ctx)
 
 
 class HomogeneousBKW:
+    transports = False
     def __init__(self, n=100000, K0=0.6, eps=1.0, dt=0.05, precision=T.FP64, seed=0, trunc=T.TRUNC_RAD, m_init=2,
                  workspace=256 << 20):
         cs = np.array([0, n], np.int64)
@@ -114,6 +117,7 @@ class HomogeneousBKW:
 
 
 class BatchedRelaxation:
+    transports = False
     def __init__(self, n_cells=4096, lo=64, hi=8192, eps_lo=1e-4, eps_hi=10.0, alpha=0.6, dt=0.05,
                  precision=T.FP32_MIXED, seed=0, trunc=T.TRUNC_RAD, m_init=2, workspace=1 << 30,
                  order="given", ctx=None, problem_base=0, problem_per_cell=True, counts=None):
@@ -147,6 +151,9 @@ class BatchedRelaxation:
         T.trmc_init_cells(self.ctx, self.state, _dev(ci))
         if order == "largest_first":          # cell sizes never change here: order once
             self.state.set_cell_order(np.argsort(-counts, kind="stable").astype(np.int32))
+        elif order == "adaptive":
+            self.state.use_adaptive_order()
+        self.launches_per_step = 1 + (order == "adaptive")
         self.params = T.collide_params(trunc=trunc, m=m_init, indicator=T.IND_PXX)
         self.step_index = 0
 
@@ -158,8 +165,6 @@ class BatchedRelaxation:
         if events:
             events[2].record()
         self.step_index += 1
-
-    launches_per_step = 1
 
     def close(self):
         if self.own_ctx:
@@ -178,13 +183,14 @@ def rankine_hugoniot(mach, rho_l=1.0, t_l=1.0, gamma=5.0 / 3.0):
 
 
 class StationaryShock:
+    transports = True
     """1D stationary normal shock on [0,1] (Sec. 5.2): upstream Rankine-
     Hugoniot state on the left flowing in through a reservoir, downstream
     state on the right flowing out through the other, initial step at 0.5;
     hard-sphere VHS, CFL time step, ghost cells at both ends (not collided)."""
 
     def __init__(self, n_cells=4000, mean_per_cell=2500, mach=3.0, eps=1e-3, precision=T.FP32_MIXED, seed=0,
-                 alpha=1.0, trunc=T.TRUNC_RAD, m_init=2, cfl=0.5, workspace=1 << 30, headroom=1.25):
+                 alpha=1.0, trunc=T.TRUNC_RAD, m_init=2, cfl=0.5, workspace=1 << 30, headroom=1.25, order="given"):
         import torch
         left, right = rankine_hugoniot(mach)
         self.left, self.right = left, right
@@ -212,6 +218,9 @@ class StationaryShock:
                                      cell_param=cp, carry=precision == T.FP32_MIXED)
         if trunc == T.TRUNC_RAD:
             self.state.m_max.fill_(m_init)
+        if order == "adaptive":
+            self.state.use_adaptive_order()
+        self.launches_per_step = 6 + (order == "adaptive")   # cfl, count, scan, scatter, refill, [order], collide
         self.ctx = T.trmc_create(precision, seed, workspace)
         T.trmc_init_cells(self.ctx, self.state, _dev(ci))
         self.domains = T.domains_tensor([(0, nc, 0.0, 1.0, T.BC_RESERVOIR, left, right, mass)])
@@ -230,8 +239,6 @@ class StationaryShock:
         if events:
             events[2].record()
         self.step_index += 1
-
-    launches_per_step = 6     # cfl, count, scan, scatter, refill, collide
 
     def close(self):
         T.trmc_destroy(self.ctx)

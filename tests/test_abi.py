@@ -48,7 +48,7 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
 def test_struct_layouts_match_header():
     import ctypes
     from paper_1009_2768_gb300 import trmc
-    assert ctypes.sizeof(trmc.State) == 17 * 8 + 8 + 4 + 4
+    assert ctypes.sizeof(trmc.State) == 18 * 8 + 8 + 4 + 4
     assert ctypes.sizeof(trmc.CollideParams) == 6 * 8 + 6 * 4
     assert ctypes.sizeof(trmc.Domain) == 88
     assert ctypes.sizeof(trmc.CellParam) == 32

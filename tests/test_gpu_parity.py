@@ -211,6 +211,32 @@ def test_transport_parity_bit_exact():
     assert np.array_equal(vg, vo)
 
 
+@pytest.mark.parametrize("n_cells,lo,hi", [(400, 0.0, 1.0), (7, 0.1, 0.83), (1000, -2.5, 3.0)])
+def test_transport_parity_at_cell_faces(n_cells, lo, hi):
+    """Positions on the cell faces and one ulp either side, where the cell
+    index floor((x - lo) / dx) is decided by the last bit of the quotient."""
+    need_gpu()
+    dx = (hi - lo) / n_cells
+    xs, cell = [], []
+    for k in range(1, n_cells):
+        for f in (lo + k * dx, lo + k * (hi - lo) / n_cells, lo + (k * dx + dx * 1e-17)):
+            for y in (f, np.nextafter(f, -np.inf), np.nextafter(f, np.inf)):
+                xs.append(y)
+                cell.append(k - 1 if y < lo + k * dx else k)
+    xs, cell = np.array(xs), np.array(cell)
+    order = np.argsort(cell, kind="stable")
+    xs, cell = xs[order], cell[order]
+    counts = np.bincount(cell, minlength=n_cells)
+    cs = synth.starts(counts)
+    g = synth.rng(14)
+    v = g.standard_normal((3, len(xs))) * 1e-3
+    doms = [(0, n_cells, lo, hi)]
+    for dt in (0.0, 1e-9):
+        xg, vg, csg, _ = gpu_transport(xs, v, cs, doms, dt=[dt])
+        xo, vo, cso = O.transport(xs, v, cs, doms, [dt])
+        assert np.array_equal(csg, cso) and np.array_equal(xg, xo) and np.array_equal(vg, vo)
+
+
 def test_transport_cfl_mode_matches_oracle_dt():
     need_gpu()
     x, v, cs, doms = tube_state(64, 300, seed=12, ntubes=3)

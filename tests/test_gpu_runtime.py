@@ -88,3 +88,27 @@ def test_autotuner_picks_a_measured_shape():
     assert set(times) == {(128, 4), (64, 8)} and best in times
     assert times[best] == min(times.values())
     sim.close()
+
+
+@pytest.mark.parametrize("precision", [T.FP64, T.FP32_MIXED])
+def test_adaptive_order_does_not_change_results(precision):
+    """Cells handed out longest first by the measured times of the previous
+    launch (a permutation rewritten before every collide) step exactly like
+    the identity order."""
+    need_gpu()
+    from paper_1009_2768_gb300.workloads import ShockTubes
+    a = ShockTubes((1e-1, 1e-3), n_cells=64, mean_per_cell=300, precision=precision, seed=4)
+    b = ShockTubes((1e-1, 1e-3), n_cells=64, mean_per_cell=300, precision=precision, seed=4)
+    b.state.use_adaptive_order()
+    for _ in range(6):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    T.trmc_check(b.ctx)
+    assert same(snapshot(a), snapshot(b))
+    order = b.state.cell_order.cpu().numpy()
+    cost = b.state.cell_cost.cpu().numpy().view(np.uint32)
+    assert np.array_equal(np.sort(order), np.arange(b.state.n_cells))
+    assert cost.max() > 0
+    a.close()
+    b.close()
