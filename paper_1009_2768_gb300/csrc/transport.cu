@@ -28,30 +28,67 @@ namespace {
 constexpr int kTT = 256;   // threads per CTA
 constexpr double kTwoPi = 6.283185307179586;
 
+// GB300 has 2 FP64 lanes per SM and clock, so the FP64 mover keeps FP64
+// instructions to the four roundings the method defines (x + v_x dt, and
+// (x - lo) / dx as a product with the rounded reciprocal); comparisons and the
+// floor use integer operations on the bit patterns.
+//
+// Order-preserving integer image of a double (-0.0 maps to +0.0's image).
+__device__ __forceinline__ long long okey(double d)
+{
+    long long b = __double_as_longlong(d);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
+
+// floor(q) for 0 <= q < 2^20 from the bit pattern.  Returns false where q is
+// within 2^-29 of an integer (or outside that range): there the product may
+// round to the other side of the integer than the correctly rounded quotient
+// it stands for, and the caller divides instead.
+__device__ __forceinline__ bool bits_floor(double q, int &fl)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(q);
+    if (b >> 63) return false;
+    const int e = int(b >> 52) - 1023;
+    if (e >= 20 || e < -52) return false;
+    const unsigned long long mant = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+    unsigned long long frac;                       // fraction of q in units of 2^-52
+    if (e >= 0) {
+        fl = int(mant >> (52 - e));
+        frac = (mant & ((1ull << (52 - e)) - 1ull)) << e;
+    } else {
+        fl = 0;
+        frac = mant >> (-e);
+    }
+    const unsigned long long top = frac >> (52 - 29);
+    return top != 0ull && top != (1ull << 29) - 1ull;
+}
+
 // Position update and new cell (relative to the domain's first cell, -1 if
 // the particle leaves through a reservoir face), double.
 struct Mover64 {
     double lo, hi, dx, inv_dx, dt;
+    long long klo, khi;   // okey(lo), okey(hi)
     int nc, res;          // interior cells; reservoir domain (ghost cell first)
     __device__ __forceinline__ int move(double &x, double &vx) const
     {
         double xn = __dadd_rn(x, __dmul_rn(vx, dt));
+        const long long k = okey(xn);
         if (res) {
-            if (xn < lo || xn >= hi) return -1;
-        } else if (xn < lo) { xn = __dsub_rn(__dmul_rn(2.0, lo), xn); vx = -vx; }
-        else if (xn > hi) { xn = __dsub_rn(__dmul_rn(2.0, hi), xn); vx = -vx; }
+            if (k < klo || k >= khi) return -1;
+        } else if (k < klo) { xn = __dsub_rn(__dmul_rn(2.0, lo), xn); vx = -vx; }
+        else if (k > khi) { xn = __dsub_rn(__dmul_rn(2.0, hi), xn); vx = -vx; }
         x = xn;
-        // floor of the correctly rounded quotient (xn - lo) / dx, mostly without
-        // the FP64 division: the product with the rounded reciprocal is within
-        // |q| * 3.4e-16 of that quotient, so below 2^20 cells their floors agree
-        // unless the product lies within 1e-9 of an integer; there the
-        // division is done
+        // floor of the correctly rounded quotient (xn - lo) / dx: the product
+        // with the rounded reciprocal is within |q| * 3.4e-16 of it, so their
+        // floors agree unless the product lies within 2^-29 of an integer
         const double a = __dsub_rn(xn, lo);
-        const double qa = __dmul_rn(a, inv_dx);
-        double f = floor(qa);
-        const double fr = __dsub_rn(qa, f);
-        if (fr < 1e-9 || fr > 1.0 - 1e-9 || qa >= 1048576.0) f = floor(__ddiv_rn(a, dx));
-        int c = (f < 0.0) ? 0 : (f > double(nc - 1) ? nc - 1 : int(f));
+        int c;
+        if (!bits_floor(__dmul_rn(a, inv_dx), c)) {
+            const double f = floor(__ddiv_rn(a, dx));
+            c = (f < 0.0) ? 0 : (f > double(nc - 1) ? nc - 1 : int(f));
+        }
+        if (c > nc - 1) c = nc - 1;
         return c + res;
     }
 };
@@ -115,6 +152,7 @@ __device__ __forceinline__ Mover64 make_mover<double>(const trmc_domain &D, doub
     m.lo = D.x_lo; m.hi = D.x_hi; m.nc = interior_cells(D); m.dt = dt; m.res = D.bc == TRMC_BC_RESERVOIR;
     m.dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(m.nc));
     m.inv_dx = __ddiv_rn(1.0, m.dx);
+    m.klo = okey(m.lo); m.khi = okey(m.hi);
     return m;
 }
 template <>
