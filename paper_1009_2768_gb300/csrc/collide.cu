@@ -97,6 +97,12 @@ struct Sh {
     // exclusive label prefix per level (triangular rows), input and output
     // locations, acceptance threshold xi*Sigma and scattering direction
     int32_t WL[NLEV], WB[NLEV + 1], nWL;
+    // the tail: deep levels above the highest level of more than kWarpLevel
+    // collisions (LB); its records from index tail0 run in dependency order:
+    // prodOf maps a tail consumer slot (from IB[LB + 1]) to the record that
+    // fills it, done holds the round in which a record ran (0: not yet)
+    int32_t LB, tail0, ntail, tailbase;
+    int32_t *prodOf, *done;
     int32_t *LP;
     int2 *psrc, *pdst;
     Real *prnd;
@@ -411,24 +417,42 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                         sh.C[lv] = T >> 1;
                     }
                     int32_t *row = sh.Mt + tri(lv);
+                    int32_t *srow = sh.St + tri(lv);
                     for (int k = lane; k < lv; k += 32) row[k] = 0;
                     __syncwarp();
                     const int Cn = sh.C[lv];
-                    for (int c = lane; c < Cn && c < kPreLabels; c += 32) atomicAdd(&row[sh.lab[lv][c]], 1);
-                    for (int g = kPreLabels / 4 + lane; g < (Cn + 3) >> 2; g += 32) {
-                        const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
+                    if (Cn <= kPreLabels) {
+                        // few collisions: only the demand slots their labels touch
+                        // change; their slot bases are read first, then the counts
+                        if (lane < Cn) {
+                            const int k = sh.lab[lv][lane], j = lv - 1 - k;
+                            srow[k] = sh.D[k];
+                            srow[j] = sh.D[j];
+                        }
+                        __syncwarp();
+                        if (lane < Cn) {
+                            const int k = sh.lab[lv][lane];
+                            atomicAdd(&row[k], 1);
+                            atomicAdd(&sh.D[k], 1);
+                            atomicAdd(&sh.D[lv - 1 - k], 1);
+                        }
+                    } else {
+                        for (int c = lane; c < kPreLabels; c += 32) atomicAdd(&row[sh.lab[lv][c]], 1);
+                        for (int g = kPreLabels / 4 + lane; g < (Cn + 3) >> 2; g += 32) {
+                            const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (4 * g + j < Cn) atomicAdd(&row[below(w.w[j], uint32_t(lv))], 1);
+                            for (int j = 0; j < 4; ++j)
+                                if (4 * g + j < Cn) atomicAdd(&row[below(w.w[j], uint32_t(lv))], 1);
+                        }
+                        __syncwarp();
+                        // slot bases of this level's consumers, then the demand it adds
+                        for (int k = lane; k < lv; k += 32) {
+                            const int d = sh.D[k];
+                            srow[k] = d;
+                            sh.D[k] = d + row[k] + row[lv - 1 - k];
+                        }
                     }
                     __syncwarp();
-                    // slot bases of this level's consumers, then the demand it adds
-                    int32_t *srow = sh.St + tri(lv);
-                    for (int k = lane; k < lv; k += 32) {
-                        const int d = sh.D[k];
-                        srow[k] = d;
-                        sh.D[k] = d + row[k] + row[lv - 1 - k];
-                    }
                     if (lane == 0) sh.out[lv] = 2 * Cn - sh.D[lv];
                     __syncwarp();
                     --lv;
@@ -498,6 +522,30 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     if (!sh.LP || !sh.psrc || !sh.pdst || !sh.prnd) {
                         sh.pass_smem = s0; sh.pass_slab = g0; sh.pass_smem_cap = sc0; sh.pass_slab_cap = gc0;
                         sh.nWL = 0;
+                    }
+                }
+                // the tail, run in dependency order when there is room for its maps
+                sh.LB = 0;
+                for (int lv = 1; lv <= m; ++lv)
+                    if (sh.C[lv] > kWarpLevel) sh.LB = lv;
+                sh.ntail = 0;
+                if (sh.nWL > 0) {
+                    int jt = 0;
+                    while (jt < sh.nWL && sh.WL[jt] <= sh.LB) ++jt;
+                    const int nt = sh.WB[sh.nWL] - sh.WB[jt];
+                    const int nslots = sh.IB[m + 1] - sh.IB[sh.LB + 1];
+                    if (sh.nWL - jt >= 2 && nt > 0) {
+                        char *s0 = sh.pass_smem, *g0 = sh.pass_slab;
+                        const size_t sc0 = sh.pass_smem_cap, gc0 = sh.pass_slab_cap;
+                        sh.prodOf = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab,
+                                                                sh.pass_slab_cap, 4 * size_t(nslots + 1)));
+                        sh.done = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab,
+                                                              sh.pass_slab_cap, 4 * size_t(nt)));
+                        if (sh.prodOf && sh.done) {
+                            sh.ntail = nt; sh.tail0 = sh.WB[jt]; sh.tailbase = sh.IB[sh.LB + 1];
+                        } else {
+                            sh.pass_smem = s0; sh.pass_slab = g0; sh.pass_smem_cap = sc0; sh.pass_slab_cap = gc0;
+                        }
                     }
                 }
                 // invariants of a consistent plan; a violation would index the
@@ -603,17 +651,25 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     int T = sh.Nq[lv] + Dw[lv];
                     if (T & 1) T += (sh.Nq[lv] >= 1 && ((sh.coin[lv >> 5] >> (lv & 31)) & 1u)) ? -1 : 1;
                     const int Cn = T >> 1;
-                    for (int k = lane; k < lv; k += 32) rw[k] = 0;
-                    __syncwarp();
-                    for (int c = lane; c < Cn && c < kPreLabels; c += 32) atomicAdd(&rw[sh.lab[lv][c]], 1);
-                    for (int g = kPreLabels / 4 + lane; g < (Cn + 3) >> 2; g += 32) {
-                        const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
+                    if (Cn <= kPreLabels) {
+                        if (lane < Cn) {
+                            const int k = sh.lab[lv][lane];
+                            atomicAdd(&Dw[k], 1);
+                            atomicAdd(&Dw[lv - 1 - k], 1);
+                        }
+                    } else {
+                        for (int k = lane; k < lv; k += 32) rw[k] = 0;
+                        __syncwarp();
+                        for (int c = lane; c < kPreLabels; c += 32) atomicAdd(&rw[sh.lab[lv][c]], 1);
+                        for (int g = kPreLabels / 4 + lane; g < (Cn + 3) >> 2; g += 32) {
+                            const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (4 * g + j < Cn) atomicAdd(&rw[below(w.w[j], uint32_t(lv))], 1);
+                            for (int j = 0; j < 4; ++j)
+                                if (4 * g + j < Cn) atomicAdd(&rw[below(w.w[j], uint32_t(lv))], 1);
+                        }
+                        __syncwarp();
+                        for (int k = lane; k < lv; k += 32) Dw[k] += rw[k] + rw[lv - 1 - k];
                     }
-                    __syncwarp();
-                    for (int k = lane; k < lv; k += 32) Dw[k] += rw[k] + rw[lv - 1 - k];
                     __syncwarp();
                     --lv;
                     while (lv >= 1 && sh.Nq[lv] + Dw[lv] == 0) --lv;
@@ -811,6 +867,11 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 sh.pdst[i] = ds;
                 Real *rr = sh.prnd + 4 * size_t(i);
                 rr[0] = xs; rr[1] = cp * st; rr[2] = sp * st; rr[3] = ct;
+                if (sh.ntail > 0 && i >= sh.tail0) {
+                    if (ds.x >= 0) sh.prodOf[ds.x - sh.tailbase] = i - sh.tail0;
+                    if (ds.y >= 0) sh.prodOf[ds.y - sh.tailbase] = i - sh.tail0;
+                    sh.done[i - sh.tail0] = 0;
+                }
             }
             __syncthreads();
         }
@@ -859,7 +920,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         };
         bool warp_only = false;      // the last level ran in warp 0 alone
         int jw = 0;                  // next deep level in WL
-        for (int lv = 1; lv <= m_eff; ++lv) {
+        const int ntail = sh.ntail;
+        const int lv_end = ntail > 0 ? sh.LB : m_eff;
+        for (int lv = 1; lv <= lv_end; ++lv) {
             const int Cn = sh.C[lv];
             if (Cn == 0) continue;
             if (Cn <= kWarpLevel) {
@@ -888,6 +951,51 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             }
         }
         __syncthreads();
+        if (ntail > 0) {
+            // 5b. The tail in dependency order: every round, each record whose
+            //     inputs were produced in earlier rounds (or come from leaves and
+            //     lower levels) runs.  The number of rounds is the depth of the
+            //     tail's collision graph, far below its number of levels (a
+            //     level-n product depends on levels k and n-1-k, k uniform), and
+            //     a round is at least the lowest pending level, so it ends.
+            const int t0 = sh.tail0, base = sh.tailbase;
+            int32_t *done = sh.done;
+            const int32_t *prodOf = sh.prodOf;
+            auto level_of = [&](int i) {
+                int lo_ = 0, hi_ = nWL - 1;
+                while (lo_ < hi_) {
+                    const int mid = (lo_ + hi_ + 1) >> 1;
+                    if (sh.WB[mid] <= i) lo_ = mid; else hi_ = mid - 1;
+                }
+                return sh.WL[lo_];
+            };
+            int round = 1;
+            bool pending = true;
+            for (;;) {
+                if (!__syncthreads_or(pending)) break;
+                if (round > NLEV) {          // impossible for a consistent plan; leave the cell unchanged
+                    if (tid == 0) sh.skip = 2;
+                    break;
+                }
+                pending = false;
+                for (int r = tid; r < ntail; r += bs) {
+                    if (done[r]) continue;
+                    const int2 sr = sh.psrc[t0 + r];
+                    bool ready = true;
+                    if (sr.x >= base) { const int d = done[prodOf[sr.x - base]]; ready = d != 0 && d < round; }
+                    if (ready && sr.y >= base) { const int d = done[prodOf[sr.y - base]]; ready = d != 0 && d < round; }
+                    if (ready) {
+                        collide_pre(t0 + r, wb == TRMC_LEN_K ? level_of(t0 + r) : 0);
+                        done[r] = round;
+                    } else {
+                        pending = true;
+                    }
+                }
+                ++round;
+            }
+            __syncthreads();
+            if (sh.skip) break;
+        }
 
         // 6. outputs replace the leaves.  What the collisions changed (sum of
         //    output - original over the leaves) and the thermalised set's own
