@@ -329,7 +329,13 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
     const CellRng rng{a.seed, sh.problem, sh.lcell, step};
 
     // ---- 1. stage + moments -------------------------------------------------
+    // (the indicator sums only for TRMC-RAD; the speed bound only for VHS; on
+    // GB300 every FP64 instruction counts, so maxima of non-negative doubles
+    // are taken on their bit patterns)
     {
+        const bool rad = prm.trunc == TRMC_TRUNC_RAD;
+        const bool need_m4 = rad && prm.indicator == TRMC_IND_M4, need_pxx = rad && prm.indicator == TRMC_IND_PXX;
+        const bool need_d2 = sh.alpha != 0.0;
         Sum<Real> a0, a1, a2, a3, a4;
         constexpr int U = 4;      // loads issued together, ahead of the stores they feed
         for (int i0 = tid; i0 < n; i0 += U * bs) {
@@ -346,8 +352,10 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     Vx[i] = x[u]; Vy[i] = y[u]; Vz[i] = z[u];
                     a0.add(x[u]); a1.add(y[u]); a2.add(z[u]);
                     a3.add_sq3(x[u], y[u], z[u]);
-                    const Real e = x[u] * x[u] + y[u] * y[u] + z[u] * z[u];
-                    a4.add(e * e);
+                    if (need_m4) {
+                        const Real e = x[u] * x[u] + y[u] * y[u] + z[u] * z[u];
+                        a4.add(e * e);
+                    }
                 }
             }
         }
@@ -356,15 +364,26 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         const double U0 = s[0] / double(n), U1 = s[1] / double(n), U2 = s[2] / double(n);
         const Real u0 = Real(U0), u1 = Real(U1), u2 = Real(U2);
         Real d2 = 0;
+        long long d2b = 0;
         Sum<Real> pxx;
-        for (int i = tid; i < n; i += bs) {
-            const Real ax = Vx[i] - u0, ay = Vy[i] - u1, az = Vz[i] - u2;
-            d2 = fmax(d2, ax * ax + ay * ay + az * az);
-            pxx.add(ax * ax);
+        if (need_d2 || need_pxx) {
+            for (int i = tid; i < n; i += bs) {
+                const Real ax = Vx[i] - u0, ay = Vy[i] - u1, az = Vz[i] - u2;
+                if (need_d2) {
+                    const Real q = ax * ax + ay * ay + az * az;
+                    if constexpr (sizeof(Real) == 8) d2b = max(d2b, __double_as_longlong(q));
+                    else d2 = fmaxf(d2, q);
+                }
+                if (need_pxx) pxx.add(ax * ax);
+            }
         }
-        double t[1] = {pxx.get()};
-        block_sum<1>(t, sh.red);
-        const double dmax = (sh.alpha != 0.0) ? block_max(double(d2), sh.red) : 0.0;
+        if constexpr (sizeof(Real) == 8) d2 = __longlong_as_double(d2b);
+        double t[1] = {0.0};
+        if (need_pxx) {
+            t[0] = pxx.get();
+            block_sum<1>(t, sh.red);
+        }
+        const double dmax = need_d2 ? block_max(double(d2), sh.red) : 0.0;
         if (tid == 0) {
             sh.P[0] = s[0]; sh.P[1] = s[1]; sh.P[2] = s[2]; sh.E = s[3];
             sh.U[0] = U0; sh.U[1] = U1; sh.U[2] = U2;
@@ -377,7 +396,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             const double rho = double(n) * sh.rho_scale;
             const double mu = rho * Sigma;
             sh.q = exp(-(mu * sh.dt) / sh.eps);
-            sh.S_pre = (prm.indicator == TRMC_IND_M4 ? s[4] : t[0]) / double(n);
+            sh.S_pre = (need_m4 ? s[4] : t[0]) / double(n);
         }
         __syncthreads();
     }
@@ -1208,20 +1227,23 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
     }
 
     // ---- 8. write back the changed particles; cell max |v|^2 ----------------
-    {
+    if (a.cell_vmax2) {
         Real vm = 0;
+        long long vmb = 0;
         for (int i = tid; i < n; i += bs) {
             const Real x = Vx[i], y = Vy[i], z = Vz[i];
             if ((sh.flags[i >> 5] >> (i & 31)) & 1u) { gx[base + i] = x; gy[base + i] = y; gz[base + i] = z; }
             if constexpr (sizeof(Real) == 8)       // rounded exactly as the CPU reference rounds it
-                vm = fmax(vm, __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+                vmb = max(vmb, __double_as_longlong(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z))));
             else
                 vm = fmaxf(vm, __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z)));
         }
-        if (a.cell_vmax2) {
-            const double vmax = block_max(double(vm), sh.red);
-            if (tid == 0) a.cell_vmax2[cell] = vmax;
-        }
+        if constexpr (sizeof(Real) == 8) vm = __longlong_as_double(vmb);
+        const double vmax = block_max(double(vm), sh.red);
+        if (tid == 0) a.cell_vmax2[cell] = vmax;
+    } else {
+        for (int i = tid; i < n; i += bs)
+            if ((sh.flags[i >> 5] >> (i & 31)) & 1u) { gx[base + i] = Vx[i]; gy[base + i] = Vy[i]; gz[base + i] = Vz[i]; }
     }
     if (tid == 0) {
         if (prm.trunc == TRMC_TRUNC_RAD) a.m_max[cell] = sh.m_next;
