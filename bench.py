@@ -52,7 +52,7 @@ METRIC = "particle-steps/s"
 # of the same command, keyed by the hash of csrc/collide.cu it was taken on; reported as
 # null once the kernel source differs.  See profiles/.
 NCU_TRAFFIC = {
-    "shock": {"collide_sha": "6d2dfbde8b297843", "bytes": 22815744 + 73984},
+    "shock": {"collide_sha": "b25a8d8fef70e017", "bytes": 27217664 + 666624, "fp64_pipe_active_pct": 59.1},
 }
 
 
@@ -293,11 +293,13 @@ def ours(args):
         kern, abytes, dur = "transport (count+scan+scatter)", transport_bytes, tr_avg
     achieved = abytes / dur / 1e9
     tr_rec = NCU_TRAFFIC.get(args.workload)
-    traffic = tr_rec["bytes"] if (tr_rec and kern == "collide_kernel" and tr_rec["collide_sha"] == collide_sha()) else None
+    fresh = bool(tr_rec and kern == "collide_kernel" and tr_rec["collide_sha"] == collide_sha())
+    traffic = tr_rec["bytes"] if fresh else None
     roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
             "collide_ms": float(co_ms.mean()), "transport_ms": float(tr_ms.mean()),
-            "algorithmic_bytes_per_launch": abytes}
+            "algorithmic_bytes_per_launch": abytes,
+            "fp64_pipe_active_pct": tr_rec.get("fp64_pipe_active_pct") if fresh else None}
 
     # end to end: host-resident state, H2D + step + D2H every step
     e2e = None
