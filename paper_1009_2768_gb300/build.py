@@ -32,7 +32,7 @@ def _sources():
 
 def _deps():
     return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
-            + [os.path.join(ROOT, "include", "trmc.h"), os.path.abspath(__file__)])
+            + glob.glob(os.path.join(CSRC, "*.inc")) + [os.path.join(ROOT, "include", "trmc.h"), os.path.abspath(__file__)])
 
 
 def up_to_date():
@@ -43,6 +43,9 @@ def up_to_date():
 
 
 def build(force=False, verbose=False):
+    if not os.path.exists(os.path.join(CSRC, "fp64_tables.inc")):
+        from . import gen_tables
+        gen_tables.main()
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)

@@ -149,6 +149,64 @@ __device__ __forceinline__ int block_flag_scan(bool flag, int &excl, int32_t *sc
     return total;
 }
 
+// ---- FP64 angles and logarithms of the 53-bit uniforms ----------------------
+// GB300 issues FP64 at 2 lanes per SM and clock, and every FP64 instruction of
+// a collision or a Maxwellian sample counts.  These evaluate sin/cos(2 pi u)
+// and ln u for the draws' uniforms from correctly rounded tables
+// (fp64_tables.inc, written by gen_tables.py) with short series, in about 18
+// and 14 FP64 instructions, to within 2 ulp (checked against sincospi and log
+// by trmc_fp64_selftest).
+#include "fp64_tables.inc"
+
+__device__ __forceinline__ double exact_small(uint64_t v)       // v < 2^52, exactly
+{
+    return __longlong_as_double((long long)(0x4330000000000000ull | v)) - 4503599627370496.0;
+}
+
+// u = k 2^-53, 0 <= k < 2^53: the top 8 bits of k pick a = 2 pi i / 256, the
+// other 45 give t = 2 pi (u - i / 256) in [0, 2 pi / 256); the addition
+// formulas combine sin a, cos a with the Taylor series of sin t and cos t - 1
+// (the first omitted terms, t^9 / 9! and t^10 / 10!, are below 1e-20).
+__device__ __forceinline__ void sincos_2pi(uint64_t k, double &s, double &c)
+{
+    const int i = int(k >> 45);
+    const double fd = exact_small(k & ((1ull << 45) - 1ull));
+    const double t = fma(fd, kTwoPi53[0], fd * kTwoPi53[1]);
+    const double t2 = t * t;
+    const double ps = fma(t2, fma(t2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0);
+    const double sn = fma(t * t2, ps, t);
+    const double pc = fma(t2, fma(t2, fma(t2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5);
+    const double cm1 = t2 * pc;
+    const double S = kSinCos256[i][0], C = kSinCos256[i][1];
+    s = S + fma(S, cm1, C * sn);
+    c = C + fma(C, cm1, -(S * sn));
+}
+
+// ln u, u = k 2^-53, 1 <= k <= 2^53: u = 2^(e - 52) (m / 2) with m in [1, 2),
+// m = T_j (1 + t) with T_j = 1 + j / 128 from the top 7 fraction bits and
+// t in [0, 1/128); ln u = (e - 52) ln 2 + ln(T_j / 2) + ln(1 + t), all terms
+// of one sign but the small last one, with ln(1 + t) by its series to t^8.
+// For u >= 1 - 1/128 the series of ln(1 - d) in the exact d = 1 - u keeps
+// the relative accuracy.
+__device__ __forceinline__ double log_u53(uint64_t k)
+{
+    if (k >= (1ull << 53) - (1ull << 46)) {
+        const double d = exact_small((1ull << 53) - k) * 0x1p-53;
+        const double p = fma(d, fma(d, fma(d, fma(d, fma(d, fma(d, 1.0 / 8.0, 1.0 / 7.0), 1.0 / 6.0), 1.0 / 5.0),
+                                                 1.0 / 4.0), 1.0 / 3.0), 0.5);
+        return -fma(d * d, p, d);
+    }
+    const int e = 63 - __clzll((long long)k);
+    const uint64_t frac = (k << (52 - e)) & ((1ull << 52) - 1ull);
+    const int j = int(frac >> 45);
+    const double t = exact_small(frac & ((1ull << 45) - 1ull)) * kLnT128[j][1];
+    const double p = fma(t, fma(t, fma(t, fma(t, fma(t, fma(t, -1.0 / 8.0, 1.0 / 7.0), -1.0 / 6.0), 1.0 / 5.0),
+                                             -1.0 / 4.0), 1.0 / 3.0), -0.5);
+    const double l1 = fma(t * t, p, t);
+    const double ne = double(e - 52);
+    return fma(ne, kLn2[0], fma(ne, kLn2[1], kLnT128[j][0] + l1));
+}
+
 template <typename Real> struct Math;
 template <> struct Math<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
@@ -156,23 +214,24 @@ template <> struct Math<double> {
     static __device__ __forceinline__ double uni(uint64_t w) { return u01(w); }
     // sin / cos of 2 pi u: sincospi reduces the argument exactly, so it is
     // cheaper than sin(2 pi u) and within an ulp of it
-    static __device__ __forceinline__ void angle(double u, double &s, double &c) { sincospi(2.0 * u, &s, &c); }
+    static __device__ __forceinline__ void angle(uint64_t w, double &s, double &c) { sincos_2pi(w >> 11, s, c); }
     static __device__ __forceinline__ void normals(const U64x4 &w, double &z0, double &z1, double &z2)
     {
-        const double r1 = sqrt(-2.0 * log(u01_open(w.w[0])));
-        const double r2 = sqrt(-2.0 * log(u01_open(w.w[2])));
-        double s1, c1;
-        sincospi(2.0 * u01(w.w[1]), &s1, &c1);
+        const double r1 = sqrt(-2.0 * log_u53((w.w[0] >> 11) + 1));
+        const double r2 = sqrt(-2.0 * log_u53((w.w[2] >> 11) + 1));
+        double s1, c1, s2, c2;
+        sincos_2pi(w.w[1] >> 11, s1, c1);
+        sincos_2pi(w.w[3] >> 11, s2, c2);
         z0 = r1 * c1;
         z1 = r1 * s1;
-        z2 = r2 * cospi(2.0 * u01(w.w[3]));
+        z2 = r2 * c2;
     }
 };
 template <> struct Math<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float pow_(float x, float a) { return powf(x, a); }
     static __device__ __forceinline__ float uni(uint64_t w) { return u01f(w); }
-    static __device__ __forceinline__ void angle(float u, float &s, float &c) { sincospif(2.0f * u, &s, &c); }
+    static __device__ __forceinline__ void angle(uint64_t w, float &s, float &c) { sincospif(2.0f * u01f(w), &s, &c); }
     static __device__ __forceinline__ void normals(const U64x4 &w, float &z0, float &z1, float &z2)
     {
         const float r1 = sqrtf(-2.0f * logf(u01f_open(w.w[0])));
@@ -797,7 +856,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const Real ct = Real(2) * Math<Real>::uni(w.w[1]) - Real(1);
                 const Real st = Math<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
                 Real sp, cp;
-                Math<Real>::angle(Math<Real>::uni(w.w[2]), sp, cp);
+                Math<Real>::angle(w.w[2], sp, cp);
                 const Real sx = cp * st, sy = sp * st, sz = ct;
                 const Real h = Real(0.5) * g;
                 const Real cx = Real(0.5) * (ax + bx), cy = Real(0.5) * (ay + by), cz = Real(0.5) * (az + bz);
@@ -881,7 +940,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const Real ct = Real(2) * Math<Real>::uni(w.w[1]) - Real(1);
                 const Real st = Math<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
                 Real sp, cp;
-                Math<Real>::angle(Math<Real>::uni(w.w[2]), sp, cp);
+                Math<Real>::angle(w.w[2], sp, cp);
                 sh.psrc[i] = sr;
                 sh.pdst[i] = ds;
                 Real *rr = sh.prnd + 4 * size_t(i);
@@ -1536,3 +1595,31 @@ extern "C" trmc_status trmc_collide_static(trmc_state *state, const trmc_collide
     return launch_static<float>(state, p, seed, step, max_cell_particles, status_dev, s);
 }
 
+
+// ---- self-test of the FP64 angle and logarithm evaluations --------------------
+namespace trmc {
+namespace {
+__global__ void fp64_selftest_kernel(const uint64_t *k, int n, double *out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t w = k[i];
+        double s, c, s_ref, c_ref;
+        sincos_2pi(w >> 11, s, c);
+        sincospi(2.0 * u01(w), &s_ref, &c_ref);
+        double *o = out + 6 * size_t(i);
+        o[0] = s; o[1] = c; o[2] = s_ref; o[3] = c_ref;
+        o[4] = log_u53((w >> 11) + 1);
+        o[5] = log(u01_open(w));
+    }
+}
+}  // namespace
+}  // namespace trmc
+
+extern "C" trmc_status trmc_fp64_selftest(const uint64_t *words_dev, int32_t n, double *out_dev, void *stream)
+{
+    if (n < 0 || (n > 0 && (!words_dev || !out_dev))) return TRMC_ERR_ARG;
+    if (n == 0) return TRMC_OK;
+    trmc::fp64_selftest_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0,
+                                 static_cast<cudaStream_t>(stream)>>>(words_dev, n, out_dev);
+    return cudaGetLastError() == cudaSuccess ? TRMC_OK : TRMC_ERR_CUDA;
+}

@@ -26,7 +26,8 @@ REPORT_LEN = 16 + 3 * (MCAP + 2)
 REPORT_FIELDS = ["N", "passes", "m_first", "m_last", "m_next", "R_final", "N0", "leaves",
                  "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "wbrej"]
 EXPORTS = ["trmc_create", "trmc_destroy", "trmc_last_error", "trmc_check", "trmc_init_cells",
-           "trmc_collide", "trmc_transport", "trmc_moments", "trmc_collide_static", "trmc_set_collide_launch"]
+           "trmc_collide", "trmc_transport", "trmc_moments", "trmc_collide_static", "trmc_set_collide_launch",
+           "trmc_fp64_selftest"]
 STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -112,6 +113,7 @@ def load():
         lib.trmc_set_collide_launch.argtypes = [P, C.c_int32, C.c_int32]
         lib.trmc_collide_static.argtypes = [C.POINTER(State), C.POINTER(CollideParams), C.c_int32, C.c_uint64,
                                             C.c_uint64, C.c_int32, P, P]
+        lib.trmc_fp64_selftest.argtypes = [P, C.c_int32, P, P]
         for f in EXPORTS:
             if f != "trmc_last_error":
                 getattr(lib, f).restype = C.c_int
@@ -186,6 +188,13 @@ def trmc_collide_static(state, params, precision, seed, step, max_cell_particles
         why = {ERR_ARG: "invalid argument", ERR_CAPACITY: "a cell of max_cell_particles does not fit the static "
                f"scratch of {STATIC_SCRATCH_BYTES >> 20} MiB", ERR_CUDA: "CUDA call failed"}.get(code, "error")
         raise TrmcError(code, f"trmc_collide_static: {why}")
+
+
+def trmc_fp64_selftest(words, out, stream=None):
+    """words: uint64 (as int64) device tensor [n]; out: float64 device tensor [n, 6]."""
+    code = load().trmc_fp64_selftest(_ptr(words), words.numel(), _ptr(out), _stream(stream))
+    if code != OK:
+        raise TrmcError(code, "trmc_fp64_selftest failed")
 
 
 # ---------------------------------------------------------------- helpers
