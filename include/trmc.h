@@ -262,6 +262,17 @@ trmc_status trmc_collide_static(trmc_state *state, const trmc_collide_params *pa
  * on the stream; TRMC_ERR_ARG for a negative n or NULL arrays. */
 trmc_status trmc_fp64_selftest(const uint64_t *words_dev, int32_t n, double *out_dev, void *stream);
 
+/* ---- self-test of the split's integer Iround --------------------------------
+ * The paper has no counterpart: a check of the library's integer evaluation of
+ * the split count of Alg. 4.2, Iround(q R) = floor(x) + [u < x - floor(x)] with
+ * x = q R rounded as one FP64 multiply and u = K 2^-53, which the collision
+ * step uses in place of FP64 arithmetic.  For i < n: q_dev[i] in [0, 1],
+ * R_dev[i] in [1, 2^31), K_dev[i] < 2^53 (all device); out_dev[i] (device)
+ * receives the count.  Asynchronous on the stream; TRMC_ERR_ARG for a
+ * negative n or NULL arrays. */
+trmc_status trmc_split_selftest(const double *q_dev, const int32_t *R_dev, const uint64_t *K_dev, int32_t n,
+                                int32_t *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

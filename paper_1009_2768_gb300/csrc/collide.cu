@@ -70,9 +70,9 @@ struct Args {
 
 template <typename Real>
 struct Sh {
-    int32_t Nq[NLEV], Nn[NLEV], D[NLEV], C[NLEV], out[NLEV], O[NLEV], IB[NLEV];
+    int32_t Nq[NLEV], D[NLEV], C[NLEV], O[NLEV], IB[NLEV];
     int32_t Pn[kMC + 1];
-    double uS[NLEV], uP[NLEV];
+    uint64_t uSK[NLEV];              // split uniforms of the levels, u = uSK 2^-53
     U64x4 keys[NLEV];
     double red[kRedScratch];
     uint8_t lab[NLEV][kPreLabels];   // labels of the first kPreLabels collisions of each level
@@ -81,7 +81,7 @@ struct Sh {
     int32_t scan[33], nrej;
     uint32_t coin[3];                // parity coin of level lv: bit lv (uP[lv] < 1/2)
     int32_t cand[4], cand_ok[4], cand_next;
-    int32_t feas, pdrop, psurp, pdrop_tot, psurp_tot, skip, cont, m_top, m_first, n0_first;
+    int32_t feas, pdrop_tot, psurp_tot, skip, cont, m_top, m_first, n0_first;
     double q, Sigma, U[3], P[3], E, S_pre, dP[3], dE, dS, Pp[3], Ep, Sp, carry[4], Pt[3], Et;
     double alpha, dt, eps, rho_scale;
     uint64_t problem, lcell;
@@ -147,6 +147,42 @@ __device__ __forceinline__ int block_flag_scan(bool flag, int &excl, int32_t *sc
     const int total = scratch[nw - 1];
     __syncthreads();
     return total;
+}
+
+// ---- Iround of the split in integer arithmetic -------------------------------
+// Alg. 4.2 gives level n the count Iround(q R), R the particles not yet
+// placed, and the FP64 reference evaluates it as x = fl(q R) (round to
+// nearest, ties to even), then floor(x) + [u < x - floor(x)] with the level's
+// uniform u = K 2^-53.  The same value from the bits of q: the exact product
+// M R of q's 53-bit significand and R (at most 84 bits), rounded to 53 bits
+// like the FP64 multiply, then the integer part and the fraction compared
+// with K, all exact.  q is a probability (0 <= q <= 1) and 1 <= R < 2^31.
+// This keeps the sequential split off GB300's FP64 pipe (2 lanes/clk/SM).
+__device__ __forceinline__ int iround_q(uint64_t qb, uint32_t R, uint64_t K)
+{
+    const uint32_t E = uint32_t(qb >> 52) & 0x7FFu;
+    if (E == 0) return (qb != 0 && K == 0) ? 1 : 0;      // q = 0, or subnormal: 0 <= x < 2^-53
+    if (E >= 1023) return int(R);                          // q = 1: x = R
+    const uint64_t M = (qb & ((1ull << 52) - 1ull)) | (1ull << 52);
+    const uint64_t lo = M * uint64_t(R), hi = __umul64hi(M, uint64_t(R));
+    const int L = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);   // bits of M R
+    int s = L - 53;                                        // bits rounded off, 0..31
+    uint64_t X = lo;
+    if (s > 0) {
+        X = (lo >> s) | (hi << (64 - s));
+        const uint64_t dropped = lo & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+        if (dropped > half || (dropped == half && (X & 1ull))) {
+            if (++X == (1ull << 53)) { X = 1ull << 52; ++s; }
+        }
+    }
+    const int d = 1075 - int(E) - s;                       // x = X 2^-d, d >= 22
+    const uint64_t fl = d < 64 ? (X >> d) : 0ull;
+    const uint64_t Fr = d < 64 ? (X & ((1ull << d) - 1ull)) : X;   // x - floor(x) = Fr 2^-d
+    bool up;
+    if (d <= 53) up = K < (Fr << (53 - d));                // K 2^-53 < Fr 2^-d
+    else if (Fr == 0) up = false;
+    else up = (d - 53 >= 64) ? (K == 0) : (K <= ((Fr - 1ull) >> (d - 53)));   // K 2^(d-53) <= Fr - 1
+    return int(fl) + (up ? 1 : 0);
 }
 
 // ---- FP64 angles and logarithms of the 53-bit uniforms ----------------------
@@ -336,7 +372,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         if (m0 < 1) m0 = 1;
         if (m0 > prm.m_cap) m0 = prm.m_cap;
         sh.m = m0; sh.m_next = m0; sh.m_first = m0; sh.lo = 0; sh.pass = 0; sh.npart = n; sh.skip = 0;
-        sh.feas = sh.pdrop = sh.psurp = sh.pdrop_tot = sh.psurp_tot = 0;
+        sh.feas = sh.pdrop_tot = sh.psurp_tot = 0;
         sh.n0_prev = 0; sh.D0_prev = 0; sh.nrej = 0;
         sh.dP[0] = sh.dP[1] = sh.dP[2] = 0.0; sh.dE = 0.0; sh.dS = 0.0;
         for (int j = 0; j < 4; ++j) sh.carry[j] = a.cell_carry ? a.cell_carry[4 * int64_t(cell) + j] : 0.0;
@@ -470,235 +506,285 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
 
         // One attempt of the tree plan (warp 0) on depth sh.m_top, then, if the
         // trees find enough leaves, the layout of the pass's buffers; otherwise
-        // sh.cont is set and sh.m_top holds the next depth to try.
+        // sh.cont is set and sh.m_top holds the next depth to try.  The plan
+        // lives in registers: lane j holds levels j and j + 32 (quota, demand,
+        // collisions, outputs); level 64, the deepest possible, never receives
+        // demand and is held by every lane.
         auto plan_attempt = [&]() {
-            // Tree plan, top level first, with the leaf-feasibility loop.  Levels
-            // with neither quota nor demand have no collision and are skipped;
-            // Nn is read-only below because every lane reads it to skip.
-            if (!sh.skip) {
-                for (int j = lane; j < NLEV; j += 32) {
-                    sh.D[j] = 0; sh.C[j] = 0; sh.out[j] = 0;
-                    sh.Nn[j] = (j <= sh.m_top) ? sh.Nq[j] : 0;
+            if (sh.skip) return;
+            constexpr unsigned FULL = 0xffffffffu;
+            const int m_top = sh.m_top;
+            const int jA = lane, jB = lane + 32;
+            const int nA = jA <= m_top ? sh.Nq[jA] : 0, nB = jB <= m_top ? sh.Nq[jB] : 0;
+            const int n64 = m_top >= 64 ? sh.Nq[64] : 0;
+            int dA = 0, dB = 0, cA = 0, cB = 0, oA = 0, oB = 0, c64 = 0, o64 = 0, pdrop = 0, psurp = 0;
+            const uint32_t coin0 = sh.coin[0], coin1 = sh.coin[1], coin2 = sh.coin[2];
+            // highest level in 1..top with a quota or a demand (0: none); levels
+            // without either have no collision and are skipped
+            auto next_level = [&](int top) -> int {
+                if (top >= 64 && n64 > 0) return 64;
+                const unsigned bB = __ballot_sync(FULL, jB <= top && nB + dB > 0);
+                if (bB) return 63 - __clz(bB);
+                const unsigned bA = __ballot_sync(FULL, jA >= 1 && jA <= top && nA + dA > 0);
+                return bA ? 31 - __clz(bA) : 0;
+            };
+            for (int lv = next_level(m_top); lv >= 1; lv = next_level(lv - 1)) {
+                int nl = n64, dl = 0;
+                if (lv < 64) {
+                    nl = __shfl_sync(FULL, lv >= 32 ? nB : nA, lv & 31);
+                    dl = __shfl_sync(FULL, lv >= 32 ? dB : dA, lv & 31);
                 }
-                if (lane == 0) { sh.pdrop = 0; sh.psurp = 0; }
-                __syncwarp();
-                const int m_top = sh.m_top;
-                int lv = m_top;
-                while (lv >= 1 && sh.Nn[lv] + sh.D[lv] == 0) --lv;
-                while (lv >= 1) {
-                    if (lane == 0) {
-                        int T = sh.Nn[lv] + sh.D[lv];
-                        if (T & 1) {
-                            if (sh.Nn[lv] >= 1 && ((sh.coin[lv >> 5] >> (lv & 31)) & 1u)) { T -= 1; sh.pdrop++; }
-                            else { T += 1; sh.psurp++; }
-                        }
-                        sh.C[lv] = T >> 1;
+                int T = nl + dl;
+                if (T & 1) {
+                    const uint32_t cw = lv < 32 ? coin0 : lv < 64 ? coin1 : coin2;
+                    if (nl >= 1 && ((cw >> (lv & 31)) & 1u)) { T -= 1; ++pdrop; }
+                    else { T += 1; ++psurp; }
+                }
+                const int Cn = T >> 1;
+                int32_t *row = sh.Mt + tri(lv), *srow = sh.St + tri(lv);
+                // slot bases of this level's consumers: the demand of the levels above
+                if (jA < lv) srow[jA] = dA;
+                if (jB < lv) srow[jB] = dB;
+                // r: collisions labelled k = j; s: collisions whose second input
+                // is of level j (k = lv - 1 - j)
+                int rA = 0, rB = 0, sA = 0, sB = 0;
+                if (Cn <= kPreLabels) {
+                    const uint64_t L0 = *reinterpret_cast<const uint64_t *>(&sh.lab[lv][0]);
+                    const uint64_t L1 = *reinterpret_cast<const uint64_t *>(&sh.lab[lv][8]);
+                    for (int c = 0; c < Cn; ++c) {
+                        const int k = int(((c < 8 ? L0 : L1) >> (8 * (c & 7))) & 0xFFu), j = lv - 1 - k;
+                        rA += k == jA; rB += k == jB;
+                        sA += j == jA; sB += j == jB;
                     }
-                    int32_t *row = sh.Mt + tri(lv);
-                    int32_t *srow = sh.St + tri(lv);
-                    for (int k = lane; k < lv; k += 32) row[k] = 0;
+                    if (jA < lv) row[jA] = rA;
+                    if (jB < lv) row[jB] = rB;
+                } else {
+                    if (jA < lv) row[jA] = 0;
+                    if (jB < lv) row[jB] = 0;
                     __syncwarp();
-                    const int Cn = sh.C[lv];
-                    if (Cn <= kPreLabels) {
-                        // few collisions: only the demand slots their labels touch
-                        // change; their slot bases are read first, then the counts
-                        if (lane < Cn) {
-                            const int k = sh.lab[lv][lane], j = lv - 1 - k;
-                            srow[k] = sh.D[k];
-                            srow[j] = sh.D[j];
-                        }
-                        __syncwarp();
-                        if (lane < Cn) {
-                            const int k = sh.lab[lv][lane];
-                            atomicAdd(&row[k], 1);
-                            atomicAdd(&sh.D[k], 1);
-                            atomicAdd(&sh.D[lv - 1 - k], 1);
-                        }
-                    } else {
-                        for (int c = lane; c < kPreLabels; c += 32) atomicAdd(&row[sh.lab[lv][c]], 1);
-                        for (int g = kPreLabels / 4 + lane; g < (Cn + 3) >> 2; g += 32) {
-                            const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
+                    if (lane < kPreLabels) atomicAdd(&row[sh.lab[lv][lane]], 1);
+                    for (int g = kPreLabels / 4 + lane; g < (Cn + 3) >> 2; g += 32) {
+                        const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                if (4 * g + j < Cn) atomicAdd(&row[below(w.w[j], uint32_t(lv))], 1);
-                        }
-                        __syncwarp();
-                        // slot bases of this level's consumers, then the demand it adds
-                        for (int k = lane; k < lv; k += 32) {
-                            const int d = sh.D[k];
-                            srow[k] = d;
-                            sh.D[k] = d + row[k] + row[lv - 1 - k];
-                        }
+                        for (int j = 0; j < 4; ++j)
+                            if (4 * g + j < Cn) atomicAdd(&row[below(w.w[j], uint32_t(lv))], 1);
                     }
                     __syncwarp();
-                    if (lane == 0) sh.out[lv] = 2 * Cn - sh.D[lv];
-                    __syncwarp();
-                    --lv;
-                    while (lv >= 1 && sh.Nn[lv] + sh.D[lv] == 0) --lv;
+                    if (jA < lv) { rA = row[jA]; sA = row[lv - 1 - jA]; }
+                    if (jB < lv) { rB = row[jB]; sB = row[lv - 1 - jB]; }
                 }
-                if (lane == 0) {
-                    const int n0q = sh.Nq[0];
-                    const int A = npart - n0q;
-                    sh.cont = 0;
-                    if (sh.D[0] <= A) { sh.n0 = n0q; sh.D0 = sh.D[0]; sh.R = A - sh.D[0]; }
-                    else if (sh.D[0] - A <= n0q) { sh.n0 = n0q - (sh.D[0] - A); sh.D0 = sh.D[0]; sh.R = 0; }
-                    else {
-                        // Lowering the depth by one level at a time (the rule) gives the
-                        // same plan again while the removed top level is empty, so go
-                        // straight below the highest level with a quota; the number of
-                        // one-level reductions is still counted.
-                        int h = m_top;
-                        while (h >= 1 && sh.Nq[h] == 0) --h;
-                        const int nt = (h >= 1 ? h : 1) - 1;
-                        sh.feas += m_top - nt;
-                        sh.m_top = nt;
-                        sh.cont = 1;
-                    }
+                dA += rA + sA;
+                dB += rB + sB;
+                if (lv == 64) { c64 = Cn; o64 = 2 * Cn - dl; }
+                else if (lane == (lv & 31)) {
+                    if (lv < 32) { cA = Cn; oA = 2 * Cn - dl; }
+                    else { cB = Cn; oB = 2 * Cn - dl; }
                 }
-                __syncwarp();
             }
-            // layout of the product buffers; output / input offsets
-            if (lane == 0 && !sh.skip && !sh.cont) {
-                const int m = sh.m_top;
-                sh.pdrop_tot += sh.pdrop;
-                sh.psurp_tot += sh.psurp;
+            // leaf feasibility (Sec. 4.1: a tree cannot be longer than the cell)
+            const int d0 = __shfl_sync(FULL, dA, 0);
+            const int n0q = sh.Nq[0], A = npart - n0q;
+            int n0 = n0q, R = 0;
+            if (d0 <= A) {
+                R = A - d0;
+            } else if (d0 - A <= n0q) {
+                n0 = n0q - (d0 - A);
+            } else {
+                // Lowering the depth by one level at a time (the rule) gives the
+                // same plan again while the removed top level is empty, so go
+                // straight below the highest level with a quota; the number of
+                // one-level reductions is still counted.
+                const unsigned qB = __ballot_sync(FULL, jB <= m_top && nB > 0);
+                const unsigned qA = __ballot_sync(FULL, jA >= 1 && jA <= m_top && nA > 0);
+                const int h = n64 > 0 ? 64 : qB ? 63 - __clz(qB) : qA ? 31 - __clz(qA) : 0;
+                const int nt = (h >= 1 ? h : 1) - 1;
+                if (lane == 0) { sh.feas += m_top - nt; sh.m_top = nt; sh.cont = 1; }
+                __syncwarp();
+                return;
+            }
+            // layout of the pass: output offsets O and consumer-slot offsets IB
+            // of every level (prefix sums over levels 1..m)
+            const int m = m_top;
+            const bool inA = jA >= 1 && jA <= m, inB = jB <= m;
+            int pO = inA ? oA : 0, qO = inB ? oB : 0, pI = inA ? dA : 0, qI = inB ? dB : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t0 = __shfl_up_sync(FULL, pO, o), t1 = __shfl_up_sync(FULL, qO, o);
+                const int t2 = __shfl_up_sync(FULL, pI, o), t3 = __shfl_up_sync(FULL, qI, o);
+                if (lane >= o) { pO += t0; qO += t1; pI += t2; qI += t3; }
+            }
+            qO += __shfl_sync(FULL, pO, 31);
+            qI += __shfl_sync(FULL, pI, 31);
+            const int O63 = __shfl_sync(FULL, qO, 31), I63 = __shfl_sync(FULL, qI, 31);
+            const int Otot = O63 + (m >= 64 ? o64 : 0), Dge1 = I63;     // D of level 64 is 0
+            if (jA < m + 1) { sh.O[jA + 1] = pO; sh.IB[jA + 1] = pI; }
+            if (jB < m + 1) { sh.O[jB + 1] = qO; sh.IB[jB + 1] = qI; }
+            if (lane == 0 && m >= 64) { sh.O[65] = Otot; sh.IB[65] = Dge1; }
+            sh.D[jA] = dA; sh.D[jB] = dB; sh.C[jA] = cA; sh.C[jB] = cB;
+            if (lane == 0) { sh.D[64] = 0; sh.D[65] = 0; sh.C[64] = c64; sh.C[65] = 0; }
+            // deep levels (at most kWarpLevel collisions) in ascending order with
+            // the offsets of their collisions in the per-collision records
+            const bool wA = inA && cA > 0 && cA <= kWarpLevel, wB = inB && cB > 0 && cB <= kWarpLevel;
+            const bool w64 = m >= 64 && c64 > 0 && c64 <= kWarpLevel;
+            const unsigned bwA = __ballot_sync(FULL, wA), bwB = __ballot_sync(FULL, wB);
+            const unsigned ltm = (1u << lane) - 1u;
+            const int iA = __popc(bwA & ltm), iB = __popc(bwA) + __popc(bwB & ltm);
+            const int nWL = __popc(bwA) + __popc(bwB) + (w64 ? 1 : 0);
+            int eA = wA ? cA : 0, eB = wB ? cB : 0;
+            const int ownA = eA, ownB = eB;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t0 = __shfl_up_sync(FULL, eA, o), t1 = __shfl_up_sync(FULL, eB, o);
+                if (lane >= o) { eA += t0; eB += t1; }
+            }
+            eB += __shfl_sync(FULL, eA, 31);
+            const int W63 = __shfl_sync(FULL, eB, 31), W = W63 + (w64 ? c64 : 0);
+            if (wA) { sh.WL[iA] = jA; sh.WB[iA] = eA - ownA; }
+            if (wB) { sh.WL[iB] = jB; sh.WB[iB] = eB - ownB; }
+            // the tail: deep levels above the highest level of more than
+            // kWarpLevel collisions (LB)
+            const unsigned lbB = __ballot_sync(FULL, inB && cB > kWarpLevel);
+            const unsigned lbA = __ballot_sync(FULL, inA && cA > kWarpLevel);
+            const int LB = (m >= 64 && c64 > kWarpLevel) ? 64 : lbB ? 63 - __clz(lbB) : lbA ? 31 - __clz(lbA) : 0;
+            const int jt = __popc(__ballot_sync(FULL, wA && jA <= LB)) + __popc(__ballot_sync(FULL, wB && jB <= LB));
+            const int WBjt = __reduce_add_sync(FULL, unsigned((wA && jA <= LB ? cA : 0) + (wB && jB <= LB ? cB : 0)));
+            const int IBlb = __reduce_add_sync(FULL, unsigned((jA >= 1 && jA <= LB ? dA : 0) + (jB <= LB ? dB : 0)));
+            // invariants of a consistent plan; a violation would index the
+            // buffers out of range, so the cell is left unchanged instead
+            const bool bad = (inA && (oA < 0 || cA < 0)) || (inB && (oB < 0 || cB < 0));
+            const bool ok = n0 >= 0 && d0 >= 0 && R >= 0 && n0 + d0 + R == npart && Otot == d0 &&
+                            !__any_sync(FULL, bad) && (m < 64 || (o64 >= 0 && c64 >= 0));
+            if (lane == 0) {
+                sh.cont = 0;
+                sh.n0 = n0; sh.D0 = d0; sh.R = R;
+                sh.pdrop_tot += pdrop;
+                sh.psurp_tot += psurp;
                 sh.m_eff = m;
-                sh.O[1] = 0; sh.IB[1] = 0;
-                for (int lv = 1; lv <= m; ++lv) { sh.O[lv + 1] = sh.O[lv] + sh.out[lv]; sh.IB[lv + 1] = sh.IB[lv] + sh.D[lv]; }
-                sh.Dge1 = sh.IB[m + 1];
+                sh.Dge1 = Dge1;
+                if (w64) { sh.WL[nWL - 1] = 64; sh.WB[nWL - 1] = W63; }
+                sh.WB[nWL] = W;
                 sh.IBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
-                                                   3 * size_t(sh.Dge1 + 1) * sizeof(Real)));
+                                                   3 * size_t(Dge1 + 1) * sizeof(Real)));
                 sh.OBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
-                                                   3 * size_t(sh.D0 + 1) * sizeof(Real)));
+                                                   3 * size_t(d0 + 1) * sizeof(Real)));
                 if (!sh.IBuf || !sh.OBuf) sh.skip = 1;
                 sh.ILBuf = sh.OLBuf = nullptr; sh.ext = nullptr;
                 if (prm.trunc == TRMC_TRUNC_WB) {
                     sh.ILBuf = static_cast<double *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
-                                                          8 * size_t(sh.Dge1 + 1)));
+                                                          8 * size_t(Dge1 + 1)));
                     sh.OLBuf = static_cast<double *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
-                                                          8 * size_t(sh.D0 + 1)));
+                                                          8 * size_t(d0 + 1)));
                     sh.ext = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
-                                                         4 * size_t(sh.D0 + 1)));
+                                                         4 * size_t(d0 + 1)));
                     if (!sh.ILBuf || !sh.OLBuf || !sh.ext) sh.skip = 1;
                 }
                 // records of the deep levels' collisions; without room for them
                 // the waves compute everything in place (same results)
-                int w = 0;
-                sh.nWL = 0;
-                for (int lv = 1; lv <= m; ++lv)
-                    if (sh.C[lv] > 0 && sh.C[lv] <= kWarpLevel) { sh.WL[sh.nWL] = lv; sh.WB[sh.nWL++] = w; w += sh.C[lv]; }
-                sh.WB[sh.nWL] = w;
-                if (w > 0) {
+                int nwl = nWL;
+                if (W > 0) {
                     char *s0 = sh.pass_smem, *g0 = sh.pass_slab;
                     const size_t sc0 = sh.pass_smem_cap, gc0 = sh.pass_slab_cap;
                     sh.LP = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
                                                         4 * size_t(tri(m + 1) + 1)));
-                    sh.psrc = static_cast<int2 *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 8 * size_t(w)));
-                    sh.pdst = static_cast<int2 *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 8 * size_t(w)));
+                    sh.psrc = static_cast<int2 *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 8 * size_t(W)));
+                    sh.pdst = static_cast<int2 *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 8 * size_t(W)));
                     sh.prnd = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
-                                                       4 * size_t(w) * sizeof(Real)));
+                                                       4 * size_t(W) * sizeof(Real)));
                     if (!sh.LP || !sh.psrc || !sh.pdst || !sh.prnd) {
                         sh.pass_smem = s0; sh.pass_slab = g0; sh.pass_smem_cap = sc0; sh.pass_slab_cap = gc0;
-                        sh.nWL = 0;
+                        nwl = 0;
                     }
                 }
-                // the tail, run in dependency order when there is room for its maps
-                sh.LB = 0;
-                for (int lv = 1; lv <= m; ++lv)
-                    if (sh.C[lv] > kWarpLevel) sh.LB = lv;
+                sh.nWL = nwl;
+                sh.LB = LB;
+                // the tail runs in dependency order when there is room for its maps
                 sh.ntail = 0;
-                if (sh.nWL > 0) {
-                    int jt = 0;
-                    while (jt < sh.nWL && sh.WL[jt] <= sh.LB) ++jt;
-                    const int nt = sh.WB[sh.nWL] - sh.WB[jt];
-                    const int nslots = sh.IB[m + 1] - sh.IB[sh.LB + 1];
-                    if (sh.nWL - jt >= 2 && nt > 0) {
-                        char *s0 = sh.pass_smem, *g0 = sh.pass_slab;
-                        const size_t sc0 = sh.pass_smem_cap, gc0 = sh.pass_slab_cap;
-                        sh.prodOf = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab,
-                                                                sh.pass_slab_cap, 4 * size_t(nslots + 1)));
-                        sh.done = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab,
-                                                              sh.pass_slab_cap, 4 * size_t(nt)));
-                        if (sh.prodOf && sh.done) {
-                            sh.ntail = nt; sh.tail0 = sh.WB[jt]; sh.tailbase = sh.IB[sh.LB + 1];
-                        } else {
-                            sh.pass_smem = s0; sh.pass_slab = g0; sh.pass_smem_cap = sc0; sh.pass_slab_cap = gc0;
-                        }
+                const int nt = W - WBjt, nslots = Dge1 - IBlb;
+                if (nwl > 0 && nwl - jt >= 2 && nt > 0) {
+                    char *s0 = sh.pass_smem, *g0 = sh.pass_slab;
+                    const size_t sc0 = sh.pass_smem_cap, gc0 = sh.pass_slab_cap;
+                    sh.prodOf = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab,
+                                                            sh.pass_slab_cap, 4 * size_t(nslots + 1)));
+                    sh.done = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab,
+                                                          sh.pass_slab_cap, 4 * size_t(nt)));
+                    if (sh.prodOf && sh.done) {
+                        sh.ntail = nt; sh.tail0 = WBjt; sh.tailbase = IBlb;
+                    } else {
+                        sh.pass_smem = s0; sh.pass_slab = g0; sh.pass_smem_cap = sc0; sh.pass_slab_cap = gc0;
                     }
                 }
-                // invariants of a consistent plan; a violation would index the
-                // buffers out of range, so the cell is left unchanged instead
-                bool ok = sh.n0 >= 0 && sh.D0 >= 0 && sh.R >= 0 && sh.n0 + sh.D0 + sh.R == npart &&
-                          sh.O[m + 1] == sh.D0;
-                for (int lv = 1; lv <= m; ++lv) ok = ok && sh.out[lv] >= 0 && sh.C[lv] >= 0;
-                if (!ok) { sh.skip = 2; }
-                if (pass == 0) sh.n0_first = sh.n0;
-                if (a.report && pass == 0) {
-                    int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
-                    r[6] = sh.n0;
-                    r[14] = m;
-                    for (int j = 0; j < NLEV; ++j) {
-                        r[16 + j] = sh.Nq[j];
-                        r[16 + NLEV + j] = sh.C[j];
-                        r[16 + 2 * NLEV + j] = sh.D[j];
-                    }
+                if (!ok) sh.skip = 2;
+                if (pass == 0) sh.n0_first = n0;
+            }
+            if (a.report && pass == 0) {
+                int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
+                if (lane == 0) { r[6] = n0; r[14] = m; }
+                for (int j = lane; j < NLEV; j += 32) r[16 + j] = sh.Nq[j];
+                r[16 + NLEV + jA] = cA; r[16 + NLEV + jB] = cB;
+                r[16 + 2 * NLEV + jA] = dA; r[16 + 2 * NLEV + jB] = dB;
+                if (lane == 0) {
+                    r[16 + NLEV + 64] = c64; r[16 + NLEV + 65] = 0;
+                    r[16 + 2 * NLEV + 64] = 0; r[16 + 2 * NLEV + 65] = 0;
                 }
             }
             __syncwarp();
         };
-        // 2-3. Warp 0 draws the split (Alg. 4.2) and builds the tree plan with
-        //      warp-level synchronisation only; warps 1.. meanwhile compute the
-        //      role permutation of the participants, which the plan does not
-        //      change (only where its ranks are cut into roles).
-        if (warp == 0) {
-            {
-                const int lo = sh.lo, m = sh.m;
-                for (int t = lane; t <= m - lo; t += 32)
-                    sh.uS[lo + t] = u01(rng.draw(uint64_t(lo + t), 0, uint32_t(pass), TAG_SPLIT).w[0]);
-                for (int t = lane; t < m; t += 32) {
-                    sh.uP[t + 1] = u01(rng.draw(uint64_t(t + 1), 0, uint32_t(pass), TAG_PARITY).w[0]);
-                    sh.keys[t + 1] = rng.draw(0, uint64_t(t + 1), uint32_t(pass), TAG_PERMK);
-                }
-                // the first kPreLabels labels of every level, off the plan's critical path
-                for (int t = lane; t < m * (kPreLabels / 4); t += 32) {
-                    const int lv = 1 + t / (kPreLabels / 4), g = t % (kPreLabels / 4);
-                    const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) sh.lab[lv][4 * g + j] = uint8_t(below(w.w[j], uint32_t(lv)));
-                }
+        // 2. Split (Alg. 4.2): one uniform per level, drawn by the whole CTA.
+        //    Every warp then runs the short sequential recurrence itself, in
+        //    integer arithmetic that reproduces the FP64 Iround bit for bit
+        //    (iround_q), so that each knows the depth the split reached.
+        {
+            const int lo = sh.lo, m = sh.m;
+            for (int t = tid; t <= m - lo; t += bs)
+                sh.uSK[lo + t] = rng.draw(uint64_t(lo + t), 0, uint32_t(pass), TAG_SPLIT).w[0] >> 11;
+            for (int j = tid; j < NLEV; j += bs) sh.Nq[j] = 0;
+            if (tid < 3) sh.coin[tid] = 0u;
+        }
+        __syncthreads();
+        int m_split;
+        {
+            const uint64_t qb = uint64_t(__double_as_longlong(sh.q));
+            const int lo = sh.lo, m = sh.m;
+            int rem = npart;
+            m_split = m;
+            for (int lv = lo; lv <= m; ++lv) {
+                const int c = iround_q(qb, uint32_t(rem), sh.uSK[lv]);
+                if (tid == 0) sh.Nq[lv] = c;
+                rem -= c;
+                if (rem == 0) { m_split = lv; break; }
             }
-            __syncwarp();
-            // the parity coins as bits: the plan then needs no FP64 compare
-            for (int t0 = 0; t0 < NLEV; t0 += 32) {
-                const int lv = t0 + lane;
-                const unsigned b = __ballot_sync(0xffffffffu, lv >= 1 && lv <= sh.m && sh.uP[lv] < 0.5);
-                if (lane == 0) sh.coin[t0 >> 5] = b;
-            }
-            __syncwarp();
-            if (lane == 0) {
-                for (int j = 0; j < NLEV; ++j) sh.Nq[j] = 0;
-                int rem = npart, m_eff = sh.m;
-                for (int lv = sh.lo; lv <= sh.m; ++lv) {
-                    const double x = sh.q * double(rem);
-                    const double fl = floor(x);
-                    const int c = int(fl) + ((sh.uS[lv] < x - fl) ? 1 : 0);
-                    sh.Nq[lv] = c;
-                    rem -= c;
-                    if (rem == 0) { m_eff = lv; break; }
-                }
-                if (rem > 0) sh.Nq[sh.m + 1] = rem;
-                sh.m_eff = m_eff;
-                sh.m_top = m_eff;
+            if (tid == 0) {
+                if (rem > 0) sh.Nq[m + 1] = rem;
+                sh.m_eff = m_split;
+                sh.m_top = m_split;
                 sh.pass_smem = sh.smem_rest; sh.pass_smem_cap = sh.smem_rest_cap;
                 sh.pass_slab = sh.slab_rest; sh.pass_slab_cap = sh.slab_rest_cap;
-                const size_t T = size_t(tri(m_eff + 1));
+                const size_t T = size_t(tri(m_split + 1));
                 sh.Mt = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
                 sh.St = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
                 if (!sh.Mt || !sh.St) sh.skip = 1;
             }
-            __syncwarp();
-            plan_attempt();
         }
+        // 3. The other draws of levels 1..m_eff, six per level: the parity coin
+        //    (odd counts, Alg. 4.3), the key of the level's product permutation
+        //    and its first kPreLabels labels k (Alg. 4.1), four per draw.
+        for (int t = tid; t < 6 * m_split; t += bs) {
+            const int lv = 1 + t / 6, kind = t - 6 * (lv - 1);
+            const uint64_t idx = kind == 0 ? uint64_t(lv) : kind == 1 ? 0ull : uint64_t(kind - 2);
+            const uint64_t aux = kind == 0 ? 0ull : uint64_t(lv);
+            const uint32_t tag = kind == 0 ? TAG_PARITY : kind == 1 ? TAG_PERMK : TAG_KSEL;
+            const U64x4 w = rng.draw(idx, aux, uint32_t(pass), tag);
+            if (kind == 0) {
+                if ((w.w[0] >> 63) == 0) atomicOr(&sh.coin[lv >> 5], 1u << (lv & 31));   // u < 1/2
+            } else if (kind == 1) {
+                sh.keys[lv] = w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) sh.lab[lv][4 * (kind - 2) + j] = uint8_t(below(w.w[j], uint32_t(lv)));
+            }
+        }
+        __syncthreads();
+        if (warp == 0) plan_attempt();
         // 4. roles: a permutation of the participants (warps 1.., or warp 0
         //    afterwards when the CTA is a single warp)
         if (warp > 0 || bs == 32) {
@@ -1621,5 +1707,26 @@ extern "C" trmc_status trmc_fp64_selftest(const uint64_t *words_dev, int32_t n, 
     if (n == 0) return TRMC_OK;
     trmc::fp64_selftest_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0,
                                  static_cast<cudaStream_t>(stream)>>>(words_dev, n, out_dev);
+    return cudaGetLastError() == cudaSuccess ? TRMC_OK : TRMC_ERR_CUDA;
+}
+
+// ---- self-test of the split's integer Iround ----------------------------------
+namespace trmc {
+namespace {
+__global__ void split_selftest_kernel(const double *q, const int32_t *R, const uint64_t *K, int n, int32_t *out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = iround_q(uint64_t(__double_as_longlong(q[i])), uint32_t(R[i]), K[i]);
+}
+}  // namespace
+}  // namespace trmc
+
+extern "C" trmc_status trmc_split_selftest(const double *q_dev, const int32_t *R_dev, const uint64_t *K_dev, int32_t n,
+                                           int32_t *out_dev, void *stream)
+{
+    if (n < 0 || (n > 0 && (!q_dev || !R_dev || !K_dev || !out_dev))) return TRMC_ERR_ARG;
+    if (n == 0) return TRMC_OK;
+    trmc::split_selftest_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0,
+                                  static_cast<cudaStream_t>(stream)>>>(q_dev, R_dev, K_dev, n, out_dev);
     return cudaGetLastError() == cudaSuccess ? TRMC_OK : TRMC_ERR_CUDA;
 }

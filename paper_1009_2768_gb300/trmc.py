@@ -27,7 +27,7 @@ REPORT_FIELDS = ["N", "passes", "m_first", "m_last", "m_next", "R_final", "N0", 
                  "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "wbrej"]
 EXPORTS = ["trmc_create", "trmc_destroy", "trmc_last_error", "trmc_check", "trmc_init_cells",
            "trmc_collide", "trmc_transport", "trmc_moments", "trmc_collide_static", "trmc_set_collide_launch",
-           "trmc_fp64_selftest"]
+           "trmc_fp64_selftest", "trmc_split_selftest"]
 STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -114,6 +114,7 @@ def load():
         lib.trmc_collide_static.argtypes = [C.POINTER(State), C.POINTER(CollideParams), C.c_int32, C.c_uint64,
                                             C.c_uint64, C.c_int32, P, P]
         lib.trmc_fp64_selftest.argtypes = [P, C.c_int32, P, P]
+        lib.trmc_split_selftest.argtypes = [P, P, P, C.c_int32, P, P]
         for f in EXPORTS:
             if f != "trmc_last_error":
                 getattr(lib, f).restype = C.c_int
@@ -195,6 +196,13 @@ def trmc_fp64_selftest(words, out, stream=None):
     code = load().trmc_fp64_selftest(_ptr(words), words.numel(), _ptr(out), _stream(stream))
     if code != OK:
         raise TrmcError(code, "trmc_fp64_selftest failed")
+
+
+def trmc_split_selftest(q, R, K, out, stream=None):
+    """q: float64, R: int32, K: uint64 (as int64), out: int32 device tensors [n]."""
+    code = load().trmc_split_selftest(_ptr(q), _ptr(R), _ptr(K), q.numel(), _ptr(out), _stream(stream))
+    if code != OK:
+        raise TrmcError(code, "trmc_split_selftest failed")
 
 
 # ---------------------------------------------------------------- helpers
