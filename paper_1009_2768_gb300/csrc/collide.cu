@@ -82,7 +82,7 @@ struct Sh {
     uint32_t coin[3];                // parity coin of level lv: bit lv (uP[lv] < 1/2)
     int32_t cand[4], cand_ok[4], cand_next;
     int32_t feas, pdrop_tot, psurp_tot, skip, cont, m_top, m_first, n0_first;
-    double q, Sigma, U[3], P[3], E, S_pre, dP[3], dE, dS, Pp[3], Ep, Sp, carry[4], Pt[3], Et;
+    double q, Sigma, U[3], P[3], E, S_pre, dP[3], dE, dS, Pp[3], Ep, Sp, carry[4], Pt[3], Et, msc[4];
     double alpha, dt, eps, rho_scale;
     uint64_t problem, lcell;
     U64x4 keyK;
@@ -319,6 +319,72 @@ template <> struct Sum<float> {
     __device__ __forceinline__ double get() const { return double(hi) + double(lo); }
 };
 
+// Block sums of the first K per-thread partial sums of v (K <= 16), in FP64
+// for double partials and as float pairs for compensated float partials;
+// with a divisor (K <= 8), also the totals divided by it.
+template <int K, int N>
+__device__ __forceinline__ void block_sums(const Sum<double> (&v)[N], double (&out)[K], double *red, double div = 0.0,
+                                           double *quot = nullptr)
+{
+#pragma unroll
+    for (int j = 0; j < K; ++j) out[j] = v[j].s;
+    block_sum<K>(out, red, div, quot);
+}
+template <int K, int N>
+__device__ __forceinline__ void block_sums(const Sum<float> (&v)[N], double (&out)[K], double *red, double div = 0.0,
+                                           double *quot = nullptr)
+{
+    float h[K], l[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) { h[j] = v[j].hi; l[j] = v[j].lo; }
+    block_sum_ff<K>(h, l, out, red, div, quot);
+}
+
+// One partial sum and one maximum of non-negative values (as an ordered
+// integer key) over the block, with one pair of barriers.
+template <typename Real>
+__device__ __forceinline__ void block_sum_max(const Sum<Real> &v, long long key, double &sum, long long &mkey,
+                                              double *red)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(FULL, key, o));
+    long long *rk = reinterpret_cast<long long *>(red);
+    if constexpr (sizeof(Real) == 8) {
+        double x = v.s;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+        if (lane == 0) { red[warp] = x; rk[32 + warp] = key; }
+    } else {
+        float h = v.hi, l = v.lo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ff_add(h, l, __shfl_xor_sync(FULL, h, o), __shfl_xor_sync(FULL, l, o));
+        if (lane == 0) { reinterpret_cast<float2 *>(red)[warp] = make_float2(h, l); rk[32 + warp] = key; }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        if (lane == 0) {
+            if constexpr (sizeof(Real) == 8) {
+                double s = 0.0;
+                for (int w = 0; w < nw; ++w) s += red[w];
+                red[256] = s;
+            } else {
+                float h = 0.0f, l = 0.0f;
+                for (int w = 0; w < nw; ++w) { const float2 p = reinterpret_cast<const float2 *>(red)[w]; ff_add(h, l, p.x, p.y); }
+                red[256] = double(h) + double(l);
+            }
+        } else if (lane == 1) {
+            long long m = rk[32];
+            for (int w = 1; w < nw; ++w) m = max(m, rk[32 + w]);
+            rk[257] = m;
+        }
+    }
+    __syncthreads();
+    sum = red[256];
+    mkey = rk[257];
+}
+
 // |v|^2 and the adaptive indicator in the working precision
 template <typename Real>
 __device__ __forceinline__ Real indicator_r(Real x, Real y, Real z, Real Ux, int ind)
@@ -348,7 +414,7 @@ __device__ __forceinline__ void raise_status(int *status, int code, int cell)
 
 template <typename Real>
 __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigned char *dsm, char *slab, int cell,
-                             double (&cnt)[3])
+                             int (&cnt)[3])
 {
     const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
     Real *gx = static_cast<Real *>(a.vx), *gy = static_cast<Real *>(a.vy), *gz = static_cast<Real *>(a.vz);
@@ -415,7 +481,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const double x = double(gx[base + i]), y = double(gy[base + i]), z = double(gz[base + i]);
                 vm = fmax(vm, __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
             }
-            vm = block_max(vm, sh.red);
+            vm = block_max_nonneg(vm, sh.red);
             if (tid == 0) a.cell_vmax2[cell] = vm;
         }
         return;
@@ -431,7 +497,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         const bool rad = prm.trunc == TRMC_TRUNC_RAD;
         const bool need_m4 = rad && prm.indicator == TRMC_IND_M4, need_pxx = rad && prm.indicator == TRMC_IND_PXX;
         const bool need_d2 = sh.alpha != 0.0;
-        Sum<Real> a0, a1, a2, a3, a4;
+        Sum<Real> acc[5];
         constexpr int U = 4;      // loads issued together, ahead of the stores they feed
         for (int i0 = tid; i0 < n; i0 += U * bs) {
             Real x[U], y[U], z[U];
@@ -445,18 +511,26 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const int i = i0 + u * bs;
                 if (i < n) {
                     Vx[i] = x[u]; Vy[i] = y[u]; Vz[i] = z[u];
-                    a0.add(x[u]); a1.add(y[u]); a2.add(z[u]);
-                    a3.add_sq3(x[u], y[u], z[u]);
+                    acc[0].add(x[u]); acc[1].add(y[u]); acc[2].add(z[u]);
+                    acc[3].add_sq3(x[u], y[u], z[u]);
                     if (need_m4) {
                         const Real e = x[u] * x[u] + y[u] * y[u] + z[u] * z[u];
-                        a4.add(e * e);
+                        acc[4].add(e * e);
                     }
                 }
             }
         }
-        double s[5] = {a0.get(), a1.get(), a2.get(), a3.get(), a4.get()};
-        block_sum<5>(s, sh.red);
-        const double U0 = s[0] / double(n), U1 = s[1] / double(n), U2 = s[2] / double(n);
+        // totals, and the mean velocity (warp 0 divides, once per cell)
+        double s[5] = {0, 0, 0, 0, 0}, su[5];
+        if (need_m4) {
+            block_sums<5>(acc, s, sh.red, double(n), su);
+        } else {
+            double s4[4], su4[4];
+            block_sums<4>(acc, s4, sh.red, double(n), su4);
+            for (int j = 0; j < 4; ++j) { s[j] = s4[j]; su[j] = su4[j]; }
+            su[4] = 0.0;
+        }
+        const double U0 = su[0], U1 = su[1], U2 = su[2];
         const Real u0 = Real(U0), u1 = Real(U1), u2 = Real(U2);
         Real d2 = 0;
         long long d2b = 0;
@@ -472,13 +546,15 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 if (need_pxx) pxx.add(ax * ax);
             }
         }
-        if constexpr (sizeof(Real) == 8) d2 = __longlong_as_double(d2b);
+        if constexpr (sizeof(Real) == 4) d2b = (long long)__float_as_int(d2);
         double t[1] = {0.0};
-        if (need_pxx) {
-            t[0] = pxx.get();
-            block_sum<1>(t, sh.red);
+        double dmax = 0.0;
+        if (need_d2 || need_pxx) {
+            long long mk;
+            block_sum_max<Real>(pxx, d2b, t[0], mk, sh.red);
+            if constexpr (sizeof(Real) == 8) dmax = __longlong_as_double(mk);
+            else dmax = double(__int_as_float(int(mk)));
         }
-        const double dmax = need_d2 ? block_max(double(d2), sh.red) : 0.0;
         if (tid == 0) {
             sh.P[0] = s[0]; sh.P[1] = s[1]; sh.P[2] = s[2]; sh.E = s[3];
             sh.U[0] = U0; sh.U[1] = U1; sh.U[2] = U2;
@@ -491,7 +567,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             const double rho = double(n) * sh.rho_scale;
             const double mu = rho * Sigma;
             sh.q = exp(-(mu * sh.dt) / sh.eps);
-            sh.S_pre = (need_m4 ? s[4] : t[0]) / double(n);
+            sh.S_pre = need_m4 ? su[4] : t[0] / double(n);
         }
         __syncthreads();
     }
@@ -933,7 +1009,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             bool acc = true;
             if (alpha != Real(0)) {
                 const Real ga = (alpha == Real(1)) ? g : Math<Real>::pow_(g, alpha);
-                if (ga > Sigma) cnt[2] += 1.0;
+                if (ga > Sigma) cnt[2] += 1;
                 const Real xi = Math<Real>::uni(w.w[0]);
                 acc = xi * Sigma < ga;
             }
@@ -948,9 +1024,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const Real cx = Real(0.5) * (ax + bx), cy = Real(0.5) * (ay + by), cz = Real(0.5) * (az + bz);
                 oax = cx + h * sx; oay = cy + h * sy; oaz = cz + h * sz;
                 obx = cx - h * sx; oby = cy - h * sy; obz = cz - h * sz;
-                cnt[0] += 1.0;
+                cnt[0] += 1;
             } else {
-                cnt[1] += 1.0;
+                cnt[1] += 1;
             }
             if (t0 < Dn) { const int q = IBn + t0; IBx[q] = oax; IBy[q] = oay; IBz[q] = oaz; }
             else { const int q = On + t0 - Dn; OBx[q] = oax; OBy[q] = oay; OBz[q] = oaz; }
@@ -1053,7 +1129,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             bool acc = true;
             if (alpha != Real(0)) {
                 const Real ga = (alpha == Real(1)) ? g : Math<Real>::pow_(g, alpha);
-                if (ga > Sigma) cnt[2] += 1.0;
+                if (ga > Sigma) cnt[2] += 1;
                 acc = xs < ga;
             }
             Real oax = ax, oay = ay, oaz = az, obx = bx, oby = by, obz = bz;
@@ -1062,9 +1138,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const Real cx = Real(0.5) * (ax + bx), cy = Real(0.5) * (ay + by), cz = Real(0.5) * (az + bz);
                 oax = cx + h * sx; oay = cy + h * sy; oaz = cz + h * sz;
                 obx = cx - h * sx; oby = cy - h * sy; obz = cz - h * sz;
-                cnt[0] += 1.0;
+                cnt[0] += 1;
             } else {
-                cnt[1] += 1.0;
+                cnt[1] += 1;
             }
             if (ds.x >= 0) { IBx[ds.x] = oax; IBy[ds.x] = oay; IBz[ds.x] = oaz; }
             else { const int q = ~ds.x; OBx[q] = oax; OBy[q] = oay; OBz[q] = oaz; }
@@ -1167,7 +1243,11 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         //    adaptive indicator from the changed particles only, without
         //    cancelling two sums over the whole cell.
         {
-            Sum<Real> c0, c1, c2, c3, c4;
+            // cs[0..3]: change of momentum and energy over the leaves, cs[4..7]: the
+            // thermalised set's momentum and energy, cs[8], cs[9]: the indicator's
+            // change and the set's indicator (TRMC-RAD only)
+            Sum<Real> cs[10];
+            const bool rad = prm.trunc == TRMC_TRUNC_RAD;
             const Real Ux = Real(sh.U[0]);
             auto place = [&](int jx) {
                 const int sl = inv[n0 + jx];
@@ -1175,13 +1255,13 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const Real x = OBx[jx], y = OBy[jx], z = OBz[jx];
                 Vx[sl] = x; Vy[sl] = y; Vz[sl] = z;
                 if constexpr (sizeof(Real) == 8) {
-                    c0.add(x - ox); c1.add(y - oy); c2.add(z - oz);
-                    c3.add((x * x + y * y + z * z) - (ox * ox + oy * oy + oz * oz));
-                    c4.add(indicator(x, y, z, sh.U, prm.indicator) - indicator(ox, oy, oz, sh.U, prm.indicator));
+                    cs[0].add(x - ox); cs[1].add(y - oy); cs[2].add(z - oz);
+                    cs[3].add((x * x + y * y + z * z) - (ox * ox + oy * oy + oz * oz));
+                    if (rad) cs[8].add(indicator(x, y, z, sh.U, prm.indicator) - indicator(ox, oy, oz, sh.U, prm.indicator));
                 } else {
-                    c0.add(x); c0.add(-ox); c1.add(y); c1.add(-oy); c2.add(z); c2.add(-oz);
-                    c3.add_sq3(x, y, z); c3.sub_sq3(ox, oy, oz);
-                    c4.add(indicator_r(x, y, z, Ux, prm.indicator) - indicator_r(ox, oy, oz, Ux, prm.indicator));
+                    cs[0].add(x); cs[0].add(-ox); cs[1].add(y); cs[1].add(-oy); cs[2].add(z); cs[2].add(-oz);
+                    cs[3].add_sq3(x, y, z); cs[3].sub_sq3(ox, oy, oz);
+                    if (rad) cs[8].add(indicator_r(x, y, z, Ux, prm.indicator) - indicator_r(ox, oy, oz, Ux, prm.indicator));
                 }
             };
             int nrej = 0;
@@ -1208,23 +1288,33 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     else if (jx < D0) place(jx);
                     nrej += tot;
                 }
+                __syncthreads();            // the pool below reads the rejected slots written above
             } else {
                 for (int jx = tid; jx < D0; jx += bs) place(jx);
             }
-            double s[5] = {c0.get(), c1.get(), c2.get(), c3.get(), c4.get()};
-            block_sum<5>(s, sh.red);
-            Sum<Real> p0, p1, p2, p3, p4;
             const int pool0 = n0 + D0, R = sh.R, Rx = R + nrej;
             for (int t = tid; t < Rx; t += bs) {
                 const int sl = t < R ? inv[pool0 + t] : sh.ext[t - R];
                 const Real x = Vx[sl], y = Vy[sl], z = Vz[sl];
-                p0.add(x); p1.add(y); p2.add(z);
-                p3.add_sq3(x, y, z);
-                if constexpr (sizeof(Real) == 8) p4.add(indicator(x, y, z, sh.U, prm.indicator));
-                else p4.add(indicator_r(x, y, z, Ux, prm.indicator));
+                cs[4].add(x); cs[5].add(y); cs[6].add(z);
+                cs[7].add_sq3(x, y, z);
+                if (rad) {
+                    if constexpr (sizeof(Real) == 8) cs[9].add(indicator(x, y, z, sh.U, prm.indicator));
+                    else cs[9].add(indicator_r(x, y, z, Ux, prm.indicator));
+                }
             }
-            double p[5] = {p0.get(), p1.get(), p2.get(), p3.get(), p4.get()};
-            block_sum<5>(p, sh.red);
+            double s[5], p[5];
+            if (rad) {
+                double t[10];
+                block_sums<10>(cs, t, sh.red);
+                for (int j = 0; j < 4; ++j) { s[j] = t[j]; p[j] = t[4 + j]; }
+                s[4] = t[8]; p[4] = t[9];
+            } else {
+                double t[8];
+                block_sums<8>(cs, t, sh.red);
+                for (int j = 0; j < 4; ++j) { s[j] = t[j]; p[j] = t[4 + j]; }
+                s[4] = 0.0; p[4] = 0.0;
+            }
             if (tid == 0) {
                 sh.dP[0] += s[0]; sh.dP[1] += s[1]; sh.dP[2] += s[2]; sh.dE += s[3]; sh.dS += s[4];
                 sh.Pp[0] = p[0]; sh.Pp[1] = p[1]; sh.Pp[2] = p[2]; sh.Ep = p[3]; sh.Sp = p[4];
@@ -1293,40 +1383,48 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
     const int32_t *ext = sh.ext;
     auto pslot = [&](int t) { return t < R0 ? inv[pool0 + t] : ext[t - R0]; };
     if (R >= 2) {
-        Sum<Real> q0, q1, q2;
+        Sum<Real> qs[3];
         for (int t = tid; t < R; t += bs) {
             Real z0, z1, z2;
             Math<Real>::normals(rng.draw(uint64_t(t), 0, 0, TAG_MAXW), z0, z1, z2);
             const int sl = pslot(t);
             Vx[sl] = z0; Vy[sl] = z1; Vz[sl] = z2;
-            q0.add(z0); q1.add(z1); q2.add(z2);
+            qs[0].add(z0); qs[1].add(z1); qs[2].add(z2);
         }
-        double s[3] = {q0.get(), q1.get(), q2.get()};
-        block_sum<3>(s, sh.red);
-        const double zb0 = s[0] / double(R), zb1 = s[1] / double(R), zb2 = s[2] / double(R);
+        double s[3], zb[3];
+        block_sums<3>(qs, s, sh.red, double(R), zb);       // zb: the samples' mean
+        const double zb0 = zb[0], zb1 = zb[1], zb2 = zb[2];
         const Real rz0 = Real(zb0), rz1 = Real(zb1), rz2 = Real(zb2);
-        Sum<Real> qe;
+        Sum<Real> qe[1];
         for (int t = tid; t < R; t += bs) {
             const int sl = pslot(t);
             if constexpr (sizeof(Real) == 8) {
                 const double a0 = Vx[sl] - zb0, a1 = Vy[sl] - zb1, a2 = Vz[sl] - zb2;
-                qe.add(a0 * a0 + a1 * a1 + a2 * a2);
+                qe[0].add(a0 * a0 + a1 * a1 + a2 * a2);
             } else {
-                qe.add_sq3(Vx[sl] - rz0, Vy[sl] - rz1, Vz[sl] - rz2);
+                qe[0].add_sq3(Vx[sl] - rz0, Vy[sl] - rz1, Vz[sl] - rz2);
             }
         }
-        double e[1] = {qe.get()};
-        block_sum<1>(e, sh.red);
+        double e[1];
+        block_sums<1>(qe, e, sh.red);
         // target: what the set carried, minus the collisions' round-off change,
-        // plus what earlier steps' rounding to the storage precision left over
-        const double Pt0 = sh.Pp[0] - sh.dP[0] + sh.carry[0], Pt1 = sh.Pp[1] - sh.dP[1] + sh.carry[1],
-                     Pt2 = sh.Pp[2] - sh.dP[2] + sh.carry[2];
-        const double Et = sh.Ep - sh.dE + sh.carry[3];
-        if (tid == 0) { sh.Pt[0] = Pt0; sh.Pt[1] = Pt1; sh.Pt[2] = Pt2; sh.Et = Et; }
-        double et = Et - (Pt0 * Pt0 + Pt1 * Pt1 + Pt2 * Pt2) / double(R);
-        if (et < 0.0) et = 0.0;
-        const double sc = (e[0] > 0.0) ? sqrt(et / e[0]) : 0.0;
-        const double u0 = Pt0 / double(R), u1 = Pt1 / double(R), u2 = Pt2 / double(R);
+        // plus what earlier steps' rounding to the storage precision left over;
+        // the energy scale and the mean are computed once, by four lanes
+        if (tid < 4) {
+            const double Pt0 = sh.Pp[0] - sh.dP[0] + sh.carry[0], Pt1 = sh.Pp[1] - sh.dP[1] + sh.carry[1],
+                         Pt2 = sh.Pp[2] - sh.dP[2] + sh.carry[2];
+            if (lane == 0) {
+                const double Et = sh.Ep - sh.dE + sh.carry[3];
+                sh.Pt[0] = Pt0; sh.Pt[1] = Pt1; sh.Pt[2] = Pt2; sh.Et = Et;
+                double et = Et - (Pt0 * Pt0 + Pt1 * Pt1 + Pt2 * Pt2) / double(R);
+                if (et < 0.0) et = 0.0;
+                sh.msc[0] = (e[0] > 0.0) ? sqrt(et / e[0]) : 0.0;
+            } else {
+                sh.msc[lane] = (lane == 1 ? Pt0 : lane == 2 ? Pt1 : Pt2) / double(R);
+            }
+        }
+        __syncthreads();
+        const double sc = sh.msc[0], u0 = sh.msc[1], u1 = sh.msc[2], u2 = sh.msc[3];
         if constexpr (sizeof(Real) == 8) {
             for (int t = tid; t < R; t += bs) {
                 const int sl = pslot(t);
@@ -1351,15 +1449,15 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         // new carry: what the stored thermalised set misses of its target
         // (R >= 2), or the collisions' round-off change (R <= 1)
         if (R >= 2) {
-            Sum<Real> r0, r1, r2, r3;
+            Sum<Real> rs[4];
             for (int t = tid; t < R; t += bs) {
                 const int sl = pslot(t);
                 const Real x = Vx[sl], y = Vy[sl], z = Vz[sl];
-                r0.add(x); r1.add(y); r2.add(z);
-                r3.add_sq3(x, y, z);
+                rs[0].add(x); rs[1].add(y); rs[2].add(z);
+                rs[3].add_sq3(x, y, z);
             }
-            double r[4] = {r0.get(), r1.get(), r2.get(), r3.get()};
-            block_sum<4>(r, sh.red);
+            double r[4];
+            block_sums<4>(rs, r, sh.red);
             if (tid == 0) {
                 sh.carry[0] = sh.Pt[0] - r[0]; sh.carry[1] = sh.Pt[1] - r[1]; sh.carry[2] = sh.Pt[2] - r[2];
                 sh.carry[3] = sh.Et - r[3];
@@ -1384,7 +1482,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 vm = fmaxf(vm, __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z)));
         }
         if constexpr (sizeof(Real) == 8) vm = __longlong_as_double(vmb);
-        const double vmax = block_max(double(vm), sh.red);
+        const double vmax = block_max_nonneg(double(vm), sh.red);
         if (tid == 0) a.cell_vmax2[cell] = vmax;
     } else {
         for (int i = tid; i < n; i += bs)
@@ -1418,7 +1516,7 @@ __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
         __syncthreads();
         if (ticket >= a.n_cells) break;
         const int cell = a.cell_order ? a.cell_order[ticket] : ticket;
-        double cnt[3] = {0, 0, 0};   // collisions, dummy, exceed
+        int cnt[3] = {0, 0, 0};      // collisions, dummy, exceed
         const long long t_start = clock64();
         process_cell<Real>(a, step, sh, dsm, slab, cell, cnt);
         if (a.cell_cost && threadIdx.x == 0) {
@@ -1427,7 +1525,7 @@ __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
         }
         __syncthreads();
         if (a.report || a.stats) {
-            block_sum<3>(cnt, sh.red);
+            block_sum_int<3>(cnt, sh.red);
             if (threadIdx.x == 0 && sh.n >= 2 && !sh.skip) {
                 if (a.report) {
                     int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;

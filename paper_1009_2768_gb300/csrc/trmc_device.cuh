@@ -127,34 +127,158 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
-// Reduction scratch: warp partials at [w*K + j] (w < 32, K <= 8), block_sum
-// totals at [256 + j], the block_max total at [264].
+// Reduction scratch: warp partials at [w*K + j] (w*K < 256: CTAs of up to 256
+// threads for K = 16), block_sum totals at [256 + j], their quotients by a
+// divisor at [264 + j] (K <= 8), the block_max total at [264].
 constexpr int kRedScratch = 272;
 
-// Sum K doubles over the block (K <= 8); every thread gets the totals.
-// scratch holds kRedScratch doubles.  Warp partials are combined by warp 0 alone (lane j
-// sums value j), so the FP64 work beyond the warp trees is K lanes x (warps)
-// adds instead of every thread re-summing every partial.  Two barriers.
+// Sum K doubles over the block (K <= 16); every thread gets the totals and,
+// with a divisor (K <= 8), the totals divided by it.
+// scratch holds kRedScratch doubles.  Inside a warp the K values are
+// reduce-scattered: at each of the first log2(P) shuffle steps (P = K rounded
+// up to a power of two) a lane keeps half of its values and adds its
+// partner's copies of them, so a warp spends P - 1 + log2(32/P) FP64 adds
+// instead of 5K (GB300 issues FP64 at 2 lanes/clk/SM; a warp instruction costs
+// 16 cycles whatever its active lanes).  Warp partials are then combined by
+// warp 0 alone, lane j summing value j.  Fixed order, hence deterministic.
 template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double *scratch)
+__device__ __forceinline__ void block_sum(double (&v)[K], double *scratch, double div = 0.0, double *quot = nullptr)
 {
-    static_assert(K >= 1 && K <= 8, "block_sum handles 1..8 values");
+    static_assert(K >= 1 && K <= 16, "block_sum handles 1..16 values");
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int P = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : 16, G = 32 / P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double t[P];
 #pragma unroll
-    for (int j = 0; j < K; ++j) v[j] = warp_sum(v[j]);
-    if (lane == 0) {
+    for (int i = 0; i < P; ++i) t[i] = i < K ? v[i] : 0.0;
+    int idx = 0;
 #pragma unroll
-        for (int j = 0; j < K; ++j) scratch[warp * K + j] = v[j];
+    for (int h = P / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double send = up ? t[i] : t[i + h], keep = up ? t[i + h] : t[i];
+            t[i] = keep + __shfl_xor_sync(FULL, send, o);
+        }
+        if (up) idx += h;
     }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) t[0] += __shfl_xor_sync(FULL, t[0], o);
+    if ((lane & (G - 1)) == 0 && idx < K) scratch[warp * K + idx] = t[0];
     __syncthreads();
     if (warp == 0 && lane < K) {
         double s = 0.0;
         for (int w = 0; w < nw; ++w) s += scratch[w * K + lane];
         scratch[256 + lane] = s;
+        if (quot && K <= 8) scratch[264 + lane] = s / div;
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < K; ++j) v[j] = scratch[256 + j];
+    if (quot && K <= 8) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) quot[j] = scratch[264 + j];
+    }
+}
+
+// a + b for unevaluated float pairs (hi, lo): TwoSum of the high parts, the
+// low parts and the rounding error added, renormalised (about 48 bits)
+__device__ __forceinline__ void ff_add(float &ah, float &al, float bh, float bl)
+{
+    const float s = ah + bh, bb = s - ah;
+    float e = (ah - (s - bb)) + (bh - bb);
+    e += al + bl;
+    const float h = s + e;
+    al = e - (h - s);
+    ah = h;
+}
+
+// The same block sum for K compensated float partial sums (hi, lo), added as
+// float pairs all the way, so no FP64 instruction is issued until warp 0
+// converts the K totals.
+template <int K>
+__device__ __forceinline__ void block_sum_ff(const float (&vh)[K], const float (&vl)[K], double (&out)[K],
+                                             double *scratch, double div = 0.0, double *quot = nullptr)
+{
+    static_assert(K >= 1 && K <= 16, "block_sum_ff handles 1..16 values");
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int P = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : 16, G = 32 / P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    float th[P], tl[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) { th[i] = i < K ? vh[i] : 0.0f; tl[i] = i < K ? vl[i] : 0.0f; }
+    int idx = 0;
+#pragma unroll
+    for (int h = P / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float sh_ = up ? th[i] : th[i + h], sl_ = up ? tl[i] : tl[i + h];
+            float kh = up ? th[i + h] : th[i], kl = up ? tl[i + h] : tl[i];
+            ff_add(kh, kl, __shfl_xor_sync(FULL, sh_, o), __shfl_xor_sync(FULL, sl_, o));
+            th[i] = kh; tl[i] = kl;
+        }
+        if (up) idx += h;
+    }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1)
+        ff_add(th[0], tl[0], __shfl_xor_sync(FULL, th[0], o), __shfl_xor_sync(FULL, tl[0], o));
+    float2 *sf = reinterpret_cast<float2 *>(scratch);
+    if ((lane & (G - 1)) == 0 && idx < K) sf[warp * K + idx] = make_float2(th[0], tl[0]);
+    __syncthreads();
+    if (warp == 0 && lane < K) {
+        float h = 0.0f, l = 0.0f;
+        for (int w = 0; w < nw; ++w) { const float2 p = sf[w * K + lane]; ff_add(h, l, p.x, p.y); }
+        const double s = double(h) + double(l);
+        scratch[256 + lane] = s;
+        if (quot && K <= 8) scratch[264 + lane] = s / div;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < K; ++j) out[j] = scratch[256 + j];
+    if (quot && K <= 8) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) quot[j] = scratch[264 + j];
+    }
+}
+
+// Sum K ints over the block; every thread gets the totals (K <= 8).
+template <int K>
+__device__ __forceinline__ void block_sum_int(int (&v)[K], double *scratch)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int *si = reinterpret_cast<int *>(scratch);
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = int(__reduce_add_sync(0xffffffffu, unsigned(v[j])));
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) si[warp * K + j] = v[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        int s = 0;
+        for (int w = 0; w < nw; ++w) s += si[w * K + j];
+        v[j] = s;
+    }
+    __syncthreads();
+}
+
+// Maximum of a non-negative double over the block, on the bit patterns (they
+// order like the values), so it costs no FP64 instruction.
+__device__ __forceinline__ double block_max_nonneg(double v, double *scratch)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    long long b = __double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    long long *sl = reinterpret_cast<long long *>(scratch);
+    if (lane == 0) sl[warp] = b;
+    __syncthreads();
+    long long m = sl[0];
+    for (int w = 1; w < nw; ++w) m = max(m, sl[w]);
+    __syncthreads();
+    return __longlong_as_double(m);
 }
 
 __device__ __forceinline__ double block_max(double v, double *scratch)
