@@ -259,6 +259,17 @@ def ours(args):
     for _ in range(args.warmup):
         sim.step()
     T.trmc_check(sim.ctx)
+    launch = None
+    if not args.no_tune:
+        # the collide launch shape (threads per CTA, CTAs per SM) for this
+        # workload's cell sizes, measured on the live state before timing
+        from paper_1009_2768_gb300 import runtime as RT
+        times, best = RT.autotune_collide(sim, steps=3)
+        launch = {"threads": best[0], "ctas_per_sm": best[1], "tuned_ms": {f"{k[0]}x{k[1]}": round(v, 4)
+                                                                          for k, v in times.items()}}
+        for _ in range(2):
+            sim.step()
+        T.trmc_check(sim.ctx)
     K = args.steps
     clocks = Clocks(local)
     if dist:
@@ -352,7 +363,8 @@ def ours(args):
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "particles_per_gpu": n,
                        "cells_per_gpu": sim.state.n_cells,
-                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
+                       "collide_launch": launch},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": sim.launches_per_step * K, "clocks": clk, "forms": forms,
             "step_stats": {k: st[k] / K for k in ("collisions", "dummy", "maxwell", "changed", "passes")},
@@ -437,6 +449,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default collide launch shape")
     ap.add_argument("--workload", default="shock", choices=["shock", "batched", "bkw", "stationary", "serving"])
     ap.add_argument("--rates", default="1,10,50,200", help="serving: arrival rates (requests/s) to sweep")
     ap.add_argument("--requests", type=int, default=0, help="serving: requests per rate (default 8*rate in [8, 48])")

@@ -18,7 +18,7 @@ import numpy as np
 
 from . import trmc as T
 
-DEFAULT_SHAPES = ((128, 4), (128, 6), (128, 3), (96, 4), (64, 8), (256, 2))
+DEFAULT_SHAPES = ((128, 4), (96, 4), (96, 5), (128, 3), (160, 3), (192, 2), (256, 2), (64, 8))
 
 
 def largest_first(cell_start):
