@@ -149,6 +149,21 @@ __device__ __forceinline__ int block_flag_scan(bool flag, int &excl, int32_t *sc
     return total;
 }
 
+// a < RN(sqrt(g2)) for a >= 0, g2 >= 0, given a2 = fl(a a), decided on the
+// squares and exactly as the comparison with the correctly rounded square
+// root: more than 4 units apart in the last place (the bit patterns of
+// non-negative doubles order like their values), a^2 and g2 are on the sides
+// they show, and a is more than an ulp away from sqrt(g2); only nearer than
+// that is the square root taken.  Hard-sphere acceptance (Alg. 4.4) then costs
+// one FP64 multiply instead of a square root for every rejected collision.
+__device__ __forceinline__ bool lt_sqrt(double a, double a2, double g2)
+{
+    const long long d = __double_as_longlong(a2) - __double_as_longlong(g2);
+    if (d < -4) return true;
+    if (d > 4) return false;
+    return a < sqrt(g2);
+}
+
 // ---- Iround of the split in integer arithmetic -------------------------------
 // Alg. 4.2 gives level n the count Iround(q R), R the particles not yet
 // placed, and the FP64 reference evaluates it as x = fl(q R) (round to
@@ -805,10 +820,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             }
             __syncwarp();
         };
-        // 2. Split (Alg. 4.2): one uniform per level, drawn by the whole CTA.
-        //    Every warp then runs the short sequential recurrence itself, in
-        //    integer arithmetic that reproduces the FP64 Iround bit for bit
-        //    (iround_q), so that each knows the depth the split reached.
+        // 2. Split (Alg. 4.2): one uniform per level, drawn by the whole CTA,
+        //    then the recurrence in integer arithmetic that reproduces the FP64
+        //    Iround bit for bit (iround_q).
         {
             const int lo = sh.lo, m = sh.m;
             for (int t = tid; t <= m - lo; t += bs)
@@ -819,27 +833,41 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         __syncthreads();
         int m_split;
         {
-            const uint64_t qb = uint64_t(__double_as_longlong(sh.q));
-            const int lo = sh.lo, m = sh.m;
-            int rem = npart;
-            m_split = m;
-            for (int lv = lo; lv <= m; ++lv) {
-                const int c = iround_q(qb, uint32_t(rem), sh.uSK[lv]);
-                if (tid == 0) sh.Nq[lv] = c;
-                rem -= c;
-                if (rem == 0) { m_split = lv; break; }
+            // Warp 0 runs the recurrence speculatively: lane j evaluates level
+            // lv + j with the current remainder; the levels before the first
+            // non-zero count get none, and only there does the remainder change.
+            // A split whose counts are mostly zero (small q) takes a few rounds.
+            if (warp == 0) {
+                constexpr unsigned FULL = 0xffffffffu;
+                const uint64_t qb = uint64_t(__double_as_longlong(sh.q));
+                const int m = sh.m;
+                int rem = npart, lv = sh.lo, ms = m;
+                while (lv <= m) {
+                    const int l = lv + lane;
+                    const int c = l <= m ? iround_q(qb, uint32_t(rem), sh.uSK[l]) : 0;
+                    const unsigned nz = __ballot_sync(FULL, c != 0);
+                    if (nz == 0) { lv += 32; continue; }
+                    const int f = __ffs(nz) - 1;
+                    const int cf = __shfl_sync(FULL, c, f);
+                    if (lane == 0) sh.Nq[lv + f] = cf;
+                    rem -= cf;
+                    if (rem == 0) { ms = lv + f; break; }
+                    lv += f + 1;
+                }
+                if (lane == 0) {
+                    if (rem > 0) sh.Nq[m + 1] = rem;
+                    sh.m_eff = ms;
+                    sh.m_top = ms;
+                    sh.pass_smem = sh.smem_rest; sh.pass_smem_cap = sh.smem_rest_cap;
+                    sh.pass_slab = sh.slab_rest; sh.pass_slab_cap = sh.slab_rest_cap;
+                    const size_t T = size_t(tri(ms + 1));
+                    sh.Mt = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
+                    sh.St = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
+                    if (!sh.Mt || !sh.St) sh.skip = 1;
+                }
             }
-            if (tid == 0) {
-                if (rem > 0) sh.Nq[m + 1] = rem;
-                sh.m_eff = m_split;
-                sh.m_top = m_split;
-                sh.pass_smem = sh.smem_rest; sh.pass_smem_cap = sh.smem_rest_cap;
-                sh.pass_slab = sh.slab_rest; sh.pass_slab_cap = sh.slab_rest_cap;
-                const size_t T = size_t(tri(m_split + 1));
-                sh.Mt = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
-                sh.St = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
-                if (!sh.Mt || !sh.St) sh.skip = 1;
-            }
+            __syncthreads();
+            m_split = sh.m_eff;
         }
         // 3. The other draws of levels 1..m_eff, six per level: the parity coin
         //    (odd counts, Alg. 4.3), the key of the level's product permutation
@@ -969,6 +997,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         Real *IBx = sh.IBuf, *IBy = sh.IBuf + (Dge1 + 1), *IBz = sh.IBuf + 2 * (Dge1 + 1);
         Real *OBx = sh.OBuf, *OBy = sh.OBuf + (D0 + 1), *OBz = sh.OBuf + 2 * (D0 + 1);
         const Real alpha = Real(sh.alpha), Sigma = Real(sh.Sigma);
+        const double Sigma2 = double(Sigma) * double(Sigma);
         const int wb = prm.trunc == TRMC_TRUNC_WB ? prm.wb_length : 0;
         double *IL = sh.ILBuf, *OL = sh.OLBuf;
         auto level_setup = [&](int lv) {          // warp 0: label prefix and product key
@@ -1005,13 +1034,23 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             if (j == 0) { const int sl = inv[n0 + s1]; bx = Vx[sl]; by = Vy[sl]; bz = Vz[sl]; }
             else { const int q = sh.IB[j] + s1; bx = IBx[q]; by = IBy[q]; bz = IBz[q]; }
             const Real dx = ax - bx, dy = ay - by, dz = az - bz;
-            const Real g = Math<Real>::sqrt_(dx * dx + dy * dy + dz * dz);
+            const Real g2 = dx * dx + dy * dy + dz * dz;
+            Real g = Real(0);
             bool acc = true;
-            if (alpha != Real(0)) {
-                const Real ga = (alpha == Real(1)) ? g : Math<Real>::pow_(g, alpha);
-                if (ga > Sigma) cnt[2] += 1;
-                const Real xi = Math<Real>::uni(w.w[0]);
-                acc = xi * Sigma < ga;
+            if (sizeof(Real) == 8 && alpha == Real(1)) {
+                // hard spheres in FP64: the bound and the acceptance on the squares
+                if (lt_sqrt(double(Sigma), Sigma2, double(g2))) cnt[2] += 1;
+                const double xs = double(Math<Real>::uni(w.w[0]) * Sigma);
+                acc = lt_sqrt(xs, xs * xs, double(g2));
+                if (acc) g = Math<Real>::sqrt_(g2);
+            } else {
+                g = Math<Real>::sqrt_(g2);
+                if (alpha != Real(0)) {
+                    const Real ga = (alpha == Real(1)) ? g : Math<Real>::pow_(g, alpha);
+                    if (ga > Sigma) cnt[2] += 1;
+                    const Real xi = Math<Real>::uni(w.w[0]);
+                    acc = xi * Sigma < ga;
+                }
             }
             Real oax = ax, oay = ay, oaz = az, obx = bx, oby = by, obz = bz;
             if (acc) {
@@ -1125,12 +1164,20 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             if (sr.y >= 0) { bx = IBx[sr.y]; by = IBy[sr.y]; bz = IBz[sr.y]; }
             else { const int sl = ~sr.y; bx = Vx[sl]; by = Vy[sl]; bz = Vz[sl]; }
             const Real dx = ax - bx, dy = ay - by, dz = az - bz;
-            const Real g = Math<Real>::sqrt_(dx * dx + dy * dy + dz * dz);
+            const Real g2 = dx * dx + dy * dy + dz * dz;
+            Real g = Real(0);
             bool acc = true;
-            if (alpha != Real(0)) {
-                const Real ga = (alpha == Real(1)) ? g : Math<Real>::pow_(g, alpha);
-                if (ga > Sigma) cnt[2] += 1;
-                acc = xs < ga;
+            if (sizeof(Real) == 8 && alpha == Real(1)) {
+                if (lt_sqrt(double(Sigma), Sigma2, double(g2))) cnt[2] += 1;
+                acc = lt_sqrt(double(xs), double(xs) * double(xs), double(g2));
+                if (acc) g = Math<Real>::sqrt_(g2);
+            } else {
+                g = Math<Real>::sqrt_(g2);
+                if (alpha != Real(0)) {
+                    const Real ga = (alpha == Real(1)) ? g : Math<Real>::pow_(g, alpha);
+                    if (ga > Sigma) cnt[2] += 1;
+                    acc = xs < ga;
+                }
             }
             Real oax = ax, oay = ay, oaz = az, obx = bx, oby = by, obz = bz;
             if (acc) {
