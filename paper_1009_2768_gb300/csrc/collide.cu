@@ -85,7 +85,7 @@ struct Sh {
     double q, Sigma, U[3], P[3], E, S_pre, dP[3], dE, dS, Pp[3], Ep, Sp, carry[4], Pt[3], Et, msc[4];
     double alpha, dt, eps, rho_scale;
     uint64_t problem, lcell;
-    U64x4 keyK;
+    U64x4 keyP0;                     // key of the pass's role permutation
     Real *V;
     uint32_t *flags;
     int32_t *inv[2];
@@ -592,7 +592,6 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         const int pass = sh.pass, warp = tid >> 5, npart = sh.npart;
         int32_t *inv = sh.inv[pass & 1];
         const int32_t *invp = sh.inv[(pass + 1) & 1];
-        int32_t *fwd = sh.inv[1];                       // pass 0: pi(i) of every slot, for the change flags
         const int poolp = sh.n0_prev + sh.D0_prev;
 
         // One attempt of the tree plan (warp 0) on depth sh.m_top, then, if the
@@ -649,6 +648,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     }
                     if (jA < lv) row[jA] = rA;
                     if (jB < lv) row[jB] = rB;
+                } else if (lv == 1) {
+                    // every level-1 collision has k = 0: no label draws needed
+                    if (lane == 0) { rA = Cn; sA = Cn; row[0] = Cn; }
                 } else {
                     if (jA < lv) row[jA] = 0;
                     if (jB < lv) row[jB] = 0;
@@ -829,6 +831,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 sh.uSK[lo + t] = rng.draw(uint64_t(lo + t), 0, uint32_t(pass), TAG_SPLIT).w[0] >> 11;
             for (int j = tid; j < NLEV; j += bs) sh.Nq[j] = 0;
             if (tid < 3) sh.coin[tid] = 0u;
+            if (tid == bs - 1) sh.keyP0 = rng.draw(0, 0, uint32_t(pass), TAG_PERM0);
         }
         __syncthreads();
         int m_split;
@@ -874,6 +877,11 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         //    and its first kPreLabels labels k (Alg. 4.1), four per draw.
         for (int t = tid; t < 6 * m_split; t += bs) {
             const int lv = 1 + t / 6, kind = t - 6 * (lv - 1);
+            if (lv == 1 && kind >= 2) {                 // k = 0 for every level-1 collision
+#pragma unroll
+                for (int j = 0; j < 4; ++j) sh.lab[1][4 * (kind - 2) + j] = 0;
+                continue;
+            }
             const uint64_t idx = kind == 0 ? uint64_t(lv) : kind == 1 ? 0ull : uint64_t(kind - 2);
             const uint64_t aux = kind == 0 ? 0ull : uint64_t(lv);
             const uint32_t tag = kind == 0 ? TAG_PARITY : kind == 1 ? TAG_PERMK : TAG_KSEL;
@@ -889,16 +897,21 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         }
         __syncthreads();
         if (warp == 0) plan_attempt();
-        // 4. roles: a permutation of the participants (warps 1.., or warp 0
-        //    afterwards when the CTA is a single warp)
+        // 4. roles (the "random choice" of Alg. 4.3): a permutation pi of the
+        //    participants gives slot pi^-1(r) the rank r.  Only ranks from n0 on
+        //    (leaves, then the thermalised set) are ever looked up, so only they
+        //    are computed, with the inverse permutation: the ranks from the
+        //    level-0 quota on by warps 1.. while warp 0 plans (warp 0 afterwards
+        //    in a single-warp CTA), those the leaf rule borrows from level 0
+        //    once the plan is known.
+        Perm perm;
+        perm.init(uint32_t(npart), sh.keyP0);
+        const int nq0 = sh.Nq[0];
         if (warp > 0 || bs == 32) {
-            Perm perm;
-            perm.init(uint32_t(npart), rng.draw(0, 0, uint32_t(pass), TAG_PERM0));
             const int t0 = bs == 32 ? tid : tid - 32, st = bs == 32 ? bs : bs - 32;
-            for (int i = t0; i < npart; i += st) {
-                const int r = int(perm.fwd(uint32_t(i)));
+            for (int r = nq0 + t0; r < npart; r += st) {
+                const int i = int(perm.inv(uint32_t(r)));
                 inv[r] = (pass == 0) ? i : invp[poolp + i];
-                if (pass == 0) fwd[i] = r;
             }
         }
         __syncthreads();
@@ -925,6 +938,8 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                             atomicAdd(&Dw[k], 1);
                             atomicAdd(&Dw[lv - 1 - k], 1);
                         }
+                    } else if (lv == 1) {
+                        if (lane == 0) Dw[0] += 2 * Cn;
                     } else {
                         for (int k = lane; k < lv; k += 32) rw[k] = 0;
                         __syncwarp();
@@ -981,12 +996,20 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         }
         if (sh.skip) break;
         const int m_eff = sh.m_eff, n0 = sh.n0, D0 = sh.D0, Dge1 = sh.Dge1;
+        if (n0 < nq0) {
+            for (int r = n0 + tid; r < nq0; r += bs) {
+                const int i = int(perm.inv(uint32_t(r)));
+                inv[r] = (pass == 0) ? i : invp[poolp + i];
+            }
+            __syncthreads();
+        }
         if (pass == 0) {
             // which slots change: every rank from n0 on (leaves and thermalised)
-            for (int b0 = tid - lane; b0 < npart; b0 += bs) {
-                const int i = b0 + lane;
-                const unsigned msk = __ballot_sync(0xffffffffu, i < npart && fwd[i] >= n0);
-                if (lane == 0) sh.flags[b0 >> 5] = msk;
+            for (int w = tid; w < (npart + 31) >> 5; w += bs) sh.flags[w] = 0u;
+            __syncthreads();
+            for (int r = n0 + tid; r < npart; r += bs) {
+                const int i = inv[r];
+                atomicOr(&sh.flags[i >> 5], 1u << (i & 31));
             }
         }
 

@@ -97,6 +97,19 @@ struct Perm {
         }
         return (L << h) | R;
     }
+    // the rounds of enc undone, last first
+    __device__ __forceinline__ uint32_t dec(uint32_t y) const
+    {
+        const uint32_t mask = (1u << h) - 1u;
+        uint32_t L = y >> h, R = y & mask;
+#pragma unroll
+        for (int r = 3; r >= 0; --r) {
+            const uint32_t t = R ^ (feistel_round(L, k[r]) & mask);
+            R = L;
+            L = t;
+        }
+        return (L << h) | R;
+    }
     // pi(x) for x < n
     __device__ __forceinline__ uint32_t fwd(uint32_t x) const
     {
@@ -104,6 +117,14 @@ struct Perm {
         uint32_t y = enc(x);
         while (y >= n) y = enc(y);
         return y;
+    }
+    // pi^-1(y) for y < n: the cycle through y walked backwards
+    __device__ __forceinline__ uint32_t inv(uint32_t y) const
+    {
+        if (n <= 1) return 0;
+        uint32_t x = dec(y);
+        while (x >= n) x = dec(x);
+        return x;
     }
 };
 
