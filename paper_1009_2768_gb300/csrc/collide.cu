@@ -756,18 +756,21 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 sh.Dge1 = Dge1;
                 if (w64) { sh.WL[nWL - 1] = 64; sh.WB[nWL - 1] = W63; }
                 sh.WB[nWL] = W;
-                sh.IBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                // the arenas' bump pointers in registers while the buffers are laid out
+                char *ps = sh.pass_smem, *pg = sh.pass_slab;
+                size_t pcs = sh.pass_smem_cap, pcg = sh.pass_slab_cap;
+                sh.IBuf = static_cast<Real *>(take(ps, pcs, pg, pcg,
                                                    3 * size_t(Dge1 + 1) * sizeof(Real)));
-                sh.OBuf = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                sh.OBuf = static_cast<Real *>(take(ps, pcs, pg, pcg,
                                                    3 * size_t(d0 + 1) * sizeof(Real)));
                 if (!sh.IBuf || !sh.OBuf) sh.skip = 1;
                 sh.ILBuf = sh.OLBuf = nullptr; sh.ext = nullptr;
                 if (prm.trunc == TRMC_TRUNC_WB) {
-                    sh.ILBuf = static_cast<double *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                    sh.ILBuf = static_cast<double *>(take(ps, pcs, pg, pcg,
                                                           8 * size_t(Dge1 + 1)));
-                    sh.OLBuf = static_cast<double *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                    sh.OLBuf = static_cast<double *>(take(ps, pcs, pg, pcg,
                                                           8 * size_t(d0 + 1)));
-                    sh.ext = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                    sh.ext = static_cast<int32_t *>(take(ps, pcs, pg, pcg,
                                                          4 * size_t(d0 + 1)));
                     if (!sh.ILBuf || !sh.OLBuf || !sh.ext) sh.skip = 1;
                 }
@@ -775,16 +778,16 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 // the waves compute everything in place (same results)
                 int nwl = nWL;
                 if (W > 0) {
-                    char *s0 = sh.pass_smem, *g0 = sh.pass_slab;
-                    const size_t sc0 = sh.pass_smem_cap, gc0 = sh.pass_slab_cap;
-                    sh.LP = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                    char *s0 = ps, *g0 = pg;
+                    const size_t sc0 = pcs, gc0 = pcg;
+                    sh.LP = static_cast<int32_t *>(take(ps, pcs, pg, pcg,
                                                         4 * size_t(tri(m + 1) + 1)));
-                    sh.psrc = static_cast<int2 *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 8 * size_t(W)));
-                    sh.pdst = static_cast<int2 *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 8 * size_t(W)));
-                    sh.prnd = static_cast<Real *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap,
+                    sh.psrc = static_cast<int2 *>(take(ps, pcs, pg, pcg, 8 * size_t(W)));
+                    sh.pdst = static_cast<int2 *>(take(ps, pcs, pg, pcg, 8 * size_t(W)));
+                    sh.prnd = static_cast<Real *>(take(ps, pcs, pg, pcg,
                                                        4 * size_t(W) * sizeof(Real)));
                     if (!sh.LP || !sh.psrc || !sh.pdst || !sh.prnd) {
-                        sh.pass_smem = s0; sh.pass_slab = g0; sh.pass_smem_cap = sc0; sh.pass_slab_cap = gc0;
+                        ps = s0; pg = g0; pcs = sc0; pcg = gc0;
                         nwl = 0;
                     }
                 }
@@ -794,18 +797,19 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 sh.ntail = 0;
                 const int nt = W - WBjt, nslots = Dge1 - IBlb;
                 if (nwl > 0 && nwl - jt >= 2 && nt > 0) {
-                    char *s0 = sh.pass_smem, *g0 = sh.pass_slab;
-                    const size_t sc0 = sh.pass_smem_cap, gc0 = sh.pass_slab_cap;
-                    sh.prodOf = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab,
-                                                            sh.pass_slab_cap, 4 * size_t(nslots + 1)));
-                    sh.done = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab,
-                                                          sh.pass_slab_cap, 4 * size_t(nt)));
+                    char *s0 = ps, *g0 = pg;
+                    const size_t sc0 = pcs, gc0 = pcg;
+                    sh.prodOf = static_cast<int32_t *>(take(ps, pcs, pg,
+                                                            pcg, 4 * size_t(nslots + 1)));
+                    sh.done = static_cast<int32_t *>(take(ps, pcs, pg,
+                                                          pcg, 4 * size_t(nt)));
                     if (sh.prodOf && sh.done) {
                         sh.ntail = nt; sh.tail0 = WBjt; sh.tailbase = IBlb;
                     } else {
-                        sh.pass_smem = s0; sh.pass_slab = g0; sh.pass_smem_cap = sc0; sh.pass_slab_cap = gc0;
+                        ps = s0; pg = g0; pcs = sc0; pcg = gc0;
                     }
                 }
+                sh.pass_smem = ps; sh.pass_slab = pg; sh.pass_smem_cap = pcs; sh.pass_slab_cap = pcg;
                 if (!ok) sh.skip = 2;
                 if (pass == 0) sh.n0_first = n0;
             }
@@ -1657,11 +1661,28 @@ __global__ void __launch_bounds__(1024) order_kernel(const uint32_t *cost, int n
     for (int c = tid; c < n; c += blockDim.x) order[atomicAdd(&cnt[cost_bucket(cost[c])], 1)] = c;
 }
 
+// The kernel's dynamic shared-memory limit, set once per device to the most a
+// CTA can have, so that every launch shape (and the allocation-free entry
+// point) fits under it whatever order they come in.
+template <typename Real>
+cudaError_t allow_max_smem(int device, int smem_optin)
+{
+    constexpr int kDev = 64;
+    static bool done[kDev] = {};
+    if (device >= 0 && device < kDev && done[device]) return cudaSuccess;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, collide_kernel<Real>);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(collide_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_optin - int(fa.sharedSizeBytes));
+    if (e == cudaSuccess && device >= 0 && device < kDev) done[device] = true;
+    return e;
+}
+
 template <typename Real>
 trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *prm, uint64_t step,
                      int64_t *report, trmc_stats *stats, cudaStream_t s)
 {
-    static int configured_smem = -1;
     // CTA size and CTAs per SM from the context (default 128 x 4): several
     // cells per SM overlap one cell's serial phases with the others' work;
     // the shared-memory budget of an SM is split evenly between them
@@ -1669,12 +1690,8 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     const int budget = ctx->smem_optin >= 200 * 1024 ? 220 * 1024 : int(ctx->smem_optin);
     int smem = budget / per_sm_target - int(sizeof(Sh<Real>)) - 1024;
     if (smem > int(ctx->smem_optin) - int(sizeof(Sh<Real>))) smem = int(ctx->smem_optin) - int(sizeof(Sh<Real>));
-    cudaError_t e;
-    if (configured_smem != smem) {
-        e = cudaFuncSetAttribute(collide_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return cuda_error(ctx, e, "cudaFuncSetAttribute(collide)");
-        configured_smem = smem;
-    }
+    cudaError_t e = allow_max_smem<Real>(ctx->device, int(ctx->smem_optin));
+    if (e != cudaSuccess) return cuda_error(ctx, e, "cudaFuncSetAttribute(collide)");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_kernel<Real>, threads, smem);
     if (e != cudaSuccess) return cuda_error(ctx, e, "occupancy(collide)");
@@ -1783,8 +1800,7 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
     }
     const int smem = D.smem_optin >= 200 * 1024 ? (220 * 1024) / per_sm_target - int(sizeof(Sh<Real>)) - 1024
                                                 : D.smem_optin / 2 - int(sizeof(Sh<Real>)) - 1024;
-    if (cudaFuncSetAttribute(collide_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return TRMC_ERR_CUDA;
+    if (allow_max_smem<Real>(dev, D.smem_optin) != cudaSuccess) return TRMC_ERR_CUDA;
     const size_t avail = size_t(TRMC_STATIC_SCRATCH_BYTES) - kStaticControl;
     const size_t need = static_cell_bytes(max_cell, sizeof(Real), prm->trunc == TRMC_TRUNC_WB);
     int grid = int(std::min<size_t>(avail / need, size_t(D.num_sms) * per_sm_target));

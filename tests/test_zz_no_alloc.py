@@ -54,3 +54,28 @@ def test_static_rejects_cells_larger_than_its_scratch():
     with pytest.raises(T.TrmcError) as e:
         T.trmc_collide_static(st, p, T.FP64, 0, 0, 1 << 30)
     assert e.value.code == T.ERR_CAPACITY
+
+
+def test_static_between_calls_of_a_wide_launch_shape():
+    """A context whose collide launch uses two CTAs per SM (about twice the
+    shared memory per CTA of the default) keeps working after an
+    allocation-free call in between, and its results do not depend on it."""
+    need_gpu()
+    cs, (ref, st) = _states(T.FP64, COUNTS, seed=33)
+    p = T.collide_params(dt=0.05, eps=0.05, alpha=1.0, rho_scale=1.0 / 500, trunc=T.TRUNC_RAD, m=2)
+    c_ref, c = ctx(T.FP64, seed=0), T.trmc_create(T.FP64, 0, 256 << 20)
+    T.trmc_set_collide_launch(c, 256, 2)
+    tmp = T.ParticleState(cs, precision=T.FP64, rad=True)
+    tmp.set_velocities(st.v[:, :int(cs[-1])].cpu().numpy())
+    tmp.m_max.fill_(2)
+    for step in (1, 2):
+        T.trmc_collide(c_ref, ref, p, step)
+        T.trmc_collide(c, st, p, step)
+        T.trmc_collide_static(tmp, p, T.FP64, 0, step, max(COUNTS))
+        T.trmc_check(c)
+        T.trmc_check(c_ref)
+    T.trmc_destroy(c)
+    n = int(cs[-1])
+    # the wider CTAs sum the moments in another order: equal to rounding
+    assert_velocity_parity(st.v[:, :n].cpu().numpy(), ref.v[:, :n].cpu().numpy(), cs)
+    assert torch.equal(tmp.v[:, :n], ref.v[:, :n])
