@@ -42,7 +42,8 @@ namespace {
 
 constexpr int NLEV = kMC + 2;
 constexpr int kWarpLevel = 64;     // levels with at most this many collisions run in one warp
-constexpr int kPreLabels = 16;     // labels per level drawn ahead of the plan
+constexpr int kPreLabels = 16;     // labels per level drawn ahead of the plan, at least
+constexpr int kMaxPre = 64;        // and at most
 
 struct Args {
     void *vx, *vy, *vz;
@@ -75,7 +76,9 @@ struct Sh {
     uint64_t uSK[NLEV];              // split uniforms of the levels, u = uSK 2^-53
     U64x4 keys[NLEV];
     double red[kRedScratch];
-    uint8_t lab[NLEV][kPreLabels];   // labels of the first kPreLabels collisions of each level
+    uint8_t lab[NLEV][kMaxPre];      // labels of the first npre[lv] collisions of each level
+    uint8_t npre[NLEV];
+    int32_t dbase[NLEV + 1], ndraws; // first draw of each level in the level-draw phase, their number
     int32_t cell, n, m, lo, m_eff, pass, n0, D0, R, npart, m_next, Dge1;
     int32_t n0_prev, D0_prev;
     int32_t scan[33], nrej;
@@ -638,7 +641,10 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 // r: collisions labelled k = j; s: collisions whose second input
                 // is of level j (k = lv - 1 - j)
                 int rA = 0, rB = 0, sA = 0, sB = 0;
-                if (Cn <= kPreLabels) {
+                if (lv == 1) {
+                    // every level-1 collision has k = 0: no labels needed
+                    if (lane == 0) { rA = Cn; sA = Cn; row[0] = Cn; }
+                } else if (Cn <= kPreLabels) {
                     const uint64_t L0 = *reinterpret_cast<const uint64_t *>(&sh.lab[lv][0]);
                     const uint64_t L1 = *reinterpret_cast<const uint64_t *>(&sh.lab[lv][8]);
                     for (int c = 0; c < Cn; ++c) {
@@ -648,15 +654,19 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     }
                     if (jA < lv) row[jA] = rA;
                     if (jB < lv) row[jB] = rB;
-                } else if (lv == 1) {
-                    // every level-1 collision has k = 0: no label draws needed
-                    if (lane == 0) { rA = Cn; sA = Cn; row[0] = Cn; }
                 } else {
+                    // label histogram: the predrawn labels (lanes with equal labels
+                    // add once), then draws for the collisions beyond them
                     if (jA < lv) row[jA] = 0;
                     if (jB < lv) row[jB] = 0;
                     __syncwarp();
-                    if (lane < kPreLabels) atomicAdd(&row[sh.lab[lv][lane]], 1);
-                    for (int g = kPreLabels / 4 + lane; g < (Cn + 3) >> 2; g += 32) {
+                    const int np = sh.npre[lv], cpre = Cn < np ? Cn : np;
+                    const int k0 = lane < cpre ? int(sh.lab[lv][lane]) : -1;
+                    const int k1 = lane + 32 < cpre ? int(sh.lab[lv][lane + 32]) : -1;
+                    const unsigned g0 = __match_any_sync(FULL, k0), g1 = __match_any_sync(FULL, k1);
+                    if (k0 >= 0 && __ffs(g0) - 1 == lane) atomicAdd(&row[k0], __popc(g0));
+                    if (k1 >= 0 && __ffs(g1) - 1 == lane) atomicAdd(&row[k1], __popc(g1));
+                    for (int g = (np >> 2) + lane; g < (Cn + 3) >> 2; g += 32) {
                         const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
@@ -848,10 +858,38 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 constexpr unsigned FULL = 0xffffffffu;
                 const uint64_t qb = uint64_t(__double_as_longlong(sh.q));
                 const int m = sh.m;
+                // q as a 0.64 fixed-point number Q (exact for q >= 2^-12, else
+                // truncated, which R Q can be off by less than 2^31 units)
+                const uint32_t qE = uint32_t(qb >> 52) & 0x7FFu;
+                const uint64_t qM = (qb & ((1ull << 52) - 1ull)) | (1ull << 52);
+                uint64_t Q = 0, Qslack = 0;
+                const bool qfix = qE >= 1011 - 63 && qE < 1023;
+                if (qfix) {
+                    if (qE >= 1011) Q = qM << (qE - 1011);
+                    else { Q = qM >> (1011 - qE); Qslack = 1ull << 32; }
+                }
                 int rem = npart, lv = sh.lo, ms = m;
                 while (lv <= m) {
                     const int l = lv + lane;
-                    const int c = l <= m ? iround_q(qb, uint32_t(rem), sh.uSK[l]) : 0;
+                    int c = 0;
+                    if (l <= m) {
+                        const uint64_t K = sh.uSK[l];
+                        bool known = false;
+                        if (qfix) {
+                            // x = R Q 2^-64 exactly: integer part hi, fraction lo 2^-64.
+                            // Farther than an ulp of x from an integer and from u, the
+                            // FP64 product decides the same way as the exact one.
+                            const uint32_t r32 = uint32_t(rem);
+                            const uint64_t a0 = uint64_t(uint32_t(Q)) * r32, b0 = uint64_t(uint32_t(Q >> 32)) * r32;
+                            const uint64_t mid = (a0 >> 32) + (b0 & 0xFFFFFFFFull);
+                            const uint64_t lo = (mid << 32) | (a0 & 0xFFFFFFFFull), hi = (b0 >> 32) + (mid >> 32);
+                            const int bl = hi ? 64 - __clzll((long long)hi) : 0;
+                            const uint64_t marg = (1ull << (bl + 11)) + Qslack, u = K << 11;
+                            const uint64_t du = lo > u ? lo - u : u - lo;
+                            if (lo > marg && lo < 0ull - marg && du > marg) { c = int(hi) + (u < lo ? 1 : 0); known = true; }
+                        }
+                        if (!known) c = iround_q(qb, uint32_t(rem), K);
+                    }
                     const unsigned nz = __ballot_sync(FULL, c != 0);
                     if (nz == 0) { lv += 32; continue; }
                     const int f = __ffs(nz) - 1;
@@ -860,6 +898,35 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     rem -= cf;
                     if (rem == 0) { ms = lv + f; break; }
                     lv += f + 1;
+                }
+                __syncwarp();
+                // the level draws: parity coin and product key of every level 1..ms,
+                // and labels of levels >= 2: at least kPreLabels and about as many
+                // more as half the level's quota (its collisions), up to kMaxPre
+                {
+                    auto ndraw = [&](int l, int &np) -> int {
+                        np = 0;
+                        if (l > ms) return 0;
+                        if (l == 1) return 2;
+                        int g = kPreLabels / 4 + ((sh.Nq[l] + 7) >> 3);
+                        if (g > kMaxPre / 4) g = kMaxPre / 4;
+                        np = 4 * g;
+                        return 2 + g;
+                    };
+                    int npA, npB;
+                    const int cA_ = ndraw(lane + 1, npA), cB_ = ndraw(lane + 33, npB);
+                    int pA = cA_, pB = cB_;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t0 = __shfl_up_sync(FULL, pA, o), t1 = __shfl_up_sync(FULL, pB, o);
+                        if (lane >= o) { pA += t0; pB += t1; }
+                    }
+                    pB += __shfl_sync(FULL, pA, 31);
+                    sh.dbase[lane + 1] = pA - cA_;
+                    sh.dbase[lane + 33] = pB - cB_;
+                    sh.npre[lane + 1] = uint8_t(npA);
+                    sh.npre[lane + 33] = uint8_t(npB);
+                    if (lane == 31) { sh.dbase[65] = pB; sh.ndraws = pB; }
                 }
                 if (lane == 0) {
                     if (rem > 0) sh.Nq[m + 1] = rem;
@@ -876,27 +943,30 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             __syncthreads();
             m_split = sh.m_eff;
         }
-        // 3. The other draws of levels 1..m_eff, six per level: the parity coin
-        //    (odd counts, Alg. 4.3), the key of the level's product permutation
-        //    and its first kPreLabels labels k (Alg. 4.1), four per draw.
-        for (int t = tid; t < 6 * m_split; t += bs) {
-            const int lv = 1 + t / 6, kind = t - 6 * (lv - 1);
-            if (lv == 1 && kind >= 2) {                 // k = 0 for every level-1 collision
+        // 3. The other draws of levels 1..m_eff: the parity coin (odd counts,
+        //    Alg. 4.3), the key of the level's product permutation and its first
+        //    npre labels k (Alg. 4.1), four per draw.
+        {
+            const int ndr = sh.ndraws;
+            for (int t = tid; t < ndr; t += bs) {
+                int a_ = 1, b_ = m_split;                 // level: the last with dbase <= t
+                while (a_ < b_) {
+                    const int mid = (a_ + b_ + 1) >> 1;
+                    if (sh.dbase[mid] <= t) a_ = mid; else b_ = mid - 1;
+                }
+                const int lv = a_, kind = t - sh.dbase[lv];
+                const uint64_t idx = kind == 0 ? uint64_t(lv) : kind == 1 ? 0ull : uint64_t(kind - 2);
+                const uint64_t aux = kind == 0 ? 0ull : uint64_t(lv);
+                const uint32_t tag = kind == 0 ? TAG_PARITY : kind == 1 ? TAG_PERMK : TAG_KSEL;
+                const U64x4 w = rng.draw(idx, aux, uint32_t(pass), tag);
+                if (kind == 0) {
+                    if ((w.w[0] >> 63) == 0) atomicOr(&sh.coin[lv >> 5], 1u << (lv & 31));   // u < 1/2
+                } else if (kind == 1) {
+                    sh.keys[lv] = w;
+                } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) sh.lab[1][4 * (kind - 2) + j] = 0;
-                continue;
-            }
-            const uint64_t idx = kind == 0 ? uint64_t(lv) : kind == 1 ? 0ull : uint64_t(kind - 2);
-            const uint64_t aux = kind == 0 ? 0ull : uint64_t(lv);
-            const uint32_t tag = kind == 0 ? TAG_PARITY : kind == 1 ? TAG_PERMK : TAG_KSEL;
-            const U64x4 w = rng.draw(idx, aux, uint32_t(pass), tag);
-            if (kind == 0) {
-                if ((w.w[0] >> 63) == 0) atomicOr(&sh.coin[lv >> 5], 1u << (lv & 31));   // u < 1/2
-            } else if (kind == 1) {
-                sh.keys[lv] = w;
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) sh.lab[lv][4 * (kind - 2) + j] = uint8_t(below(w.w[j], uint32_t(lv)));
+                    for (int j = 0; j < 4; ++j) sh.lab[lv][4 * (kind - 2) + j] = uint8_t(below(w.w[j], uint32_t(lv)));
+                }
             }
         }
         __syncthreads();
@@ -936,19 +1006,20 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     int T = sh.Nq[lv] + Dw[lv];
                     if (T & 1) T += (sh.Nq[lv] >= 1 && ((sh.coin[lv >> 5] >> (lv & 31)) & 1u)) ? -1 : 1;
                     const int Cn = T >> 1;
-                    if (Cn <= kPreLabels) {
+                    if (lv == 1) {
+                        if (lane == 0) Dw[0] += 2 * Cn;
+                    } else if (Cn <= kPreLabels) {
                         if (lane < Cn) {
                             const int k = sh.lab[lv][lane];
                             atomicAdd(&Dw[k], 1);
                             atomicAdd(&Dw[lv - 1 - k], 1);
                         }
-                    } else if (lv == 1) {
-                        if (lane == 0) Dw[0] += 2 * Cn;
                     } else {
                         for (int k = lane; k < lv; k += 32) rw[k] = 0;
                         __syncwarp();
-                        for (int c = lane; c < kPreLabels; c += 32) atomicAdd(&rw[sh.lab[lv][c]], 1);
-                        for (int g = kPreLabels / 4 + lane; g < (Cn + 3) >> 2; g += 32) {
+                        const int np = sh.npre[lv], cpre = Cn < np ? Cn : np;
+                        for (int c = lane; c < cpre; c += 32) atomicAdd(&rw[sh.lab[lv][c]], 1);
+                        for (int g = (np >> 2) + lane; g < (Cn + 3) >> 2; g += 32) {
                             const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
