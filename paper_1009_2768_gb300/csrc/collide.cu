@@ -868,7 +868,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     if (qE >= 1011) Q = qM << (qE - 1011);
                     else { Q = qM >> (1011 - qE); Qslack = 1ull << 32; }
                 }
-                int rem = npart, lv = sh.lo, ms = m;
+                int rem = npart, lv = sh.lo, ms = m, htop = 0;
                 while (lv <= m) {
                     const int l = lv + lane;
                     int c = 0;
@@ -895,18 +895,20 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     const int f = __ffs(nz) - 1;
                     const int cf = __shfl_sync(FULL, c, f);
                     if (lane == 0) sh.Nq[lv + f] = cf;
+                    htop = lv + f;
                     rem -= cf;
                     if (rem == 0) { ms = lv + f; break; }
                     lv += f + 1;
                 }
                 __syncwarp();
-                // the level draws: parity coin and product key of every level 1..ms,
-                // and labels of levels >= 2: at least kPreLabels and about as many
-                // more as half the level's quota (its collisions), up to kMaxPre
+                // the level draws: parity coin and product key of every level from 1
+                // to the highest with a quota (none above it has collisions), and
+                // labels of levels >= 2: at least kPreLabels and about as many more
+                // as half the level's quota (its collisions), up to kMaxPre
                 {
                     auto ndraw = [&](int l, int &np) -> int {
                         np = 0;
-                        if (l > ms) return 0;
+                        if (l > htop) return 0;
                         if (l == 1) return 2;
                         int g = kPreLabels / 4 + ((sh.Nq[l] + 7) >> 3);
                         if (g > kMaxPre / 4) g = kMaxPre / 4;
