@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kTT) count_kernel(const Real *x, const Real *v
                                                     const trmc_domain *doms, int nd, int nc_total, const double *dt,
                                                     int64_t *counts, int *status, const uint64_t *cell_key,
                                                     uint32_t problem_id, uint64_t seed, uint64_t step,
-                                                    const uint64_t *step_dev)
+                                                    const uint64_t *step_dev, double *cell_vmax2)
 {
     __shared__ CellDom sd;
     __shared__ unsigned long long tot[3];
@@ -228,16 +228,28 @@ __global__ void __launch_bounds__(kTT) count_kernel(const Real *x, const Real *v
     const int local = c - sd.first;
     const bool ghost = D.bc == TRMC_BC_RESERVOIR && (local == 0 || local == D.n_cells - 1);
     bool bad = false;
-    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-        Real xi = x[i], vi = vx[i];
-        const int nl = mv.move(xi, vi);
-        if (nl < 0) continue;                       // left through a reservoir face
-        int d = nl - local;
-        if (d < -1 || d > 1 || (ghost && d == 0)) { bad = true; d = d < 0 ? -1 : 1; }
-        n3[d + 1]++;
+    constexpr int U = 4;                            // loads issued together
+    for (int64_t i0 = b + threadIdx.x; i0 < e; i0 += U * blockDim.x) {
+        Real xs[U], vs[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + int64_t(u) * blockDim.x;
+            if (i < e) { xs[u] = x[i]; vs[u] = vx[i]; }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + int64_t(u) * blockDim.x >= e) continue;
+            const int nl = mv.move(xs[u], vs[u]);
+            if (nl < 0) continue;                   // left through a reservoir face
+            int d = nl - local;
+            if (d < -1 || d > 1 || (ghost && d == 0)) { bad = true; d = d < 0 ? -1 : 1; }
+            n3[d + 1]++;
+        }
     }
-    if (ghost && threadIdx.x == 0)                  // the refill takes the "stay" slot
+    if (ghost && threadIdx.x == 0) {                // the refill takes the "stay" slot
         n3[1] = (unsigned long long)refill_count(D, c, cell_key, problem_id, seed, step_dev ? *step_dev : step);
+        if (cell_vmax2) cell_vmax2[c] = 0.0;        // the refill kernel takes the maximum over its CTAs
+    }
     if (bad) { if (atomicCAS(status, 0, TRMC_ERR_STATE) == 0) status[1] = c; }
     for (int j = 0; j < 3; ++j) {
         unsigned long long v = n3[j];
@@ -301,7 +313,11 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int64_t *counts, int n
 }
 
 // Kernel 4: refill the ghost cells of reservoir domains from their
-// Maxwellians (one CTA per ghost cell), uniform positions in the cell.
+// Maxwellians (kRefillCTAs CTAs per ghost cell: a ghost cell takes thousands
+// of particles, each a chain of FP64 transcendentals), uniform positions in
+// the cell.  The ghost cell's max |v|^2 (zeroed by kernel 1) is the maximum
+// over the CTAs, taken on the bit patterns of the non-negative values.
+constexpr int kRefillCTAs = 32;
 template <typename Real>
 __global__ void __launch_bounds__(kTT) refill_kernel(const trmc_domain *doms, int nd, int nc_total,
                                                      const int64_t *new_start, const uint64_t *cell_key,
@@ -310,7 +326,8 @@ __global__ void __launch_bounds__(kTT) refill_kernel(const trmc_domain *doms, in
                                                      Real *vzo, int64_t capacity, double *cell_vmax2)
 {
     __shared__ double red[kRedScratch];
-    const int d = blockIdx.x >> 1, side = blockIdx.x & 1;
+    const int part = blockIdx.x % kRefillCTAs, gc = blockIdx.x / kRefillCTAs;
+    const int d = gc >> 1, side = gc & 1;
     if (d >= nd) return;
     const trmc_domain D = doms[d];
     if (D.bc != TRMC_BC_RESERVOIR || !domain_ok(D, nc_total)) return;
@@ -324,7 +341,7 @@ __global__ void __launch_bounds__(kTT) refill_kernel(const trmc_domain *doms, in
     if (cell_key) { rng.problem = cell_key[g] >> 32; rng.cell = cell_key[g] & 0xFFFFFFFFull; }
     const int64_t b = new_start[g], n = new_start[g + 1] - b;
     double vm = 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    for (int64_t j = int64_t(part) * blockDim.x + threadIdx.x; j < n; j += int64_t(kRefillCTAs) * blockDim.x) {
         const U64x4 w = rng.draw(uint64_t(j), 0, 0, TAG_RESERVOIR);
         const U64x4 w2 = rng.draw(uint64_t(j), 1, 0, TAG_RESERVOIR);
         const double r1 = sqrt(-2.0 * log(u01_open(w.w[0]))), a1 = kTwoPi * u01(w.w[1]);
@@ -336,7 +353,8 @@ __global__ void __launch_bounds__(kTT) refill_kernel(const trmc_domain *doms, in
         vm = fmax(vm, __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)));
     }
     vm = block_max(vm, red);
-    if (threadIdx.x == 0 && cell_vmax2) cell_vmax2[g] = vm;
+    if (threadIdx.x == 0 && cell_vmax2 && vm > 0.0)
+        atomicMax(reinterpret_cast<unsigned long long *>(cell_vmax2 + g), (unsigned long long)__double_as_longlong(vm));
 }
 
 // Kernel 3: stable scatter of one old cell into the new order.
@@ -366,13 +384,19 @@ __global__ void __launch_bounds__(kTT) scatter_kernel(const Real *x, const Real 
     typename MoverT<Real>::type mv;
     int local = 0;
     if (sd.d >= 0) { mv = make_mover<Real>(doms[sd.d], dt[sd.d]); local = c - sd.first; }
+    // the next chunk's loads are issued before this chunk's barriers
+    Real nx = 0, nv = 0, ny = 0, nz = 0;
+    if (b + threadIdx.x < e) { nx = x[b + threadIdx.x]; nv = vx[b + threadIdx.x]; ny = vy[b + threadIdx.x]; nz = vz[b + threadIdx.x]; }
     for (int64_t chunk = b; chunk < e; chunk += blockDim.x) {
         const int64_t i = chunk + threadIdx.x;
         bool live = i < e;
-        Real xi = 0, vi = 0, yi = 0, zi = 0;
+        Real xi = nx, vi = nv, yi = ny, zi = nz;
+        {
+            const int64_t in = i + blockDim.x;
+            if (in < e) { nx = x[in]; nv = vx[in]; ny = vy[in]; nz = vz[in]; }
+        }
         int d = 0;
         if (live) {
-            xi = x[i]; vi = vx[i]; yi = vy[i]; zi = vz[i];
             if (sd.d >= 0) {
                 const int nl = mv.move(xi, vi);
                 if (nl < 0) live = false;           // left through a reservoir face
@@ -423,14 +447,14 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_domain *doms, int
     }
     const Real *x = static_cast<const Real *>(st->x), *vx = static_cast<const Real *>(st->vx);
     count_kernel<Real><<<nc, kTT, 0, s>>>(x, vx, st->cell_start, doms, nd, nc, dt, ctx->tr_counts, ctx->status,
-                                          st->cell_key, st->problem_id, ctx->seed, step, st->step_dev);
+                                          st->cell_key, st->problem_id, ctx->seed, step, st->step_dev, st->cell_vmax2);
     scan_kernel<<<1, 1024, 0, s>>>(ctx->tr_counts, nc, st->cell_start_alt, st->capacity, ctx->status);
     scatter_kernel<Real><<<nc, kTT, 0, s>>>(x, vx, static_cast<const Real *>(st->vy), static_cast<const Real *>(st->vz),
                                             st->cell_start, doms, nd, dt, ctx->tr_counts, st->cell_start_alt, nc,
                                             static_cast<Real *>(st->x_alt), static_cast<Real *>(st->vx_alt),
                                             static_cast<Real *>(st->vy_alt), static_cast<Real *>(st->vz_alt),
                                             ctx->status, st->capacity);
-    refill_kernel<Real><<<2 * nd, kTT, 0, s>>>(doms, nd, nc, st->cell_start_alt, st->cell_key, st->problem_id, ctx->seed,
+    refill_kernel<Real><<<2 * nd * kRefillCTAs, kTT, 0, s>>>(doms, nd, nc, st->cell_start_alt, st->cell_key, st->problem_id, ctx->seed,
                                                step, st->step_dev, static_cast<Real *>(st->x_alt),
                                                static_cast<Real *>(st->vx_alt), static_cast<Real *>(st->vy_alt),
                                                static_cast<Real *>(st->vz_alt), st->capacity, st->cell_vmax2);
