@@ -260,7 +260,11 @@ def ours(args):
         sim.step()
     T.trmc_check(sim.ctx)
     launch = None
-    if not args.no_tune:
+    if args.launch:
+        th, per = (int(v) for v in args.launch.lower().split("x"))
+        T.trmc_set_collide_launch(sim.ctx, th, per)
+        launch = {"threads": th, "ctas_per_sm": per, "tuned_ms": None}
+    elif not args.no_tune:
         # the collide launch shape (threads per CTA, CTAs per SM) for this
         # workload's cell sizes, measured on the live state before timing
         from paper_1009_2768_gb300 import runtime as RT
@@ -450,6 +454,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default collide launch shape")
+    ap.add_argument("--launch", default="", help="collide launch shape THREADSxCTAS_PER_SM (no autotuning)")
     ap.add_argument("--workload", default="shock", choices=["shock", "batched", "bkw", "stationary", "serving"])
     ap.add_argument("--rates", default="1,10,50,200", help="serving: arrival rates (requests/s) to sweep")
     ap.add_argument("--requests", type=int, default=0, help="serving: requests per rate (default 8*rate in [8, 48])")

@@ -213,8 +213,13 @@ __global__ void __launch_bounds__(kTT) count_kernel(const Real *x, const Real *v
 {
     __shared__ CellDom sd;
     __shared__ unsigned long long tot[3];
+    __shared__ typename MoverT<Real>::type smv;    // set up once per CTA (FP64 divisions: 2 lanes/clk/SM)
     const int c = blockIdx.x;
-    if (threadIdx.x == 0) { sd = find_domain(doms, nd, c, nc_total, status); tot[0] = tot[1] = tot[2] = 0; }
+    if (threadIdx.x == 0) {
+        sd = find_domain(doms, nd, c, nc_total, status);
+        tot[0] = tot[1] = tot[2] = 0;
+        if (sd.d >= 0) smv = make_mover<Real>(doms[sd.d], dt[sd.d]);
+    }
     __syncthreads();
     const int64_t b = cs[c], e = cs[c + 1];
     unsigned long long n3[3] = {0, 0, 0};
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(kTT) count_kernel(const Real *x, const Real *v
         return;
     }
     const trmc_domain D = doms[sd.d];
-    const auto mv = make_mover<Real>(D, dt[sd.d]);
+    const auto mv = smv;
     const int local = c - sd.first;
     const bool ghost = D.bc == TRMC_BC_RESERVOIR && (local == 0 || local == D.n_cells - 1);
     bool bad = false;
@@ -369,10 +374,12 @@ __global__ void __launch_bounds__(kTT) scatter_kernel(const Real *x, const Real 
     __shared__ CellDom sd;
     __shared__ int64_t dest[3];
     __shared__ int wcnt[3][kTT / 32];
+    __shared__ typename MoverT<Real>::type smv;
     const int c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) {
         sd = find_domain(doms, nd, c, nc_total, status);
+        if (sd.d >= 0) smv = make_mover<Real>(doms[sd.d], dt[sd.d]);
         // where this cell's movers land in the new order (stable: particles from
         // the left neighbour first, then stayers, then those from the right)
         dest[2] = (c + 1 < nc_total) ? new_start[c + 1] : 0;                        // going right
@@ -383,7 +390,7 @@ __global__ void __launch_bounds__(kTT) scatter_kernel(const Real *x, const Real 
     const int64_t b = cs[c], e = cs[c + 1];
     typename MoverT<Real>::type mv;
     int local = 0;
-    if (sd.d >= 0) { mv = make_mover<Real>(doms[sd.d], dt[sd.d]); local = c - sd.first; }
+    if (sd.d >= 0) { mv = smv; local = c - sd.first; }
     // the next chunk's loads are issued before this chunk's barriers
     Real nx = 0, nv = 0, ny = 0, nz = 0;
     if (b + threadIdx.x < e) { nx = x[b + threadIdx.x]; nv = vx[b + threadIdx.x]; ny = vy[b + threadIdx.x]; nz = vz[b + threadIdx.x]; }
