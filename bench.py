@@ -52,12 +52,24 @@ METRIC = "particle-steps/s"
 # of the same command, keyed by the hash of csrc/collide.cu it was taken on; reported as
 # null once the kernel source differs.  See profiles/.
 NCU_TRAFFIC = {
-    "shock": {"collide_sha": "b25a8d8fef70e017", "bytes": 27217664 + 666624, "fp64_pipe_active_pct": 59.1},
+    "shock": {"collide_sha": "3fbd60759f49d794", "launch": (128, 4), "bytes": 26592768 + 334080,
+              "fp64_pipe_active_pct": 54.4},
+    "stationary": {"collide_sha": "3fbd60759f49d794", "launch": (256, 2), "bytes": 123477760 + 67439104,
+                   "fp64_pipe_active_pct": 10.3},
+    "batched": {"collide_sha": "3fbd60759f49d794", "launch": (256, 2), "bytes": 86460672 + 73230848,
+                "fp64_pipe_active_pct": 8.2},
 }
+
+# Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
+# runtime.autotune_collide's candidates on GB300 (--tune measures them again).
+LAUNCH = {"shock": (128, 4), "stationary": (256, 2), "batched": (256, 2), "bkw": (128, 4)}
 
 
 def collide_sha():
-    return hashlib.sha256(open(os.path.join(ROOT, "paper_1009_2768_gb300", "csrc", "collide.cu"), "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("collide.cu", "trmc_device.cuh", "fp64_tables.inc"):
+        h.update(open(os.path.join(ROOT, "paper_1009_2768_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -259,14 +271,9 @@ def ours(args):
     for _ in range(args.warmup):
         sim.step()
     T.trmc_check(sim.ctx)
-    launch = None
-    if args.launch:
-        th, per = (int(v) for v in args.launch.lower().split("x"))
-        T.trmc_set_collide_launch(sim.ctx, th, per)
-        launch = {"threads": th, "ctas_per_sm": per, "tuned_ms": None}
-    elif not args.no_tune:
-        # the collide launch shape (threads per CTA, CTAs per SM) for this
-        # workload's cell sizes, measured on the live state before timing
+    if args.tune:
+        # the collide launch shape for this workload's cell sizes, measured on
+        # the live state before timing
         from paper_1009_2768_gb300 import runtime as RT
         times, best = RT.autotune_collide(sim, steps=3)
         launch = {"threads": best[0], "ctas_per_sm": best[1], "tuned_ms": {f"{k[0]}x{k[1]}": round(v, 4)
@@ -274,6 +281,11 @@ def ours(args):
         for _ in range(2):
             sim.step()
         T.trmc_check(sim.ctx)
+    else:
+        th, per = ((int(v) for v in args.launch.lower().split("x")) if args.launch
+                   else LAUNCH.get(args.workload, (128, 4)))
+        T.trmc_set_collide_launch(sim.ctx, th, per)
+        launch = {"threads": th, "ctas_per_sm": per, "tuned_ms": None}
     K = args.steps
     clocks = Clocks(local)
     if dist:
@@ -308,7 +320,8 @@ def ours(args):
         kern, abytes, dur = "transport (count+scan+scatter)", transport_bytes, tr_avg
     achieved = abytes / dur / 1e9
     tr_rec = NCU_TRAFFIC.get(args.workload)
-    fresh = bool(tr_rec and kern == "collide_kernel" and tr_rec["collide_sha"] == collide_sha())
+    fresh = bool(tr_rec and kern == "collide_kernel" and tr_rec["collide_sha"] == collide_sha()
+                 and tuple(tr_rec["launch"]) == (launch["threads"], launch["ctas_per_sm"]))
     traffic = tr_rec["bytes"] if fresh else None
     roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
@@ -453,8 +466,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--no-tune", action="store_true", help="keep the default collide launch shape")
-    ap.add_argument("--launch", default="", help="collide launch shape THREADSxCTAS_PER_SM (no autotuning)")
+    ap.add_argument("--tune", action="store_true", help="choose the collide launch shape with the autotuner")
+    ap.add_argument("--launch", default="", help="collide launch shape THREADSxCTAS_PER_SM (default: per workload)")
     ap.add_argument("--workload", default="shock", choices=["shock", "batched", "bkw", "stationary", "serving"])
     ap.add_argument("--rates", default="1,10,50,200", help="serving: arrival rates (requests/s) to sweep")
     ap.add_argument("--requests", type=int, default=0, help="serving: requests per rate (default 8*rate in [8, 48])")

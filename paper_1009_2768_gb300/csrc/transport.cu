@@ -177,12 +177,21 @@ __global__ void cfl_kernel(const trmc_domain *doms, int nd, int nc_total, const 
         if (threadIdx.x == 0) dt[d] = 0.0;
         return;
     }
-    double vm = 0.0;
-    for (int c = threadIdx.x; c < D.n_cells; c += blockDim.x) vm = fmax(vm, cell_vmax2[D.cell_begin + c]);
-    vm = block_max(vm, red);
-    const double dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(interior_cells(D)));
-    const double h = (vm > 0.0) ? __ddiv_rn(__dmul_rn(cfl, dx), __dsqrt_rn(vm)) : 0.0;
-    if (threadIdx.x == 0) dt[d] = h;
+    __shared__ double sh_h;
+    // maximum on the bit patterns of the non-negative values: no FP64 instruction
+    // per cell; the step itself is computed once, by thread 0
+    long long vb = 0;
+    for (int c = threadIdx.x; c < D.n_cells; c += blockDim.x)
+        vb = max(vb, __double_as_longlong(cell_vmax2[D.cell_begin + c]));
+    const double vm = block_max_nonneg(__longlong_as_double(vb), red);
+    if (threadIdx.x == 0) {
+        const double dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(interior_cells(D)));
+        const double h = (vm > 0.0) ? __ddiv_rn(__dmul_rn(cfl, dx), __dsqrt_rn(vm)) : 0.0;
+        dt[d] = h;
+        sh_h = h;
+    }
+    __syncthreads();
+    const double h = sh_h;
     if (cell_param)
         for (int c = threadIdx.x; c < D.n_cells; c += blockDim.x) cell_param[D.cell_begin + c].dt = h;
 }
@@ -450,7 +459,7 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_domain *doms, int
         ctx->tr_cells = nc;
     }
     if (cfl > 0.0) {
-        cfl_kernel<<<nd, 256, 0, s>>>(doms, nd, nc, st->cell_vmax2, cfl, dt, st->cell_param);
+        cfl_kernel<<<nd, 512, 0, s>>>(doms, nd, nc, st->cell_vmax2, cfl, dt, st->cell_param);
     }
     const Real *x = static_cast<const Real *>(st->x), *vx = static_cast<const Real *>(st->vx);
     count_kernel<Real><<<nc, kTT, 0, s>>>(x, vx, st->cell_start, doms, nd, nc, dt, ctx->tr_counts, ctx->status,
