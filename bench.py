@@ -156,6 +156,92 @@ def oracle_tube_rate(n_cells, mean, steps, threads, seed=0, budget_s=None):
     return n * done / el, n, done, el
 
 
+def oracle_workload_rate(workload, threads, budget_s=15.0, seed=0):
+    """Particle-steps/s of the FP64 CPU oracle on a bounded sample of a
+    workload other than the shock tubes: (rate, particles, steps, seconds,
+    sample description).  Same generators and parameters as workloads.py."""
+    from oracle import oracle as O
+    from paper_1009_2768_gb300 import synth
+    from paper_1009_2768_gb300.workloads import rankine_hugoniot
+    t_setup = time.perf_counter()
+    if workload == "batched":
+        # the first 512 of the 4096 cells (same log-uniform counts, eps and anisotropy)
+        g = synth.rng(seed)
+        counts = synth.loguniform_ints(4096, 64, 8192, g=g)
+        eps = synth.loguniform(4096, 1e-4, 10.0, g=g)
+        ratio = g.uniform(0.3, 3.0, 4096)
+        k = 512
+        counts, eps, ratio = counts[:k], eps[:k], ratio[:k]
+        t_perp = 3.0 / (ratio + 2.0)
+        cs = synth.starts(counts)
+        ci = np.zeros((k, O.INIT_COLS))
+        ci[:, 0] = O.INIT_BIMAXWELL
+        ci[:, 4] = ratio * t_perp
+        ci[:, 5] = t_perp
+        keys = np.arange(k, dtype=np.uint64) << np.uint64(32)
+        _, v = O.init_cells(ci, cs, seed, cell_key=keys, with_x=False)
+        cp = np.stack([eps, np.full(k, 0.05), 1.0 / counts, np.full(k, 0.6)], axis=1)
+        prm = O.collide_params(trunc=O.TRUNC_RAD, m=2, seed=seed)
+        ms = np.full(k, 2, np.int32)
+        n = int(cs[-1])
+        desc = f"cells 0..511 of the 4096 ({n} particles), collide steps"
+        def step(s):
+            nonlocal v, ms
+            v, _, ms = O.collide(v, cs, prm, s, m_state=ms, cell_param=cp.ravel(), cell_key=keys, threads=threads)
+    elif workload == "stationary":
+        # the whole stationary shock (4000 cells + 2 reservoir ghosts, 1e7 particles), first steps
+        left, right = rankine_hugoniot(3.0)
+        nc0, mean = 4000, 2500
+        dx, mass = 1.0 / nc0, (0.5 * left[0] + 0.5 * right[0]) / (nc0 * mean)
+        nc = nc0 + 2
+        counts = np.empty(nc, np.int64)
+        ci = np.zeros((nc, O.INIT_COLS))
+        for c in range(nc):
+            rho, u, Tm = left if (c - 0.5) * dx < 0.5 else right
+            counts[c] = int(round(rho * dx / mass))
+            ci[c] = [O.INIT_MAXWELL, u, 0, 0, Tm, 0, 0, (c - 1) * dx, c * dx]
+        cs = synth.starts(counts)
+        x, v = O.init_cells(ci, cs, seed)
+        cp = np.zeros((nc, 4))
+        cp[:, 0] = 1e-3
+        cp[[0, -1], 0] = 1e300
+        cp[:, 2] = mass / dx
+        cp[:, 3] = 1.0
+        doms = [O.domain(0, nc, 0.0, 1.0, O.BC_RESERVOIR, left, right, mass)]
+        prm = O.collide_params(trunc=O.TRUNC_RAD, m=2, seed=seed)
+        ms = np.full(nc, 2, np.int32)
+        n = int(cs[-1])
+        desc = f"the whole stationary shock ({n} particles), transport + collide, first steps"
+        def step(s):
+            nonlocal x, v, cs, ms
+            dt = O.cfl_dt(v, cs, doms, 0.5)
+            x, v, cs = O.transport(x, v, cs, doms, dt, step=s, seed=seed, capacity=int(1.25 * n) + 4 * mean)
+            cp[:, 1] = dt[0]
+            v, _, ms = O.collide(v, cs, prm, s, m_state=ms, cell_param=cp.ravel(), threads=threads)
+    else:                                   # bkw: one cell of 1e5, single-threaded like the workload's one CTA
+        n = 100000
+        cs = np.array([0, n], np.int64)
+        ci = np.array([[O.INIT_BKW, 0, 0, 0, 1.0, 0, 0.6, 0, 1]], np.float64)
+        _, v = O.init_cells(ci, cs, seed, with_x=False)
+        prm = O.collide_params(dt=0.05, eps=1.0, alpha=0.0, rho_scale=1.0 / n, trunc=O.TRUNC_RAD, m=2,
+                               indicator=O.IND_M4, seed=seed)
+        ms = np.full(1, 2, np.int32)
+        threads = 1
+        desc = "the BKW cell (1e5 particles), collide steps, one thread"
+        def step(s):
+            nonlocal v, ms
+            v, _, ms = O.collide(v, cs, prm, s, m_state=ms, threads=1)
+    setup = time.perf_counter() - t_setup
+    done, t0 = 0, time.perf_counter()
+    while True:
+        step(done)
+        done += 1
+        if time.perf_counter() - t0 > budget_s or done >= 1000:
+            break
+    el = time.perf_counter() - t0
+    return n * done / el, n, done, el, f"{desc}: {done} steps in {el:.1f} s (set-up {setup:.1f} s)", threads
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -365,9 +451,13 @@ def ours(args):
         from oracle.build import build_oracle
         build_oracle()
         threads = os.cpu_count() or 1
-        rate, nn, done, el = oracle_tube_rate(N_CELLS, MEAN, 1000, threads, budget_s=15.0)
-        cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
-               "sample": f"one full tube (eps 1e-2, {nn} particles), {done} steps in {el:.1f} s"}
+        if args.workload == "shock":
+            rate, nn, done, el = oracle_tube_rate(N_CELLS, MEAN, 1000, threads, budget_s=15.0)
+            cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
+                   "sample": f"one full tube (eps 1e-2, {nn} particles), {done} steps in {el:.1f} s"}
+        else:
+            rate, nn, done, el, desc, used = oracle_workload_rate(args.workload, threads)
+            cpu = {"value": rate, "unit": METRIC, "cores": used, "kind": "oracle", "sample": desc}
 
     forms = None
     if rank == 0 and args.workload == "shock" and not args.no_forms:
