@@ -126,6 +126,24 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(ms, dist=None):
+    """The slowest rank's time (all ranks get it); the input itself without a
+    process group.  A device tensor under NCCL, a host tensor otherwise."""
+    if dist is None:
+        return ms
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(n_per_rank, world, steps, total_ms):
+    """Whole-job particle-steps/s of `world` independent replicas of n
+    particles each, over `steps` steps timed by the slowest rank."""
+    return n_per_rank * world * steps / (total_ms / 1e3)
+
+
 # ------------------------------------------------------------------ CPU oracle
 def oracle_tube_rate(n_cells, mean, steps, threads, seed=0, budget_s=None):
     """Particle-steps/s of the FP64 CPU oracle on one shock tube (eps 1e-2)."""
@@ -387,12 +405,8 @@ def ours(args):
     clk = clocks.stop()
     T.trmc_check(sim.ctx)
     step_ms = tr_ms + co_ms
-    total_ms = float(step_ms.sum())
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = n * world * K / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(step_ms.sum()), dist)
+    value = replica_throughput(n, world, K, total_ms)
     st = dict(zip(T.STATS_FIELDS, stats.cpu().numpy().tolist()))
 
     # roofline of the dominant kernel, from the same events
