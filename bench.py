@@ -326,6 +326,25 @@ def time_steps(sim, K, flush, stats=None):
     return tr, co
 
 
+def time_graph_steps(sim, K, flush, stats):
+    """K steps of a workload without transport, each one replay of a
+    captured single-step CUDA graph (cell order + collide), bracketed by
+    CUDA events, with an L2 flush before each; (transport, collide) ms."""
+    import torch
+    from paper_1009_2768_gb300.runtime import GraphStepper
+    g = GraphStepper(sim, steps_per_graph=1, warmup=2, step_kwargs={"stats": stats})
+    stats.zero_()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record()
+        g.replay()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    co = np.array([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)])
+    return np.zeros(K), co
+
+
 def compare_forms(flush, steps=60, warm=5):
     """The plain single-problem FP64 form (one tube alone) against the batched
     FP32-mixed form (the four tubes in one launch), on the same GPU, with the
@@ -398,7 +417,11 @@ def ours(args):
     clocks.start()
     time.sleep(0.2)
     t_wall = time.perf_counter()
-    tr_ms, co_ms = time_steps(sim, K, flush, stats)
+    if args.workload == "batched":
+        # one persistent collide launch per step, replayed from a captured CUDA graph
+        tr_ms, co_ms = time_graph_steps(sim, K, flush, stats)
+    else:
+        tr_ms, co_ms = time_steps(sim, K, flush, stats)
     t_wall = time.perf_counter() - t_wall
     if dist:
         dist.barrier()
@@ -485,6 +508,7 @@ def ours(args):
             "config": {"workload": WORKLOADS[args.workload], "particles_per_gpu": n,
                        "cells_per_gpu": sim.state.n_cells,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
+                       "cuda_graph": args.workload == "batched",
                        "collide_launch": launch},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": sim.launches_per_step * K, "clocks": clk, "forms": forms,
@@ -535,9 +559,42 @@ def serving_bench(args):
                  mean_particles=float(np.mean([r.particles for r in out])),
                  errors=[r.error for r in out if r.error][:3])
         sweep.append(s)
+        last = (i, n_req, rid - n_req, out)
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     eng.close()
+    # The plain single-problem FP64 form on the same stream as the highest rate:
+    # one slot, FP64 contexts, the same requests (same problem ids and seed), so
+    # its latencies and throughput stand beside the served FP32-mixed ones, and
+    # the moment tables of the two forms give their difference (Monte Carlo
+    # noise included: the two forms draw their trees from different arithmetic).
+    i, n_req, first, out32 = last
+    reqs64 = requests_from(synth.poisson_requests(n_req, rates[i], g=synth.rng(1000 * rank + i)),
+                           steps=args.req_steps, first_id=first)
+    eng64 = GpuEngine(n_slots=1, precision=T.FP64, seed=rank, workspace_bytes=512 << 20, chunk=args.chunk, depth=2)
+    out64 = ServingLoop(eng64, budget - eng64.fixed_bytes).run(reqs64)
+    eng64.close()
+    s64 = summary(out64)
+    svc = np.array([(r.done - r.admitted) * 1e3 for r in out64 if r.done is not None and r.error is None])
+    by_id = {r.rid: r for r in out32 if r.result is not None}
+    diffs = []
+    for r in out64:
+        a = by_id.get(r.rid)
+        if r.result is None or a is None or a.result.shape != r.result.shape:
+            continue
+        t32, t64 = a.result[:, 5], r.result[:, 5]
+        ok = np.isfinite(t32) & np.isfinite(t64) & (np.abs(t64) > 0)
+        if ok.any():
+            diffs.append(float(np.abs(t32[ok] - t64[ok]).sum() / np.abs(t64[ok]).sum()))
+    fp64_single = {"rate": rates[i], "slots": 1, "p50_ms": s64.get("p50_ms"), "p99_ms": s64.get("p99_ms"),
+                   "service_p50_ms": float(np.percentile(svc, 50)) if svc.size else None,
+                   "service_p99_ms": float(np.percentile(svc, 99)) if svc.size else None,
+                   "particle_steps_per_s": s64.get("particle_steps_per_s"), "completed": s64.get("completed"),
+                   "moment_error": {"what": "per request, L1 relative difference of the cells' temperature "
+                                            "after the last step, FP32-mixed served vs FP64 single-problem, "
+                                            "same requests and seed (statistical noise included)",
+                                    "median": float(np.median(diffs)) if diffs else None,
+                                    "max": float(np.max(diffs)) if diffs else None, "requests": len(diffs)}}
     top = sweep[-1]
     value = top.get("particle_steps_per_s") or 0.0
     peak, peak_kind = peaks()
@@ -552,6 +609,7 @@ def serving_bench(args):
                        "l2": "requests far larger than L2 on average (mean 3.8e6 particles)",
                        "parallelism": f"replicas x{world}"},
             "serving": sweep,
+            "fp64_single": fp64_single,
             "roofline": {"bound": "hbm", "kernel": "all kernels of the served mix", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": None},

@@ -28,10 +28,13 @@ def largest_first(cell_start):
 
 class GraphStepper:
     """Replays `steps_per_graph` steps of `sim` (an object with .state,
-    .ctx and .step()) from one captured CUDA graph."""
+    .ctx and .step()) from one captured CUDA graph; `step_kwargs` (e.g. a
+    statistics buffer, which then accumulates over replays) are passed to
+    the captured steps."""
 
-    def __init__(self, sim, steps_per_graph=2, warmup=2):
+    def __init__(self, sim, steps_per_graph=2, warmup=2, step_kwargs=None):
         import torch
+        kw = dict(step_kwargs or {})
         self.sim = sim
         transports = getattr(sim, "transports", False)
         if transports and steps_per_graph % 2:
@@ -49,7 +52,7 @@ class GraphStepper:
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph, stream=self.stream):
             for _ in range(steps_per_graph):
-                sim.step()
+                sim.step(**kw)
         torch.cuda.current_stream().wait_stream(self.stream)
 
     def replay(self, times=1):
