@@ -1529,31 +1529,23 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
     const int pool0 = sh.n0 + sh.D0;
     const int32_t *ext = sh.ext;
     auto pslot = [&](int t) { return t < R0 ? inv[pool0 + t] : ext[t - R0]; };
+    Sum<Real> rs[4];                  // the stored set's sums, for the carry (FP32-mixed)
     if (R >= 2) {
-        Sum<Real> qs[3];
+        // one pass for the samples and their first and second moments:
+        // e = sum |z - zbar|^2 = sum |z|^2 - zbar . sum z
+        Sum<Real> qs[4];
         for (int t = tid; t < R; t += bs) {
             Real z0, z1, z2;
             Math<Real>::normals(rng.draw(uint64_t(t), 0, 0, TAG_MAXW), z0, z1, z2);
             const int sl = pslot(t);
             Vx[sl] = z0; Vy[sl] = z1; Vz[sl] = z2;
             qs[0].add(z0); qs[1].add(z1); qs[2].add(z2);
+            qs[3].add_sq3(z0, z1, z2);
         }
-        double s[3], zb[3];
-        block_sums<3>(qs, s, sh.red, double(R), zb);       // zb: the samples' mean
-        const double zb0 = zb[0], zb1 = zb[1], zb2 = zb[2];
+        double s[4], zq[4];
+        block_sums<4>(qs, s, sh.red, double(R), zq);       // zq[0..2]: the samples' mean
+        const double zb0 = zq[0], zb1 = zq[1], zb2 = zq[2];
         const Real rz0 = Real(zb0), rz1 = Real(zb1), rz2 = Real(zb2);
-        Sum<Real> qe[1];
-        for (int t = tid; t < R; t += bs) {
-            const int sl = pslot(t);
-            if constexpr (sizeof(Real) == 8) {
-                const double a0 = Vx[sl] - zb0, a1 = Vy[sl] - zb1, a2 = Vz[sl] - zb2;
-                qe[0].add(a0 * a0 + a1 * a1 + a2 * a2);
-            } else {
-                qe[0].add_sq3(Vx[sl] - rz0, Vy[sl] - rz1, Vz[sl] - rz2);
-            }
-        }
-        double e[1];
-        block_sums<1>(qe, e, sh.red);
         // target: what the set carried, minus the collisions' round-off change,
         // plus what earlier steps' rounding to the storage precision left over;
         // the energy scale and the mean are computed once, by four lanes
@@ -1565,19 +1557,21 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 sh.Pt[0] = Pt0; sh.Pt[1] = Pt1; sh.Pt[2] = Pt2; sh.Et = Et;
                 double et = Et - (Pt0 * Pt0 + Pt1 * Pt1 + Pt2 * Pt2) / double(R);
                 if (et < 0.0) et = 0.0;
-                sh.msc[0] = (e[0] > 0.0) ? sqrt(et / e[0]) : 0.0;
+                const double e = s[3] - (s[0] * zb0 + s[1] * zb1 + s[2] * zb2);
+                sh.msc[0] = (e > 0.0) ? sqrt(et / e) : 0.0;
             } else {
                 sh.msc[lane] = (lane == 1 ? Pt0 : lane == 2 ? Pt1 : Pt2) / double(R);
             }
         }
         __syncthreads();
         const double sc = sh.msc[0], u0 = sh.msc[1], u1 = sh.msc[2], u2 = sh.msc[3];
+        const bool carry = a.cell_carry != nullptr;
         if constexpr (sizeof(Real) == 8) {
             for (int t = tid; t < R; t += bs) {
                 const int sl = pslot(t);
-                Vx[sl] = u0 + sc * (Vx[sl] - zb0);
-                Vy[sl] = u1 + sc * (Vy[sl] - zb1);
-                Vz[sl] = u2 + sc * (Vz[sl] - zb2);
+                const double x = u0 + sc * (Vx[sl] - zb0), y = u1 + sc * (Vy[sl] - zb1), z = u2 + sc * (Vz[sl] - zb2);
+                Vx[sl] = x; Vy[sl] = y; Vz[sl] = z;
+                if (carry) { rs[0].add(x); rs[1].add(y); rs[2].add(z); rs[3].add_sq3(x, y, z); }
             }
         } else {
             // FP64 scale and targets, applied in float: the stored result is a
@@ -1585,9 +1579,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             const Real fs = Real(sc), f0 = Real(u0), f1 = Real(u1), f2 = Real(u2);
             for (int t = tid; t < R; t += bs) {
                 const int sl = pslot(t);
-                Vx[sl] = f0 + fs * (Vx[sl] - rz0);
-                Vy[sl] = f1 + fs * (Vy[sl] - rz1);
-                Vz[sl] = f2 + fs * (Vz[sl] - rz2);
+                const Real x = f0 + fs * (Vx[sl] - rz0), y = f1 + fs * (Vy[sl] - rz1), z = f2 + fs * (Vz[sl] - rz2);
+                Vx[sl] = x; Vy[sl] = y; Vz[sl] = z;
+                if (carry) { rs[0].add(x); rs[1].add(y); rs[2].add(z); rs[3].add_sq3(x, y, z); }
             }
         }
     }
@@ -1596,13 +1590,6 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         // new carry: what the stored thermalised set misses of its target
         // (R >= 2), or the collisions' round-off change (R <= 1)
         if (R >= 2) {
-            Sum<Real> rs[4];
-            for (int t = tid; t < R; t += bs) {
-                const int sl = pslot(t);
-                const Real x = Vx[sl], y = Vy[sl], z = Vz[sl];
-                rs[0].add(x); rs[1].add(y); rs[2].add(z);
-                rs[3].add_sq3(x, y, z);
-            }
             double r[4];
             block_sums<4>(rs, r, sh.red);
             if (tid == 0) {
