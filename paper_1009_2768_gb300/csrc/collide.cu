@@ -41,7 +41,11 @@ namespace trmc {
 namespace {
 
 constexpr int NLEV = kMC + 2;
-constexpr int kWarpLevel = 64;     // levels with at most this many collisions run in one warp
+// Levels with at most warp_level collisions are "deep": they run in one warp or
+// in dependency order from precomputed records, the others by the whole CTA.
+// Measured on GB300: 32 for FP64 (its collisions are slow; spread them over the
+// CTA), 128 for FP32.
+constexpr int kWarpLevel64 = 32, kWarpLevel32 = 128;
 constexpr int kPreLabels = 16;     // labels per level drawn ahead of the plan, at least
 constexpr int kMaxPre = 64;        // and at most
 
@@ -67,6 +71,7 @@ struct Args {
     char *slabs;
     size_t slab_bytes;
     int smem_bytes;
+    int warp_level;
 };
 
 template <typename Real>
@@ -95,12 +100,12 @@ struct Sh {
     int32_t *Mt, *St;
     Real *IBuf, *OBuf;
     double *ILBuf, *OLBuf;           // TRMC-WB: tree length of every consumer slot / output
-    // deep levels (at most kWarpLevel collisions) in ascending order, the
+    // deep levels (at most warp_level collisions) in ascending order, the
     // offset of their collisions in the per-collision records, and the records:
     // exclusive label prefix per level (triangular rows), input and output
     // locations, acceptance threshold xi*Sigma and scattering direction
     int32_t WL[NLEV], WB[NLEV + 1], nWL;
-    // the tail: deep levels above the highest level of more than kWarpLevel
+    // the tail: deep levels above the highest level of more than warp_level
     // collisions (LB); its records from index tail0 run in dependency order:
     // prodOf maps a tail consumer slot (from IB[LB + 1]) to the record that
     // fills it, done holds the round in which a record ran (0: not yet)
@@ -538,6 +543,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 }
             }
         }
+        for (int w = tid; w < (n + 31) >> 5; w += bs) sh.flags[w] = 0u;     // change flags, set by the roles
         // totals, and the mean velocity (warp 0 divides, once per cell)
         double s[5] = {0, 0, 0, 0, 0}, su[5];
         if (need_m4) {
@@ -725,10 +731,10 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             if (lane == 0 && m >= 64) { sh.O[65] = Otot; sh.IB[65] = Dge1; }
             sh.D[jA] = dA; sh.D[jB] = dB; sh.C[jA] = cA; sh.C[jB] = cB;
             if (lane == 0) { sh.D[64] = 0; sh.D[65] = 0; sh.C[64] = c64; sh.C[65] = 0; }
-            // deep levels (at most kWarpLevel collisions) in ascending order with
+            // deep levels (at most warp_level collisions) in ascending order with
             // the offsets of their collisions in the per-collision records
-            const bool wA = inA && cA > 0 && cA <= kWarpLevel, wB = inB && cB > 0 && cB <= kWarpLevel;
-            const bool w64 = m >= 64 && c64 > 0 && c64 <= kWarpLevel;
+            const bool wA = inA && cA > 0 && cA <= a.warp_level, wB = inB && cB > 0 && cB <= a.warp_level;
+            const bool w64 = m >= 64 && c64 > 0 && c64 <= a.warp_level;
             const unsigned bwA = __ballot_sync(FULL, wA), bwB = __ballot_sync(FULL, wB);
             const unsigned ltm = (1u << lane) - 1u;
             const int iA = __popc(bwA & ltm), iB = __popc(bwA) + __popc(bwB & ltm);
@@ -745,10 +751,10 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             if (wA) { sh.WL[iA] = jA; sh.WB[iA] = eA - ownA; }
             if (wB) { sh.WL[iB] = jB; sh.WB[iB] = eB - ownB; }
             // the tail: deep levels above the highest level of more than
-            // kWarpLevel collisions (LB)
-            const unsigned lbB = __ballot_sync(FULL, inB && cB > kWarpLevel);
-            const unsigned lbA = __ballot_sync(FULL, inA && cA > kWarpLevel);
-            const int LB = (m >= 64 && c64 > kWarpLevel) ? 64 : lbB ? 63 - __clz(lbB) : lbA ? 31 - __clz(lbA) : 0;
+            // warp_level collisions (LB)
+            const unsigned lbB = __ballot_sync(FULL, inB && cB > a.warp_level);
+            const unsigned lbA = __ballot_sync(FULL, inA && cA > a.warp_level);
+            const int LB = (m >= 64 && c64 > a.warp_level) ? 64 : lbB ? 63 - __clz(lbB) : lbA ? 31 - __clz(lbA) : 0;
             const int jt = __popc(__ballot_sync(FULL, wA && jA <= LB)) + __popc(__ballot_sync(FULL, wB && jB <= LB));
             const int WBjt = __reduce_add_sync(FULL, unsigned((wA && jA <= LB ? cA : 0) + (wB && jB <= LB ? cB : 0)));
             const int IBlb = __reduce_add_sync(FULL, unsigned((jA >= 1 && jA <= LB ? dA : 0) + (jB <= LB ? dB : 0)));
@@ -1082,15 +1088,13 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         }
         if (pass == 0) {
             // which slots change: every rank from n0 on (leaves and thermalised)
-            for (int w = tid; w < (npart + 31) >> 5; w += bs) sh.flags[w] = 0u;
-            __syncthreads();
-            for (int r = n0 + tid; r < npart; r += bs) {
+            for (int r = n0 + tid; r < npart; r += bs) {          // (flags cleared with the staging)
                 const int i = inv[r];
                 atomicOr(&sh.flags[i >> 5], 1u << (i & 31));
             }
         }
 
-        // 5. collision waves, level 1 first.  Levels of at most kWarpLevel
+        // 5. collision waves, level 1 first.  Levels of at most warp_level
         //    collisions (the deep ones) run in warp 0 alone, with warp-level
         //    synchronisation; a CTA barrier is needed only where a larger
         //    level follows them.
@@ -1312,7 +1316,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         for (int lv = 1; lv <= lv_end; ++lv) {
             const int Cn = sh.C[lv];
             if (Cn == 0) continue;
-            if (Cn <= kWarpLevel) {
+            if (Cn <= a.warp_level) {
                 warp_only = true;
                 const int base = nWL > 0 ? sh.WB[jw++] : 0;
                 if (warp != 0) continue;
@@ -1782,6 +1786,7 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     a.slabs = ctx->slabs;
     a.slab_bytes = (ctx->slabs_bytes / size_t(grid)) & ~size_t(255);
     a.smem_bytes = smem;
+    a.warp_level = sizeof(Real) == 8 ? kWarpLevel64 : kWarpLevel32;
     if (st->cell_cost && st->cell_order) order_kernel<<<1, 1024, 0, s>>>(st->cell_cost, st->n_cells, st->cell_order);
     collide_kernel<Real><<<grid, threads, smem, s>>>(a);
     e = cudaGetLastError();
@@ -1891,6 +1896,7 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
     a.slabs = D.scratch + kStaticControl;
     a.slab_bytes = (avail / size_t(grid)) & ~size_t(255);
     a.smem_bytes = smem;
+    a.warp_level = sizeof(Real) == 8 ? kWarpLevel64 : kWarpLevel32;
     collide_kernel<Real><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? TRMC_OK : TRMC_ERR_CUDA;
 }
