@@ -77,6 +77,7 @@ trmc_status trmc_destroy(trmc_ctx *ctx)
     if (!ctx) return TRMC_ERR_ARG;
     if (ctx->workspace) cudaFree(ctx->workspace);
     if (ctx->tr_counts) cudaFree(ctx->tr_counts);
+    if (ctx->tr_dom) cudaFree(ctx->tr_dom);
     delete ctx;
     return TRMC_OK;
 }

@@ -22,7 +22,8 @@ struct trmc_ctx {
     size_t slabs_bytes = 0;
     // transport scratch, grown on demand
     int64_t *tr_counts = nullptr;     // [3 * cells] moves -1/0/+1 per old cell
-    int64_t *tr_scan = nullptr;       // [cells + 1]
+    void *tr_dom = nullptr;           // per-domain mover set-up (transport), [tr_ndom]
+    int tr_ndom = 0;
     int tr_cells = 0;
     // collide launch shape (trmc_set_collide_launch)
     int collide_threads = 128;

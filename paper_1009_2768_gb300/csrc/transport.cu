@@ -128,21 +128,6 @@ __device__ __forceinline__ int interior_cells(const trmc_domain &D)
     return D.bc == TRMC_BC_RESERVOIR ? D.n_cells - 2 : D.n_cells;
 }
 
-// Domain of cell c (first valid match); malformed domains are ignored and
-// reported, so their cells keep their particles and no write leaves the state.
-__device__ __forceinline__ CellDom find_domain(const trmc_domain *doms, int nd, int c, int nc_total, int *status)
-{
-    for (int d = 0; d < nd; ++d) {
-        const trmc_domain D = doms[d];
-        if (!domain_ok(D, nc_total)) {
-            if (atomicCAS(status, 0, TRMC_ERR_ARG) == 0) status[1] = d;
-            continue;
-        }
-        if (c >= D.cell_begin && c < D.cell_begin + D.n_cells) return CellDom{d, D.cell_begin};
-    }
-    return CellDom{-1, 0};
-}
-
 template <typename Real>
 __device__ __forceinline__ typename MoverT<Real>::type make_mover(const trmc_domain &D, double dt);
 template <>
@@ -165,16 +150,38 @@ __device__ __forceinline__ Mover32 make_mover<float>(const trmc_domain &D, doubl
     return m;
 }
 
-// Kernel 0: CFL time step per domain from the per-cell max |v|^2.
+// A domain's cells and mover, set up once per transport call by kernel 0, so
+// that the per-cell kernels find their domain among a few integers and need
+// no FP64 division (GB300: 2 FP64 lanes per SM and clock, ~400 cycles each).
+struct DomMove {
+    Mover64 m64;
+    Mover32 m32;
+    int first, n_cells, ok;
+};
+
+// Kernel 0: per domain, the CFL time step from the per-cell max |v|^2 (cfl > 0;
+// otherwise dt holds the caller's steps) and the domain's mover.
 __global__ void cfl_kernel(const trmc_domain *doms, int nd, int nc_total, const double *cell_vmax2, double cfl,
-                           double *dt, trmc_cell_param *cell_param)
+                           double *dt, trmc_cell_param *cell_param, DomMove *dm, int *status)
 {
     __shared__ double red[kRedScratch];
     const int d = blockIdx.x;
     if (d >= nd) return;
     const trmc_domain D = doms[d];
     if (!domain_ok(D, nc_total)) {
-        if (threadIdx.x == 0) dt[d] = 0.0;
+        if (threadIdx.x == 0) {
+            if (cfl > 0.0) dt[d] = 0.0;
+            dm[d].ok = 0; dm[d].first = D.cell_begin; dm[d].n_cells = D.n_cells;
+            if (atomicCAS(status, 0, TRMC_ERR_ARG) == 0) status[1] = d;
+        }
+        return;
+    }
+    if (cfl <= 0.0) {
+        if (threadIdx.x == 0) {
+            const double h = dt[d];
+            dm[d].m64 = make_mover<double>(D, h); dm[d].m32 = make_mover<float>(D, h);
+            dm[d].first = D.cell_begin; dm[d].n_cells = D.n_cells; dm[d].ok = 1;
+        }
         return;
     }
     __shared__ double sh_h;
@@ -189,6 +196,8 @@ __global__ void cfl_kernel(const trmc_domain *doms, int nd, int nc_total, const 
         const double h = (vm > 0.0) ? __ddiv_rn(__dmul_rn(cfl, dx), __dsqrt_rn(vm)) : 0.0;
         dt[d] = h;
         sh_h = h;
+        dm[d].m64 = make_mover<double>(D, h); dm[d].m32 = make_mover<float>(D, h);
+        dm[d].first = D.cell_begin; dm[d].n_cells = D.n_cells; dm[d].ok = 1;
     }
     __syncthreads();
     const double h = sh_h;
@@ -213,34 +222,43 @@ __device__ __forceinline__ int64_t refill_count(const trmc_domain &D, int c, con
     return int64_t(fl) + ((u01(w.w[0]) < __dsub_rn(want, fl)) ? 1 : 0);
 }
 
+// Domain of cell c among the set-up records (first valid match), -1 if none.
+__device__ __forceinline__ int find_dom(const DomMove *dm, int nd, int c)
+{
+    for (int d = 0; d < nd; ++d)
+        if (dm[d].ok && c >= dm[d].first && c < dm[d].first + dm[d].n_cells) return d;
+    return -1;
+}
+template <typename Real> __device__ __forceinline__ typename MoverT<Real>::type mover_of(const DomMove &m);
+template <> __device__ __forceinline__ Mover64 mover_of<double>(const DomMove &m) { return m.m64; }
+template <> __device__ __forceinline__ Mover32 mover_of<float>(const DomMove &m) { return m.m32; }
+
 template <typename Real>
 __global__ void __launch_bounds__(kTT) count_kernel(const Real *x, const Real *vx, const int64_t *cs,
-                                                    const trmc_domain *doms, int nd, int nc_total, const double *dt,
+                                                    const trmc_domain *doms, const DomMove *dm, int nd,
                                                     int64_t *counts, int *status, const uint64_t *cell_key,
                                                     uint32_t problem_id, uint64_t seed, uint64_t step,
                                                     const uint64_t *step_dev, double *cell_vmax2)
 {
-    __shared__ CellDom sd;
+    __shared__ int sdom;
     __shared__ unsigned long long tot[3];
-    __shared__ typename MoverT<Real>::type smv;    // set up once per CTA (FP64 divisions: 2 lanes/clk/SM)
     const int c = blockIdx.x;
     if (threadIdx.x == 0) {
-        sd = find_domain(doms, nd, c, nc_total, status);
+        sdom = find_dom(dm, nd, c);
         tot[0] = tot[1] = tot[2] = 0;
-        if (sd.d >= 0) smv = make_mover<Real>(doms[sd.d], dt[sd.d]);
     }
     __syncthreads();
+    const int dd = sdom;
     const int64_t b = cs[c], e = cs[c + 1];
     unsigned long long n3[3] = {0, 0, 0};
-    if (sd.d < 0) {
+    if (dd < 0) {
         n3[1] = (unsigned long long)(e - b);
         if (threadIdx.x == 0) { counts[3 * c] = 0; counts[3 * c + 1] = e - b; counts[3 * c + 2] = 0; }
         return;
     }
-    const trmc_domain D = doms[sd.d];
-    const auto mv = smv;
-    const int local = c - sd.first;
-    const bool ghost = D.bc == TRMC_BC_RESERVOIR && (local == 0 || local == D.n_cells - 1);
+    const auto mv = mover_of<Real>(dm[dd]);
+    const int local = c - dm[dd].first;
+    const bool ghost = mv.res && (local == 0 || local == dm[dd].n_cells - 1);
     bool bad = false;
     constexpr int U = 4;                            // loads issued together
     for (int64_t i0 = b + threadIdx.x; i0 < e; i0 += U * blockDim.x) {
@@ -261,7 +279,7 @@ __global__ void __launch_bounds__(kTT) count_kernel(const Real *x, const Real *v
         }
     }
     if (ghost && threadIdx.x == 0) {                // the refill takes the "stay" slot
-        n3[1] = (unsigned long long)refill_count(D, c, cell_key, problem_id, seed, step_dev ? *step_dev : step);
+        n3[1] = (unsigned long long)refill_count(doms[dd], c, cell_key, problem_id, seed, step_dev ? *step_dev : step);
         if (cell_vmax2) cell_vmax2[c] = 0.0;        // the refill kernel takes the maximum over its CTAs
     }
     if (bad) { if (atomicCAS(status, 0, TRMC_ERR_STATE) == 0) status[1] = c; }
@@ -374,8 +392,8 @@ __global__ void __launch_bounds__(kTT) refill_kernel(const trmc_domain *doms, in
 // Kernel 3: stable scatter of one old cell into the new order.
 template <typename Real>
 __global__ void __launch_bounds__(kTT) scatter_kernel(const Real *x, const Real *vx, const Real *vy, const Real *vz,
-                                                      const int64_t *cs, const trmc_domain *doms, int nd,
-                                                      const double *dt, const int64_t *counts,
+                                                      const int64_t *cs, const DomMove *dm, int nd,
+                                                      const int64_t *counts,
                                                       const int64_t *new_start, int nc_total,
                                                       Real *xo, Real *vxo, Real *vyo, Real *vzo, int *status,
                                                       int64_t capacity)
@@ -387,8 +405,9 @@ __global__ void __launch_bounds__(kTT) scatter_kernel(const Real *x, const Real 
     const int c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) {
-        sd = find_domain(doms, nd, c, nc_total, status);
-        if (sd.d >= 0) smv = make_mover<Real>(doms[sd.d], dt[sd.d]);
+        const int d = find_dom(dm, nd, c);
+        sd = CellDom{d, d >= 0 ? dm[d].first : 0};
+        if (d >= 0) smv = mover_of<Real>(dm[d]);
         // where this cell's movers land in the new order (stable: particles from
         // the left neighbour first, then stayers, then those from the right)
         dest[2] = (c + 1 < nc_total) ? new_start[c + 1] : 0;                        // going right
@@ -458,15 +477,22 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_domain *doms, int
         if (e != cudaSuccess) return set_error(ctx, TRMC_ERR_NOMEM, "transport scratch allocation failed");
         ctx->tr_cells = nc;
     }
-    if (cfl > 0.0) {
-        cfl_kernel<<<nd, 512, 0, s>>>(doms, nd, nc, st->cell_vmax2, cfl, dt, st->cell_param);
+    if (ctx->tr_ndom < nd) {
+        if (ctx->tr_dom) cudaFree(ctx->tr_dom);
+        ctx->tr_dom = nullptr;
+        ctx->tr_ndom = 0;
+        cudaError_t e = cudaMalloc(&ctx->tr_dom, sizeof(DomMove) * size_t(nd));
+        if (e != cudaSuccess) return set_error(ctx, TRMC_ERR_NOMEM, "transport scratch allocation failed");
+        ctx->tr_ndom = nd;
     }
+    DomMove *dm = static_cast<DomMove *>(ctx->tr_dom);
+    cfl_kernel<<<nd, 512, 0, s>>>(doms, nd, nc, st->cell_vmax2, cfl, dt, st->cell_param, dm, ctx->status);
     const Real *x = static_cast<const Real *>(st->x), *vx = static_cast<const Real *>(st->vx);
-    count_kernel<Real><<<nc, kTT, 0, s>>>(x, vx, st->cell_start, doms, nd, nc, dt, ctx->tr_counts, ctx->status,
+    count_kernel<Real><<<nc, kTT, 0, s>>>(x, vx, st->cell_start, doms, dm, nd, ctx->tr_counts, ctx->status,
                                           st->cell_key, st->problem_id, ctx->seed, step, st->step_dev, st->cell_vmax2);
     scan_kernel<<<1, 1024, 0, s>>>(ctx->tr_counts, nc, st->cell_start_alt, st->capacity, ctx->status);
     scatter_kernel<Real><<<nc, kTT, 0, s>>>(x, vx, static_cast<const Real *>(st->vy), static_cast<const Real *>(st->vz),
-                                            st->cell_start, doms, nd, dt, ctx->tr_counts, st->cell_start_alt, nc,
+                                            st->cell_start, dm, nd, ctx->tr_counts, st->cell_start_alt, nc,
                                             static_cast<Real *>(st->x_alt), static_cast<Real *>(st->vx_alt),
                                             static_cast<Real *>(st->vy_alt), static_cast<Real *>(st->vz_alt),
                                             ctx->status, st->capacity);
