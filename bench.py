@@ -52,12 +52,12 @@ METRIC = "particle-steps/s"
 # of the same command, keyed by the hash of csrc/collide.cu it was taken on; reported as
 # null once the kernel source differs.  See profiles/.
 NCU_TRAFFIC = {
-    "shock": {"collide_sha": "3fbd60759f49d794", "launch": (128, 4), "bytes": 26592768 + 334080,
-              "fp64_pipe_active_pct": 54.4},
-    "stationary": {"collide_sha": "3fbd60759f49d794", "launch": (256, 2), "bytes": 123477760 + 67439104,
-                   "fp64_pipe_active_pct": 10.3},
-    "batched": {"collide_sha": "3fbd60759f49d794", "launch": (256, 2), "bytes": 86460672 + 73230848,
-                "fp64_pipe_active_pct": 8.2},
+    "shock": {"collide_sha": "7322bb0d7b0f77a3", "launch": (128, 4), "bytes": 26228736 + 327936,
+              "fp64_pipe_active_pct": 52.2},
+    "stationary": {"collide_sha": "7322bb0d7b0f77a3", "launch": (256, 2), "bytes": 123490816 + 67298560,
+                   "fp64_pipe_active_pct": 10.2},
+    "batched": {"collide_sha": "7322bb0d7b0f77a3", "launch": (256, 2), "bytes": 87849472 + 76906496,
+                "fp64_pipe_active_pct": 8.8},
 }
 
 # Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
