@@ -440,6 +440,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                              int (&cnt)[3])
 {
     const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
+    // FP64: the input-independent part of every level's collisions (draw,
+    // threshold, direction) is computed up front, not only the deep levels'
+    constexpr bool kRecordAll = sizeof(Real) == 8;
     Real *gx = static_cast<Real *>(a.vx), *gy = static_cast<Real *>(a.vy), *gz = static_cast<Real *>(a.vz);
     const int64_t base = a.cell_start[cell];
     const int n = int(a.cell_start[cell + 1] - base);
@@ -733,8 +736,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             if (lane == 0) { sh.D[64] = 0; sh.D[65] = 0; sh.C[64] = c64; sh.C[65] = 0; }
             // deep levels (at most warp_level collisions) in ascending order with
             // the offsets of their collisions in the per-collision records
-            const bool wA = inA && cA > 0 && cA <= a.warp_level, wB = inB && cB > 0 && cB <= a.warp_level;
-            const bool w64 = m >= 64 && c64 > 0 && c64 <= a.warp_level;
+            const bool wA = inA && cA > 0 && (kRecordAll || cA <= a.warp_level);
+            const bool wB = inB && cB > 0 && (kRecordAll || cB <= a.warp_level);
+            const bool w64 = m >= 64 && c64 > 0 && (kRecordAll || c64 <= a.warp_level);
             const unsigned bwA = __ballot_sync(FULL, wA), bwB = __ballot_sync(FULL, wB);
             const unsigned ltm = (1u << lane) - 1u;
             const int iA = __popc(bwA & ltm), iB = __popc(bwA) + __popc(bwB & ltm);
@@ -1333,6 +1337,12 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 __syncwarp();
             } else {
                 if (warp_only) { __syncthreads(); warp_only = false; }
+                if (kRecordAll && nWL > 0) {
+                    const int base = sh.WB[jw++];
+                    for (int c = tid; c < Cn; c += bs) collide_pre(base + c, lv);
+                    __syncthreads();
+                    continue;
+                }
                 if (warp == 0) level_setup(lv);
                 __syncthreads();
                 Perm pk;
