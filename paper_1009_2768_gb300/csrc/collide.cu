@@ -46,6 +46,7 @@ constexpr int NLEV = kMC + 2;
 // Measured on GB300: 32 for FP64 (its collisions are slow; spread them over the
 // CTA), 128 for FP32.
 constexpr int kWarpLevel64 = 32, kWarpLevel32 = 128;
+constexpr int kRecordPerThread = 4;
 constexpr int kPreLabels = 16;     // labels per level drawn ahead of the plan, at least
 constexpr int kMaxPre = 64;        // and at most
 
@@ -440,12 +441,14 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                              int (&cnt)[3])
 {
     const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
-    // FP64: the input-independent part of every level's collisions (draw,
-    // threshold, direction) is computed up front, not only the deep levels'
-    constexpr bool kRecordAll = sizeof(Real) == 8;
     Real *gx = static_cast<Real *>(a.vx), *gy = static_cast<Real *>(a.vy), *gz = static_cast<Real *>(a.vz);
     const int64_t base = a.cell_start[cell];
     const int n = int(a.cell_start[cell + 1] - base);
+    // the input-independent part of a level's collisions (draw, threshold,
+    // direction) is computed up front for every level of at most rec_max
+    // collisions, a few per thread: there it takes latency off the level's
+    // wave; bigger levels keep every thread busy and compute it in place
+    const int rec_max = max(a.warp_level, kRecordPerThread * bs);
     const trmc_collide_params &prm = a.prm;
 
     if (tid == 0) {
@@ -736,9 +739,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             if (lane == 0) { sh.D[64] = 0; sh.D[65] = 0; sh.C[64] = c64; sh.C[65] = 0; }
             // deep levels (at most warp_level collisions) in ascending order with
             // the offsets of their collisions in the per-collision records
-            const bool wA = inA && cA > 0 && (kRecordAll || cA <= a.warp_level);
-            const bool wB = inB && cB > 0 && (kRecordAll || cB <= a.warp_level);
-            const bool w64 = m >= 64 && c64 > 0 && (kRecordAll || c64 <= a.warp_level);
+            const bool wA = inA && cA > 0 && cA <= rec_max;
+            const bool wB = inB && cB > 0 && cB <= rec_max;
+            const bool w64 = m >= 64 && c64 > 0 && c64 <= rec_max;
             const unsigned bwA = __ballot_sync(FULL, wA), bwB = __ballot_sync(FULL, wB);
             const unsigned ltm = (1u << lane) - 1u;
             const int iA = __popc(bwA & ltm), iB = __popc(bwA) + __popc(bwB & ltm);
@@ -1195,11 +1198,12 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         };
         // 5a. The deep levels run one after the other in warp 0, mostly with a
         //     few collisions each, so their latency is the cell's critical
-        //     path.  Everything of their collisions that does not depend on
-        //     the inputs -- label, input and output locations, the draw, the
-        //     acceptance threshold and the scattering direction -- is computed
-        //     first by the whole CTA; a deep level then only loads its inputs,
-        //     collides and stores.
+        //     path; the levels of up to a few collisions per thread are
+        //     latency-bound too.  Everything of these levels' collisions that
+        //     does not depend on the inputs -- label, input and output
+        //     locations, the draw, the acceptance threshold and the scattering
+        //     direction -- is computed first by the whole CTA; such a level
+        //     then only loads its inputs, collides and stores.
         const int nWL = sh.nWL;
         if (nWL > 0) {
             const int nw = bs >> 5;
@@ -1337,7 +1341,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 __syncwarp();
             } else {
                 if (warp_only) { __syncthreads(); warp_only = false; }
-                if (kRecordAll && nWL > 0) {
+                if (Cn <= rec_max && nWL > 0) {
                     const int base = sh.WB[jw++];
                     for (int c = tid; c < Cn; c += bs) collide_pre(base + c, lv);
                     __syncthreads();
