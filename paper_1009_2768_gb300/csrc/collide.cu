@@ -1765,7 +1765,7 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     // cells per SM overlap one cell's serial phases with the others' work;
     // the shared-memory budget of an SM is split evenly between them
     const int threads = ctx->collide_threads, per_sm_target = ctx->collide_ctas_per_sm;
-    const int budget = ctx->smem_optin >= 200 * 1024 ? 220 * 1024 : int(ctx->smem_optin);
+    const int budget = ctx->smem_optin >= 200 * 1024 ? 226 * 1024 : int(ctx->smem_optin);
     int smem = budget / per_sm_target - int(sizeof(Sh<Real>)) - 1024;
     if (smem > int(ctx->smem_optin) - int(sizeof(Sh<Real>))) smem = int(ctx->smem_optin) - int(sizeof(Sh<Real>));
     cudaError_t e = allow_max_smem<Real>(ctx->device, int(ctx->smem_optin));
@@ -1877,7 +1877,7 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
         D.scratch = static_cast<char *>(p);
         D.ready = true;
     }
-    const int smem = D.smem_optin >= 200 * 1024 ? (220 * 1024) / per_sm_target - int(sizeof(Sh<Real>)) - 1024
+    const int smem = D.smem_optin >= 200 * 1024 ? (226 * 1024) / per_sm_target - int(sizeof(Sh<Real>)) - 1024
                                                 : D.smem_optin / 2 - int(sizeof(Sh<Real>)) - 1024;
     if (allow_max_smem<Real>(dev, D.smem_optin) != cudaSuccess) return TRMC_ERR_CUDA;
     const size_t avail = size_t(TRMC_STATIC_SCRATCH_BYTES) - kStaticControl;
