@@ -52,12 +52,12 @@ METRIC = "particle-steps/s"
 # of the same command, keyed by the hash of csrc/collide.cu it was taken on; reported as
 # null once the kernel source differs.  See profiles/.
 NCU_TRAFFIC = {
-    "shock": {"collide_sha": "7322bb0d7b0f77a3", "launch": (128, 4), "bytes": 26228736 + 327936,
-              "fp64_pipe_active_pct": 52.2},
-    "stationary": {"collide_sha": "7322bb0d7b0f77a3", "launch": (256, 2), "bytes": 123490816 + 67298560,
-                   "fp64_pipe_active_pct": 10.2},
-    "batched": {"collide_sha": "7322bb0d7b0f77a3", "launch": (256, 2), "bytes": 87849472 + 76906496,
-                "fp64_pipe_active_pct": 8.8},
+    "shock": {"collide_sha": "b9eed3844bad6289", "launch": (128, 3), "bytes": 24367360 + 363520,
+              "fp64_pipe_active_pct": 49.2},
+    "stationary": {"collide_sha": "b9eed3844bad6289", "launch": (256, 2), "bytes": 123542016 + 75760896,
+                   "fp64_pipe_active_pct": 10.6},
+    "batched": {"collide_sha": "b9eed3844bad6289", "launch": (256, 2), "bytes": 89490688 + 93126912,
+                "fp64_pipe_active_pct": 8.7},
 }
 
 # Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
