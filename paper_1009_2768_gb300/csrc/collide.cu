@@ -226,20 +226,28 @@ __device__ __forceinline__ double exact_small(uint64_t v)       // v < 2^52, exa
 // u = k 2^-53, 0 <= k < 2^53: the top 8 bits of k pick a = 2 pi i / 256, the
 // other 45 give t = 2 pi (u - i / 256) in [0, 2 pi / 256); the addition
 // formulas combine sin a, cos a with the Taylor series of sin t and cos t - 1
-// (the first omitted terms, t^9 / 9! and t^10 / 10!, are below 1e-20).
+// (the first omitted terms, t^9 / 9! and t^10 / 10!, are below 1e-20).  All of
+// it runs in 64-bit fixed point on the integer units (t, sin t and 1 - cos t
+// scaled by 2^64, the table by 2^62; every product keeps its high 64 bits), so
+// the only FP64 instructions are the two conversions at the end.  Absolute
+// error below 2^-59 before the conversions, which round to nearest.
 __device__ __forceinline__ void sincos_2pi(uint64_t k, double &s, double &c)
 {
     const int i = int(k >> 45);
-    const double fd = exact_small(k & ((1ull << 45) - 1ull));
-    const double t = fma(fd, kTwoPi53[0], fd * kTwoPi53[1]);
-    const double t2 = t * t;
-    const double ps = fma(t2, fma(t2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0);
-    const double sn = fma(t * t2, ps, t);
-    const double pc = fma(t2, fma(t2, fma(t2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5);
-    const double cm1 = t2 * pc;
-    const double S = kSinCos256[i][0], C = kSinCos256[i][1];
-    s = S + fma(S, cm1, C * sn);
-    c = C + fma(C, cm1, -(S * sn));
+    const uint64_t T = __umul64hi((k & ((1ull << 45) - 1ull)) << 16, kQ2Pi59);   // t 2^64
+    const uint64_t T2 = __umul64hi(T, T);                                          // t^2 2^64
+    // sin t = t - t^3 (1/6 - t^2 (1/120 - t^2 / 5040))
+    uint64_t p = kQInv120 - __umul64hi(T2, kQInv5040);
+    p = kQInv6 - __umul64hi(T2, p);
+    const long long SN = (long long)(T - __umul64hi(__umul64hi(T2, T), p));
+    // 1 - cos t = t^2 (1/2 - t^2 (1/24 - t^2 (1/720 - t^2 / 40320)))
+    uint64_t q = kQInv720 - __umul64hi(T2, kQInv40320);
+    q = kQInv24 - __umul64hi(T2, q);
+    q = (1ull << 63) - __umul64hi(T2, q);
+    const long long CM = (long long)__umul64hi(T2, q);
+    const long long S = kSinCos256Q62[i][0], C = kSinCos256Q62[i][1];
+    s = double(S - __mul64hi(S, CM) + __mul64hi(C, SN)) * 0x1p-62;
+    c = double(C - __mul64hi(C, CM) - __mul64hi(S, SN)) * 0x1p-62;
 }
 
 // ln u, u = k 2^-53, 1 <= k <= 2^53: u = 2^(e - 52) (m / 2) with m in [1, 2),

@@ -8,6 +8,9 @@ missing; the file is committed, so the build normally only reads it.
   kLnT128[j]    = { ln((1 + j/128) / 2), 2^-52 / (1 + j/128) }, j = 0..127
   kTwoPi53      = { hi, lo }: 2 pi 2^-53 as an unevaluated sum of doubles
   kLn2          = { hi, lo }: ln 2 as an unevaluated sum of doubles
+  kSinCos256Q62[i] = the same sines and cosines in fixed point, round(x 2^62)
+  kQ2Pi59       = round(2 pi 2^59)
+  kQInvN        = round(2^64 / N) for N = 6, 24, 120, 720, 5040, 40320
 """
 import os
 from decimal import Decimal, getcontext
@@ -101,6 +104,16 @@ def main():
     lines.append(f"static __device__ const double kTwoPi53[2] = {{{lit(h)}, {lit(l)}}};")
     h, l = split(ln1p(Decimal(1)))
     lines.append(f"static __device__ const double kLn2[2] = {{{lit(h)}, {lit(l)}}};")
+    lines.append("static __device__ const long long kSinCos256Q62[256][2] = {")
+    for i in range(256):
+        sn, cs = sincos(2 * PI * i / 256)
+        q = [0 if abs(x) < Decimal(10) ** -40 else int((x * 2 ** 62).to_integral_value()) for x in (sn, cs)]
+        lines.append(f"    {{{q[0]}ll, {q[1]}ll}},")
+    lines.append("};")
+    lines.append(f"static __device__ const unsigned long long kQ2Pi59 = {int((2 * PI * 2 ** 59).to_integral_value())}ull;")
+    for n in (6, 24, 120, 720, 5040, 40320):
+        lines.append(f"static __device__ const unsigned long long kQInv{n} = "
+                     f"{int((Decimal(2) ** 64 / n).to_integral_value())}ull;")
     text = "\n".join(lines) + "\n"
     with open(OUT, "w") as f:
         f.write(text)

@@ -1,8 +1,9 @@
 """The library's FP64 evaluations of sin/cos(2 pi u) and ln u for the
-53-bit uniforms of its draws (table plus series) agree with CUDA's sincospi
-and log: ln u within 2 ulp; sin and cos within 2 ulp away from their zeros
-and within 2 ulp of 1 in absolute terms near them; on random words and on the
-edges of the table intervals, of the near-one branch and of the range."""
+53-bit uniforms of its draws (table plus series; the angles in 64-bit fixed
+point on the integer units) agree with CUDA's sincospi and log: ln u within
+2 ulp; sin and cos within 2 ulp away from their zeros and within 2 ulp of 1
+in absolute terms near them; on random words and on the edges of the table
+intervals, of the near-one branch and of the range."""
 import numpy as np
 import pytest
 
