@@ -255,11 +255,14 @@ trmc_status trmc_collide_static(trmc_state *state, const trmc_collide_params *pa
  * The paper has no counterpart: a check of the library's own evaluations of
  * sin/cos(2 pi u) and ln u for the 53-bit uniforms of the draws (table plus
  * series, used by the collisions and the Maxwellian resampling of FP64
- * contexts) against CUDA's sincospi and log.  For each 64-bit word w of
- * words_dev[n] (device), out_dev[n][6] (device) receives: sin, cos of
- * 2 pi u (library), the same from sincospi, ln u' (library) and log(u') from
- * CUDA, with u = (w >> 11) 2^-53 and u' = ((w >> 11) + 1) 2^-53.  Asynchronous
- * on the stream; TRMC_ERR_ARG for a negative n or NULL arrays. */
+ * contexts) and of its square root, against CUDA's sincospi, log and sqrt.
+ * For each 64-bit word w of words_dev[n] (device), out_dev[n][8] (device)
+ * receives: sin, cos of 2 pi u (library), the same from sincospi, ln u'
+ * (library) and log(u') from CUDA, sqrt(x) (library) and sqrt(x) from CUDA,
+ * with u = (w >> 11) 2^-53, u' = ((w >> 11) + 1) 2^-53 and x the double with
+ * the low 52 bits of w as fraction and 1 + (w >> 53) mod 2045 as biased
+ * exponent.  Asynchronous on the stream; TRMC_ERR_ARG for a negative n or NULL
+ * arrays. */
 trmc_status trmc_fp64_selftest(const uint64_t *words_dev, int32_t n, double *out_dev, void *stream);
 
 /* ---- self-test of the split's integer Iround --------------------------------

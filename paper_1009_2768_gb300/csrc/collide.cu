@@ -250,6 +250,35 @@ __device__ __forceinline__ void sincos_2pi(uint64_t k, double &s, double &c)
     c = double(C - __mul64hi(C, CM) - __mul64hi(S, SN)) * 0x1p-62;
 }
 
+// Square root of a double x >= 0 on the integer units: x = m 2^E with E even
+// and m < 2^54, z = m 2^-54 in [1/4, 1); 1/sqrt(z) is seeded by the float unit's
+// reciprocal square root (about 22 bits) and refined by two Newton steps
+// y (3 - z y^2) / 2 in 64-bit fixed point; sqrt(z) = z y is rounded to 53
+// bits and given the exponent 26 + E / 2.  Within 0.51 ulp (faithful; checked
+// against sqrt by trmc_fp64_selftest).  Zero, subnormal, infinite and NaN
+// inputs go to sqrt.
+__device__ __forceinline__ double sqrt_pos(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ef = int(b >> 52);                     // sign bit clear for x >= 0
+    if (ef == 0 || ef >= 0x7FF) return sqrt(x);
+    int E = ef - 1075;
+    unsigned long long m = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+    if (E & 1) { m <<= 1; E -= 1; }
+    const unsigned long long X = m << 10;           // z 2^64, in [2^62, 2^64)
+    const float y0 = rsqrtf(__uint2float_rn(unsigned(X >> 40)) * 0x1p-24f);
+    const unsigned yb = __float_as_uint(y0);         // y0 in (1, 2]
+    unsigned long long Y = (unsigned long long)((yb & 0x7FFFFFu) | 0x800000u) << (39 + int(yb >> 23) - 127);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {                // Y = y 2^62
+        const unsigned long long zy2 = __umul64hi(X, __umul64hi(Y, Y));        // z y^2 2^60
+        Y = __umul64hi(Y, ((3ull << 60) - zy2) << 2) << 1;
+    }
+    const unsigned long long S = __umul64hi(X, Y);   // sqrt(z) 2^62
+    const unsigned long long bits = ((unsigned long long)(1023 + 26 + (E >> 1) - 1) << 52) + ((S + 256ull) >> 9);
+    return __longlong_as_double((long long)bits);
+}
+
 // ln u, u = k 2^-53, 1 <= k <= 2^53: u = 2^(e - 52) (m / 2) with m in [1, 2),
 // m = T_j (1 + t) with T_j = 1 + j / 128 from the top 7 fraction bits and
 // t in [0, 1/128); ln u = (e - 52) ln 2 + ln(T_j / 2) + ln(1 + t), all terms
@@ -277,7 +306,7 @@ __device__ __forceinline__ double log_u53(uint64_t k)
 
 template <typename Real> struct Math;
 template <> struct Math<double> {
-    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt_pos(x); }
     static __device__ __forceinline__ double pow_(double x, double a) { return pow(x, a); }
     static __device__ __forceinline__ double uni(uint64_t w) { return u01(w); }
     // sin / cos of 2 pi u: sincospi reduces the argument exactly, so it is
@@ -1964,10 +1993,14 @@ __global__ void fp64_selftest_kernel(const uint64_t *k, int n, double *out)
         double s, c, s_ref, c_ref;
         sincos_2pi(w >> 11, s, c);
         sincospi(2.0 * u01(w), &s_ref, &c_ref);
-        double *o = out + 6 * size_t(i);
+        double *o = out + 8 * size_t(i);
         o[0] = s; o[1] = c; o[2] = s_ref; o[3] = c_ref;
         o[4] = log_u53((w >> 11) + 1);
         o[5] = log(u01_open(w));
+        const double x = __longlong_as_double(
+            (long long)((w & ((1ull << 52) - 1ull)) | ((1ull + (w >> 53) % 2045ull) << 52)));
+        o[6] = sqrt_pos(x);
+        o[7] = sqrt(x);
     }
 }
 }  // namespace

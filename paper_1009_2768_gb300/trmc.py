@@ -192,7 +192,7 @@ def trmc_collide_static(state, params, precision, seed, step, max_cell_particles
 
 
 def trmc_fp64_selftest(words, out, stream=None):
-    """words: uint64 (as int64) device tensor [n]; out: float64 device tensor [n, 6]."""
+    """words: uint64 (as int64) device tensor [n]; out: float64 device tensor [n, 8]."""
     code = load().trmc_fp64_selftest(_ptr(words), words.numel(), _ptr(out), _stream(stream))
     if code != OK:
         raise TrmcError(code, "trmc_fp64_selftest failed")
