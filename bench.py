@@ -52,12 +52,12 @@ METRIC = "particle-steps/s"
 # of the same command, keyed by the hash of csrc/collide.cu it was taken on; reported as
 # null once the kernel source differs.  See profiles/.
 NCU_TRAFFIC = {
-    "shock": {"collide_sha": "b9eed3844bad6289", "launch": (128, 3), "bytes": 24367360 + 363520,
-              "fp64_pipe_active_pct": 49.2},
-    "stationary": {"collide_sha": "b9eed3844bad6289", "launch": (256, 2), "bytes": 123542016 + 75760896,
-                   "fp64_pipe_active_pct": 10.6},
-    "batched": {"collide_sha": "b9eed3844bad6289", "launch": (256, 2), "bytes": 89490688 + 93126912,
-                "fp64_pipe_active_pct": 8.7},
+    "shock": {"collide_sha": "c5d8d84dfb137b1a", "launch": (128, 3), "bytes": 24382208 + 482048,
+              "fp64_pipe_active_pct": 41.7},
+    "stationary": {"collide_sha": "c5d8d84dfb137b1a", "launch": (256, 2), "bytes": 123458048 + 75530496,
+                   "fp64_pipe_active_pct": 10.7},
+    "batched": {"collide_sha": "c5d8d84dfb137b1a", "launch": (256, 2), "bytes": 90179072 + 93251072,
+                "fp64_pipe_active_pct": 8.8},
 }
 
 # Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
