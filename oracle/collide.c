@@ -597,6 +597,12 @@ int orc_collide(double *vx, double *vy, double *vz, const int64_t *cell_start,
     if (prm->m_cap < 1 || prm->m_cap > MC) return 1;
     if (prm->trunc == ORC_TRUNC_WB &&
         (prm->wb_length < ORC_LEN_K || prm->wb_length > ORC_LEN_MEAN || prm->m_fixed < 0)) return 1;
+    /* the method is defined for finite velocities whose energy sums are finite */
+    for (int32_t c = 0; c < n_cells; ++c) {
+        double e = 0.0;
+        for (int64_t i = cell_start[c]; i < cell_start[c + 1]; ++i) e += vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
+        if (!isfinite(e)) return 2;
+    }
     if (n_threads < 1) n_threads = 1;
     job_t *jobs = (job_t *)malloc(sizeof(job_t) * (size_t)n_threads);
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);

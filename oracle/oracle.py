@@ -164,6 +164,8 @@ def collide(v, cell_start, prm, step, m_state=None, cell_param=None, cell_key=No
     vx, vy, vz = (np.ascontiguousarray(v[i]) for i in range(3))
     rc = lib().orc_collide(_p(vx), _p(vy), _p(vz), _p(cs), nc, _p(ck), problem_id, step,
                            _p(ms), C.byref(prm), _p(cp), _p(rep), threads)
+    if rc == 2:
+        raise ValueError("oracle collide: a cell's velocities or energy sum are not finite")
     if rc != 0:
         raise ValueError("oracle collide rejected its arguments")
     return np.stack([vx, vy, vz]), rep, ms
@@ -195,6 +197,8 @@ def transport(x, v, cell_start, domains, dt_dom, step=0, seed=0, problem_id=0, c
     cso = np.zeros(nc + 1, np.int64)
     n = lib().orc_transport(_p(x), _p(vx), _p(vy), _p(vz), _p(cs), nc, doms, len(doms), _p(dt), _p(ck), problem_id,
                             seed, step, _p(xo), _p(vxo), _p(vyo), _p(vzo), cap, _p(cso))
+    if n == -2:
+        raise ValueError("oracle transport: non-finite position, velocity or time step")
     if n < 0:
         raise ValueError("oracle transport: particle count exceeds capacity")
     return xo[:n], np.stack([vxo[:n], vyo[:n], vzo[:n]]), cso

@@ -49,6 +49,11 @@ int64_t orc_transport(double *x, double *vx, double *vy, double *vz,
                       int64_t *cell_start_out)
 {
     int64_t np = cell_start[n_cells_total];
+    /* positions and velocities must be finite: a cell index is taken from them */
+    for (int64_t i = 0; i < np; ++i)
+        if (!isfinite(x[i]) || !isfinite(vx[i]) || !isfinite(vy[i]) || !isfinite(vz[i])) return -2;
+    for (int32_t d = 0; d < n_dom; ++d)
+        if (!isfinite(dt_dom[d])) return -2;
     int64_t *key = (int64_t *)malloc(sizeof(int64_t) * (size_t)(np > 0 ? np : 1));   /* -1: removed */
     int64_t *refill = (int64_t *)calloc((size_t)(n_cells_total > 0 ? n_cells_total : 1), sizeof(int64_t));
     /* cells that belong to no domain keep their particles */

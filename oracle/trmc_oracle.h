@@ -90,6 +90,8 @@ int orc_collide_cell(double *vx, double *vy, double *vz, int64_t n,
 /* All cells of a state; cell c holds [cell_start[c], cell_start[c+1]).
  * cell_key (nullable) gives (problem << 32 | local cell) per cell, else
  * (problem_id, c).  cell_param (nullable) overrides eps/dt/rho_scale/alpha. */
+/* Returns 0, 1 for inconsistent parameters, 2 for a cell whose velocities or
+ * energy sum are not finite. */
 int orc_collide(double *vx, double *vy, double *vz, const int64_t *cell_start,
                 int32_t n_cells, const uint64_t *cell_key, uint64_t problem_id,
                 uint64_t step, int32_t *m_state, const orc_collide_params *prm,
@@ -106,7 +108,8 @@ typedef struct {
     double particle_mass;
 } orc_domain;
 
-/* Returns the new particle count, or -1 if it would exceed capacity. */
+/* Returns the new particle count, -1 if it would exceed capacity, or -2 for a
+ * non-finite position, velocity or time step. */
 int64_t orc_transport(double *x, double *vx, double *vy, double *vz,
                       int64_t *cell_start, int32_t n_cells_total,
                       const orc_domain *dom, int32_t n_dom, const double *dt_dom,
