@@ -101,8 +101,9 @@ struct Sh {
     int32_t *Mt, *St;
     Real *IBuf, *OBuf;
     double *ILBuf, *OLBuf;           // TRMC-WB: tree length of every consumer slot / output
-    // deep levels (at most warp_level collisions) in ascending order, the
-    // offset of their collisions in the per-collision records, and the records:
+    // the recorded levels (the deep ones and those of at most a few collisions
+    // per thread) in ascending order, the offset of their collisions in the
+    // per-collision records, and the records:
     // exclusive label prefix per level (triangular rows), input and output
     // locations, acceptance threshold xi*Sigma and scattering direction
     int32_t WL[NLEV], WB[NLEV + 1], nWL;
@@ -774,7 +775,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             if (lane == 0 && m >= 64) { sh.O[65] = Otot; sh.IB[65] = Dge1; }
             sh.D[jA] = dA; sh.D[jB] = dB; sh.C[jA] = cA; sh.C[jB] = cB;
             if (lane == 0) { sh.D[64] = 0; sh.D[65] = 0; sh.C[64] = c64; sh.C[65] = 0; }
-            // deep levels (at most warp_level collisions) in ascending order with
+            // recorded levels (at most rec_max collisions) in ascending order with
             // the offsets of their collisions in the per-collision records
             const bool wA = inA && cA > 0 && cA <= rec_max;
             const bool wB = inB && cB > 0 && cB <= rec_max;
@@ -834,8 +835,8 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                                                          4 * size_t(d0 + 1)));
                     if (!sh.ILBuf || !sh.OLBuf || !sh.ext) sh.skip = 1;
                 }
-                // records of the deep levels' collisions; without room for them
-                // the waves compute everything in place (same results)
+                // records of the recorded levels' collisions; without room for
+                // them the waves compute everything in place (same results)
                 int nwl = nWL;
                 if (W > 0) {
                     char *s0 = ps, *g0 = pg;
@@ -1355,7 +1356,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             }
         };
         bool warp_only = false;      // the last level ran in warp 0 alone
-        int jw = 0;                  // next deep level in WL
+        int jw = 0;                  // next recorded level in WL
         const int ntail = sh.ntail;
         const int lv_end = ntail > 0 ? sh.LB : m_eff;
         for (int lv = 1; lv <= lv_end; ++lv) {
