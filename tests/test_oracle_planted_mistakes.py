@@ -1,7 +1,8 @@
 """The pins are sharp enough to catch a plausible mistake: copies of the
 oracle's C source, each with one mistake planted (a dropped factor, a sign,
-a missing renormalisation, q and tau swapped, a skewed label law, a wall
-that forgets to reverse v_x), are built into their own libraries and run
+a missing renormalisation, q and tau swapped, a skewed label law, a biased
+rule for odd counts, lowering the depth where leaves can be borrowed, a
+wall that forgets to reverse v_x), are built into their own libraries and run
 through the pins of tests/test_oracle_*.py; every copy must fail at least
 one of them.  The oracle itself is untouched: the copies live in a
 temporary directory and the module is pointed back at the real library
@@ -15,6 +16,7 @@ import pytest
 from oracle import oracle as O
 from tests import test_oracle_euler_limit as E
 from tests import test_oracle_physics as P
+from tests import test_oracle_plan_law as PL
 from tests import test_oracle_transport_init as TI
 
 ORACLE_DIR = os.path.dirname(os.path.abspath(O.__file__))
@@ -33,6 +35,12 @@ MISTAKES = {
     "labels: k drawn from the lower half only":
         ("collide.c", "lab[c] = (int32_t)orc_below(w[c & 3], (uint32_t)n);",
          "lab[c] = (int32_t)orc_below(w[c & 3], (uint32_t)(n + 1) / 2);"),
+    "odd count: the surplus product always kept (always round up)":
+        ("collide.c", "if (pl->Nn[n] >= 1 && orc_u01(w[0]) < 0.5)", "if (0 && pl->Nn[n] >= 1 && orc_u01(w[0]) < 0.5)"),
+    "odd count: a quota particle always dropped when the level has one":
+        ("collide.c", "if (pl->Nn[n] >= 1 && orc_u01(w[0]) < 0.5)", "if (pl->Nn[n] >= 1)"),
+    "leaves: the depth lowered instead of borrowing from level 0":
+        ("collide.c", "if (deficit <= n0) {", "if (0) {"),
     "walls: the right wall keeps v_x":
         ("transport.c", "else if (xn > hi) { xn = 2.0 * hi - xn; vx[i] = -vx[i]; }",
          "else if (xn > hi) { xn = 2.0 * hi - xn; }"),
@@ -45,6 +53,9 @@ PINS = [
     ("conservation, Maxwell molecules, eps 1e-4", lambda: P.test_conservation(0.0, 1e-4, O.TRUNC_FIXED, 1)),
     ("level occupation", P.test_level_occupation_expectation),
     ("tree label law", P.test_tree_label_law),
+    ("plan law by enumeration, 6 particles, m = 3", lambda: PL.test_oracle_plan_follows_the_enumerated_law(6, 3, 0.7)),
+    ("plan law by enumeration, 4 particles, m = 3", lambda: PL.test_oracle_plan_follows_the_enumerated_law(4, 3, 1.6)),
+    ("outputs unbiased per level", lambda: PL.test_outputs_are_unbiased_per_level(0.7)),
     ("M4 step factor, m = 2", lambda: P.test_m4_step_factor_maxwell(2)),
     ("Euler limit of the shock tube", E.test_oracle_shock_tube_follows_the_euler_riemann_solution),
 ]
