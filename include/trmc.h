@@ -23,7 +23,9 @@
  *    TRMC_FP64 contexts and float in TRMC_FP32_MIXED contexts.
  *  - Results depend only on (seed, problem id, cell index within the problem,
  *    step, particle order within the cell), never on launch shape or on
- *    which other cells share the call.
+ *    which other cells share the call: every per-cell sum runs over the same
+ *    256 virtual lanes and 8 virtual warps, combined in a fixed tree, whatever
+ *    the CTA size, so even the rounding of the FP64 sums is the same.
  */
 #ifndef TRMC_H
 #define TRMC_H
@@ -237,9 +239,14 @@ trmc_status trmc_moments(trmc_ctx *ctx, const trmc_state *state, double *out_dev
  *  - max_cell_particles: the caller's bound on the largest cell.  The scratch
  *    is split into one overflow slab per CTA sized for such a cell; if not
  *    even one slab fits, the call returns TRMC_ERR_CAPACITY and launches
- *    nothing.  A cell that still does not fit is left unchanged and reported.
+ *    nothing.  A cell that still does not fit (larger than the bound) is left
+ *    unchanged and reported through status_dev as (TRMC_ERR_CAPACITY, cell).
+ *  - The parameters are checked exactly as trmc_collide checks them
+ *    (TRMC_ERR_ARG for the same invalid states and parameters).
  *  - status_dev (optional, device int[2]): receives device-detected errors
  *    (code, first cell), as trmc_check() would report them; the caller clears it.
+ *    Without it the call cannot report device-detected errors at all: they go
+ *    to the scratch's own status word, which the next call clears unread.
  *  - The first call on a device looks up the scratch's device address and
  *    sets the kernel's shared-memory limit; make that first call before any
  *    stream capture.

@@ -37,6 +37,40 @@ trmc_status check_state(trmc_ctx *ctx, const trmc_state *st)
 }
 
 }  // namespace
+
+const char *check_collide_args(const trmc_state *state, const trmc_collide_params *p)
+{
+    if (!state) return "state is NULL";
+    if (state->n_cells < 0) return "n_cells < 0";
+    if (state->n_cells > 0 && (!state->vx || !state->vy || !state->vz || !state->cell_start))
+        return "state velocity arrays or cell_start are NULL";
+    if (state->capacity < 0) return "capacity < 0";
+    if (!p) return "params is NULL";
+    if (p->trunc < TRMC_TRUNC_FIXED || p->trunc > TRMC_TRUNC_WB) return "bad trunc";
+    if (p->trunc == TRMC_TRUNC_WB) {
+        if (p->wb_length < TRMC_LEN_K || p->wb_length > TRMC_LEN_MEAN)
+            return "TRMC-WB needs wb_length in {TRMC_LEN_K, TRMC_LEN_MIN, TRMC_LEN_MEAN}";
+        if (p->m_fixed < 0) return "TRMC-WB needs m_fixed (m_max) >= 0";
+    } else if (p->wb_length != 0) {
+        return "params.wb_length must be 0 unless trunc is TRMC_TRUNC_WB";
+    }
+    if (p->m_cap < 1 || p->m_cap > TRMC_MCAP) return "m_cap outside [1, TRMC_MCAP]";
+    if (p->trunc == TRMC_TRUNC_FIXED && (p->m_fixed < 1 || p->m_fixed > p->m_cap)) return "m_fixed outside [1, m_cap]";
+    if (p->trunc == TRMC_TRUNC_RAD) {
+        if (!state->m_max) return "TRMC-RAD needs state.m_max";
+        if (p->m_min < 1 || p->m_min > p->m_cap) return "m_min outside [1, m_cap]";
+        if (!(p->delta1 >= 0.0) || !(p->delta2 >= p->delta1)) return "need 0 <= delta1 <= delta2";
+        if (p->indicator != TRMC_IND_PXX && p->indicator != TRMC_IND_M4) return "bad indicator";
+    }
+    if (!state->cell_param) {
+        if (!(p->eps > 0.0)) return "eps must be > 0";
+        if (!(p->dt >= 0.0)) return "dt must be >= 0";
+        if (!(p->alpha >= 0.0 && p->alpha <= 1.0)) return "alpha outside [0, 1]";
+        if (!(p->rho_scale >= 0.0)) return "rho_scale must be >= 0";
+    }
+    return nullptr;
+}
+
 }  // namespace trmc
 
 using namespace trmc;
@@ -135,30 +169,8 @@ trmc_status trmc_collide(trmc_ctx *ctx, trmc_state *state, const trmc_collide_pa
     if (!ctx) return TRMC_ERR_ARG;
     trmc_status r = check_state(ctx, state);
     if (r != TRMC_OK) return r;
-    if (!p) return set_error(ctx, TRMC_ERR_ARG, "params is NULL");
-    if (p->trunc < TRMC_TRUNC_FIXED || p->trunc > TRMC_TRUNC_WB) return set_error(ctx, TRMC_ERR_ARG, "bad trunc");
-    if (p->trunc == TRMC_TRUNC_WB) {
-        if (p->wb_length < TRMC_LEN_K || p->wb_length > TRMC_LEN_MEAN)
-            return set_error(ctx, TRMC_ERR_ARG, "TRMC-WB needs wb_length in {TRMC_LEN_K, TRMC_LEN_MIN, TRMC_LEN_MEAN}");
-        if (p->m_fixed < 0) return set_error(ctx, TRMC_ERR_ARG, "TRMC-WB needs m_fixed (m_max) >= 0");
-    } else if (p->wb_length != 0) {
-        return set_error(ctx, TRMC_ERR_ARG, "params.wb_length must be 0 unless trunc is TRMC_TRUNC_WB");
-    }
-    if (p->m_cap < 1 || p->m_cap > TRMC_MCAP) return set_error(ctx, TRMC_ERR_ARG, "m_cap outside [1, TRMC_MCAP]");
-    if (p->trunc == TRMC_TRUNC_FIXED && (p->m_fixed < 1 || p->m_fixed > p->m_cap))
-        return set_error(ctx, TRMC_ERR_ARG, "m_fixed outside [1, m_cap]");
-    if (p->trunc == TRMC_TRUNC_RAD) {
-        if (!state->m_max) return set_error(ctx, TRMC_ERR_ARG, "TRMC-RAD needs state.m_max");
-        if (p->m_min < 1 || p->m_min > p->m_cap) return set_error(ctx, TRMC_ERR_ARG, "m_min outside [1, m_cap]");
-        if (!(p->delta1 >= 0.0) || !(p->delta2 >= p->delta1)) return set_error(ctx, TRMC_ERR_ARG, "need 0 <= delta1 <= delta2");
-        if (p->indicator != TRMC_IND_PXX && p->indicator != TRMC_IND_M4) return set_error(ctx, TRMC_ERR_ARG, "bad indicator");
-    }
-    if (!state->cell_param) {
-        if (!(p->eps > 0.0)) return set_error(ctx, TRMC_ERR_ARG, "eps must be > 0");
-        if (!(p->dt >= 0.0)) return set_error(ctx, TRMC_ERR_ARG, "dt must be >= 0");
-        if (!(p->alpha >= 0.0 && p->alpha <= 1.0)) return set_error(ctx, TRMC_ERR_ARG, "alpha outside [0, 1]");
-        if (!(p->rho_scale >= 0.0)) return set_error(ctx, TRMC_ERR_ARG, "rho_scale must be >= 0");
-    }
+    const char *why = check_collide_args(state, p);
+    if (why) return set_error(ctx, TRMC_ERR_ARG, why);
     if (state->n_cells == 0) return TRMC_OK;
     return launch_collide(ctx, state, p, step, report_dev, stats_dev, static_cast<cudaStream_t>(stream));
 }

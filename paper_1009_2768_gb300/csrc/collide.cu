@@ -310,8 +310,8 @@ template <> struct Math<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt_pos(x); }
     static __device__ __forceinline__ double pow_(double x, double a) { return pow(x, a); }
     static __device__ __forceinline__ double uni(uint64_t w) { return u01(w); }
-    // sin / cos of 2 pi u: sincospi reduces the argument exactly, so it is
-    // cheaper than sin(2 pi u) and within an ulp of it
+    // sin / cos of 2 pi u from the 53-bit uniform's bits, in fixed point
+    // (sincos_2pi above; within 2 ulp of CUDA's sincospi(2u))
     static __device__ __forceinline__ void angle(uint64_t w, double &s, double &c) { sincos_2pi(w >> 11, s, c); }
     static __device__ __forceinline__ void normals(const U64x4 &w, double &z0, double &z1, double &z2)
     {
@@ -381,70 +381,138 @@ template <> struct Sum<float> {
     __device__ __forceinline__ double get() const { return double(hi) + double(lo); }
 };
 
-// Block sums of the first K per-thread partial sums of v (K <= 16), in FP64
-// for double partials and as float pairs for compensated float partials;
-// with a divisor (K <= 8), also the totals divided by it.
+// ---- canonical sums ---------------------------------------------------------
+// A per-cell sum over an index range [0, N) (particles, leaves, thermalised
+// ranks) is defined independently of the CTA size: 256 virtual lanes, lane v
+// adding the terms of indices v, v + 256, v + 512, ... in increasing order;
+// 8 virtual warps of 32 consecutive lanes, each reduced by a xor butterfly
+// (offsets 16, 8, 4, 2, 1); the 8 warp totals added as
+// ((w0 + w1) + (w2 + w3)) + ((w4 + w5) + (w6 + w7)).  A CTA of bs threads
+// (bs in {32, 64, 128, 256}) runs virtual warps warp, warp + bs/32, ... one
+// after the other, so every total, and every decision taken from it (the
+// bound Sigma, q, the split), has the same bits for every launch shape.
+constexpr int kVW = 8;
+
+// Reduce the first K partial sums of virtual warp vw (every lane of the warp
+// calls it, K <= 16) and store the totals at scratch[vw * K + j].  In FP64
+// the values are reduce-scattered: at each of the first log2(P) butterfly
+// steps (P = K rounded up to a power of two) a lane keeps half of its values
+// and adds its partner's copies of them, P - 1 + log2(32/P) FP64 adds instead
+// of 5K (GB300 issues FP64 at 2 lanes/clk/SM).  Each total is the value a
+// plain xor butterfly gives (a + b = b + a at every step).
 template <int K, int N>
-__device__ __forceinline__ void block_sums(const Sum<double> (&v)[N], double (&out)[K], double *red, double div = 0.0,
-                                           double *quot = nullptr)
+__device__ __forceinline__ void vw_put(const Sum<double> (&v)[N], double *scratch, int vw)
 {
+    static_assert(K >= 1 && K <= 16 && K <= N, "vw_put handles 1..16 values");
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int P = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : 16, G = 32 / P;
+    const int lane = threadIdx.x & 31;
+    double t[P];
 #pragma unroll
-    for (int j = 0; j < K; ++j) out[j] = v[j].s;
-    block_sum<K>(out, red, div, quot);
-}
-template <int K, int N>
-__device__ __forceinline__ void block_sums(const Sum<float> (&v)[N], double (&out)[K], double *red, double div = 0.0,
-                                           double *quot = nullptr)
-{
-    float h[K], l[K];
+    for (int i = 0; i < P; ++i) t[i] = i < K ? v[i].s : 0.0;
+    int idx = 0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) { h[j] = v[j].hi; l[j] = v[j].lo; }
-    block_sum_ff<K>(h, l, out, red, div, quot);
+    for (int h = P / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double send = up ? t[i] : t[i + h], keep = up ? t[i + h] : t[i];
+            t[i] = keep + __shfl_xor_sync(FULL, send, o);
+        }
+        if (up) idx += h;
+    }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) t[0] += __shfl_xor_sync(FULL, t[0], o);
+    if ((lane & (G - 1)) == 0 && idx < K) scratch[vw * K + idx] = t[0];
 }
 
-// One partial sum and one maximum of non-negative values (as an ordered
-// integer key) over the block, with one pair of barriers.
+// The same for compensated float partials, added as float pairs (ff_add is
+// symmetric in its operands, so the butterfly is canonical too).
+template <int K, int N>
+__device__ __forceinline__ void vw_put(const Sum<float> (&v)[N], double *scratch, int vw)
+{
+    static_assert(K >= 1 && K <= 16 && K <= N, "vw_put handles 1..16 values");
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int P = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : 16, G = 32 / P;
+    const int lane = threadIdx.x & 31;
+    float th[P], tl[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) { th[i] = i < K ? v[i].hi : 0.0f; tl[i] = i < K ? v[i].lo : 0.0f; }
+    int idx = 0;
+#pragma unroll
+    for (int h = P / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float sh_ = up ? th[i] : th[i + h], sl_ = up ? tl[i] : tl[i + h];
+            float kh = up ? th[i + h] : th[i], kl = up ? tl[i + h] : tl[i];
+            ff_add(kh, kl, __shfl_xor_sync(FULL, sh_, o), __shfl_xor_sync(FULL, sl_, o));
+            th[i] = kh; tl[i] = kl;
+        }
+        if (up) idx += h;
+    }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1)
+        ff_add(th[0], tl[0], __shfl_xor_sync(FULL, th[0], o), __shfl_xor_sync(FULL, tl[0], o));
+    if ((lane & (G - 1)) == 0 && idx < K) reinterpret_cast<float2 *>(scratch)[vw * K + idx] = make_float2(th[0], tl[0]);
+}
+
+// The 8 virtual-warp totals of K values (stored by vw_put) combined in the
+// fixed tree; every thread gets the totals and, with a divisor (K <= 8), the
+// totals divided by it.  Every thread of the CTA must call it.
+template <typename Real, int K>
+__device__ __forceinline__ void vw_total(double *scratch, double (&out)[K], double div = 0.0, double *quot = nullptr)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (warp == 0 && lane < K) {
+        double s;
+        if constexpr (sizeof(Real) == 8) {
+            const double *g = scratch + lane;
+            s = ((g[0] + g[K]) + (g[2 * K] + g[3 * K])) + ((g[4 * K] + g[5 * K]) + (g[6 * K] + g[7 * K]));
+        } else {
+            const float2 *g = reinterpret_cast<const float2 *>(scratch) + lane;
+            float h[4], l[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                h[p] = g[2 * p * K].x; l[p] = g[2 * p * K].y;
+                ff_add(h[p], l[p], g[(2 * p + 1) * K].x, g[(2 * p + 1) * K].y);
+            }
+            ff_add(h[0], l[0], h[1], l[1]);
+            ff_add(h[2], l[2], h[3], l[3]);
+            ff_add(h[0], l[0], h[2], l[2]);
+            s = double(h[0]) + double(l[0]);
+        }
+        scratch[256 + lane] = s;
+        if (quot && K <= 8) scratch[264 + lane] = s / div;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < K; ++j) out[j] = scratch[256 + j];
+    if (quot && K <= 8) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) quot[j] = scratch[264 + j];
+    }
+}
+
+// One canonical sum (stored by vw_put<1>) and one maximum of non-negative
+// values (as an ordered integer key, order-free) over the CTA.
 template <typename Real>
-__device__ __forceinline__ void block_sum_max(const Sum<Real> &v, long long key, double &sum, long long &mkey,
-                                              double *red)
+__device__ __forceinline__ void vw_total_max(double *scratch, long long key, double &sum, long long &mkey)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(FULL, key, o));
-    long long *rk = reinterpret_cast<long long *>(red);
-    if constexpr (sizeof(Real) == 8) {
-        double x = v.s;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-        if (lane == 0) { red[warp] = x; rk[32 + warp] = key; }
-    } else {
-        float h = v.hi, l = v.lo;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ff_add(h, l, __shfl_xor_sync(FULL, h, o), __shfl_xor_sync(FULL, l, o));
-        if (lane == 0) { reinterpret_cast<float2 *>(red)[warp] = make_float2(h, l); rk[32 + warp] = key; }
-    }
+    long long *rk = reinterpret_cast<long long *>(scratch);
+    if (lane == 0) rk[32 + warp] = key;
+    double s[1];
+    vw_total<Real, 1>(scratch, s);            // its first barrier also publishes the keys
+    sum = s[0];
+    long long m = rk[32];
+    for (int w = 1; w < nw; ++w) m = max(m, rk[32 + w]);
+    mkey = m;
     __syncthreads();
-    if (warp == 0) {
-        if (lane == 0) {
-            if constexpr (sizeof(Real) == 8) {
-                double s = 0.0;
-                for (int w = 0; w < nw; ++w) s += red[w];
-                red[256] = s;
-            } else {
-                float h = 0.0f, l = 0.0f;
-                for (int w = 0; w < nw; ++w) { const float2 p = reinterpret_cast<const float2 *>(red)[w]; ff_add(h, l, p.x, p.y); }
-                red[256] = double(h) + double(l);
-            }
-        } else if (lane == 1) {
-            long long m = rk[32];
-            for (int w = 1; w < nw; ++w) m = max(m, rk[32 + w]);
-            rk[257] = m;
-        }
-    }
-    __syncthreads();
-    sum = red[256];
-    mkey = rk[257];
 }
 
 // |v|^2 and the adaptive indicator in the working precision
@@ -564,37 +632,44 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         const bool rad = prm.trunc == TRMC_TRUNC_RAD;
         const bool need_m4 = rad && prm.indicator == TRMC_IND_M4, need_pxx = rad && prm.indicator == TRMC_IND_PXX;
         const bool need_d2 = sh.alpha != 0.0;
-        Sum<Real> acc[5];
+        // every particle is staged; the sums run over the canonical virtual
+        // warps (for 256 threads one per warp, as the particles are loaded)
+        const int nw = bs >> 5, warp = tid >> 5;
         constexpr int U = 4;      // loads issued together, ahead of the stores they feed
-        for (int i0 = tid; i0 < n; i0 += U * bs) {
-            Real x[U], y[U], z[U];
+        for (int vw = warp; vw < kVW; vw += nw) {
+            Sum<Real> acc[5];
+            for (int i0 = 32 * vw + lane; i0 < n; i0 += U * 32 * kVW) {
+                Real x[U], y[U], z[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = i0 + u * bs;
-                if (i < n) { x[u] = gx[base + i]; y[u] = gy[base + i]; z[u] = gz[base + i]; }
-            }
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * 32 * kVW;
+                    if (i < n) { x[u] = gx[base + i]; y[u] = gy[base + i]; z[u] = gz[base + i]; }
+                }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = i0 + u * bs;
-                if (i < n) {
-                    Vx[i] = x[u]; Vy[i] = y[u]; Vz[i] = z[u];
-                    acc[0].add(x[u]); acc[1].add(y[u]); acc[2].add(z[u]);
-                    acc[3].add_sq3(x[u], y[u], z[u]);
-                    if (need_m4) {
-                        const Real e = x[u] * x[u] + y[u] * y[u] + z[u] * z[u];
-                        acc[4].add(e * e);
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * 32 * kVW;
+                    if (i < n) {
+                        Vx[i] = x[u]; Vy[i] = y[u]; Vz[i] = z[u];
+                        acc[0].add(x[u]); acc[1].add(y[u]); acc[2].add(z[u]);
+                        acc[3].add_sq3(x[u], y[u], z[u]);
+                        if (need_m4) {
+                            const Real e = x[u] * x[u] + y[u] * y[u] + z[u] * z[u];
+                            acc[4].add(e * e);
+                        }
                     }
                 }
             }
+            if (need_m4) vw_put<5>(acc, sh.red, vw);
+            else vw_put<4>(acc, sh.red, vw);
         }
         for (int w = tid; w < (n + 31) >> 5; w += bs) sh.flags[w] = 0u;     // change flags, set by the roles
         // totals, and the mean velocity (warp 0 divides, once per cell)
         double s[5] = {0, 0, 0, 0, 0}, su[5];
         if (need_m4) {
-            block_sums<5>(acc, s, sh.red, double(n), su);
+            vw_total<Real, 5>(sh.red, s, double(n), su);
         } else {
             double s4[4], su4[4];
-            block_sums<4>(acc, s4, sh.red, double(n), su4);
+            vw_total<Real, 4>(sh.red, s4, double(n), su4);
             for (int j = 0; j < 4; ++j) { s[j] = s4[j]; su[j] = su4[j]; }
             su[4] = 0.0;
         }
@@ -602,24 +677,25 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         const Real u0 = Real(U0), u1 = Real(U1), u2 = Real(U2);
         Real d2 = 0;
         long long d2b = 0;
-        Sum<Real> pxx;
-        if (need_d2 || need_pxx) {
-            for (int i = tid; i < n; i += bs) {
-                const Real ax = Vx[i] - u0, ay = Vy[i] - u1, az = Vz[i] - u2;
-                if (need_d2) {
-                    const Real q = ax * ax + ay * ay + az * az;
-                    if constexpr (sizeof(Real) == 8) d2b = max(d2b, __double_as_longlong(q));
-                    else d2 = fmaxf(d2, q);
-                }
-                if (need_pxx) pxx.add(ax * ax);
-            }
-        }
-        if constexpr (sizeof(Real) == 4) d2b = (long long)__float_as_int(d2);
         double t[1] = {0.0};
         double dmax = 0.0;
         if (need_d2 || need_pxx) {
+            for (int vw = warp; vw < kVW; vw += nw) {
+                Sum<Real> pxx[1];
+                for (int i = 32 * vw + lane; i < n; i += 32 * kVW) {
+                    const Real ax = Vx[i] - u0, ay = Vy[i] - u1, az = Vz[i] - u2;
+                    if (need_d2) {
+                        const Real q = ax * ax + ay * ay + az * az;
+                        if constexpr (sizeof(Real) == 8) d2b = max(d2b, __double_as_longlong(q));
+                        else d2 = fmaxf(d2, q);
+                    }
+                    if (need_pxx) pxx[0].add(ax * ax);
+                }
+                vw_put<1>(pxx, sh.red, vw);
+            }
+            if constexpr (sizeof(Real) == 4) d2b = (long long)__float_as_int(d2);
             long long mk;
-            block_sum_max<Real>(pxx, d2b, t[0], mk, sh.red);
+            vw_total_max<Real>(sh.red, d2b, t[0], mk);
             if constexpr (sizeof(Real) == 8) dmax = __longlong_as_double(mk);
             else dmax = double(__int_as_float(int(mk)));
         }
@@ -1449,10 +1525,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             // cs[0..3]: change of momentum and energy over the leaves, cs[4..7]: the
             // thermalised set's momentum and energy, cs[8], cs[9]: the indicator's
             // change and the set's indicator (TRMC-RAD only)
-            Sum<Real> cs[10];
             const bool rad = prm.trunc == TRMC_TRUNC_RAD;
             const Real Ux = Real(sh.U[0]);
-            auto place = [&](int jx) {
+            auto place = [&](Sum<Real> (&cs)[10], int jx) {
                 const int sl = inv[n0 + jx];
                 const Real ox = Vx[sl], oy = Vy[sl], oz = Vz[sl];
                 const Real x = OBx[jx], y = OBy[jx], z = OBz[jx];
@@ -1467,37 +1542,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     if (rad) cs[8].add(indicator_r(x, y, z, Ux, prm.indicator) - indicator_r(ox, oy, oz, Ux, prm.indicator));
                 }
             };
-            int nrej = 0;
-            if (prm.trunc == TRMC_TRUNC_WB) {
-                // TRMC-WB (Alg. 4.6): an output whose tree is longer than m_max
-                // is not placed; its leaf joins the thermalised set, after the
-                // set's own members, in output order.  A lone rejected output
-                // with no thermalised set is kept: its only Maxwellian
-                // resample with the same momentum and energy is itself.
-                const double mmax = double(prm.m_fixed);
-                const double *OL = sh.OLBuf;
-                bool keep_all = false;
-                if (sh.R == 0) {
-                    int tot = 0;
-                    for (int j0 = 0; j0 < D0; j0 += bs) tot += __syncthreads_count(j0 + tid < D0 && OL[j0 + tid] > mmax);
-                    keep_all = tot == 1;
-                }
-                for (int j0 = 0; j0 < D0; j0 += bs) {
-                    const int jx = j0 + tid;
-                    const bool rj = !keep_all && jx < D0 && OL[jx] > mmax;
-                    int ex;
-                    const int tot = block_flag_scan(rj, ex, sh.scan);
-                    if (rj) sh.ext[nrej + ex] = inv[n0 + jx];
-                    else if (jx < D0) place(jx);
-                    nrej += tot;
-                }
-                __syncthreads();            // the pool below reads the rejected slots written above
-            } else {
-                for (int jx = tid; jx < D0; jx += bs) place(jx);
-            }
-            const int pool0 = n0 + D0, R = sh.R, Rx = R + nrej;
-            for (int t = tid; t < Rx; t += bs) {
-                const int sl = t < R ? inv[pool0 + t] : sh.ext[t - R];
+            auto pool_add = [&](Sum<Real> (&cs)[10], int sl) {
                 const Real x = Vx[sl], y = Vy[sl], z = Vz[sl];
                 cs[4].add(x); cs[5].add(y); cs[6].add(z);
                 cs[7].add_sq3(x, y, z);
@@ -1505,16 +1550,58 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     if constexpr (sizeof(Real) == 8) cs[9].add(indicator(x, y, z, sh.U, prm.indicator));
                     else cs[9].add(indicator_r(x, y, z, Ux, prm.indicator));
                 }
+            };
+            // TRMC-WB (Alg. 4.6): an output whose tree is longer than m_max is
+            // not placed; its leaf joins the thermalised set, after the set's
+            // own members, in output order.  A lone rejected output with no
+            // thermalised set is kept: its only Maxwellian resample with the
+            // same momentum and energy is itself.
+            const bool wbm = prm.trunc == TRMC_TRUNC_WB;
+            const double mmax = double(prm.m_fixed);
+            const double *OL = sh.OLBuf;
+            bool keep_all = false;
+            if (wbm && sh.R == 0) {
+                int tot = 0;
+                for (int j0 = 0; j0 < D0; j0 += bs) tot += __syncthreads_count(j0 + tid < D0 && OL[j0 + tid] > mmax);
+                keep_all = tot == 1;
             }
+            // cs[0..3]: change of momentum and energy over the leaves, cs[4..7]: the
+            // thermalised set's momentum and energy (rejected leaves with their
+            // original velocities), cs[8], cs[9]: the indicator's change and the
+            // set's indicator (TRMC-RAD only); canonical sums
+            const int pool0 = n0 + D0, R = sh.R, nw = bs >> 5;
+            for (int vw = warp; vw < kVW; vw += nw) {
+                Sum<Real> cs[10];
+                for (int jx = 32 * vw + lane; jx < D0; jx += 32 * kVW) {
+                    if (wbm && !keep_all && OL[jx] > mmax) pool_add(cs, inv[n0 + jx]);
+                    else place(cs, jx);
+                }
+                for (int t = 32 * vw + lane; t < R; t += 32 * kVW) pool_add(cs, inv[pool0 + t]);
+                if (rad) vw_put<10>(cs, sh.red, vw);
+                else vw_put<8>(cs, sh.red, vw);
+            }
+            int nrej = 0;
+            if (wbm) {
+                // the rejected leaves' slots, in output order
+                for (int j0 = 0; j0 < D0; j0 += bs) {
+                    const int jx = j0 + tid;
+                    const bool rj = !keep_all && jx < D0 && OL[jx] > mmax;
+                    int ex;
+                    const int tot = block_flag_scan(rj, ex, sh.scan);
+                    if (rj) sh.ext[nrej + ex] = inv[n0 + jx];
+                    nrej += tot;
+                }
+            }
+            const int Rx = R + nrej;
             double s[5], p[5];
             if (rad) {
                 double t[10];
-                block_sums<10>(cs, t, sh.red);
+                vw_total<Real, 10>(sh.red, t);
                 for (int j = 0; j < 4; ++j) { s[j] = t[j]; p[j] = t[4 + j]; }
                 s[4] = t[8]; p[4] = t[9];
             } else {
                 double t[8];
-                block_sums<8>(cs, t, sh.red);
+                vw_total<Real, 8>(sh.red, t);
                 for (int j = 0; j < 4; ++j) { s[j] = t[j]; p[j] = t[4 + j]; }
                 s[4] = 0.0; p[4] = 0.0;
             }
@@ -1585,21 +1672,25 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
     const int pool0 = sh.n0 + sh.D0;
     const int32_t *ext = sh.ext;
     auto pslot = [&](int t) { return t < R0 ? inv[pool0 + t] : ext[t - R0]; };
-    Sum<Real> rs[4];                  // the stored set's sums, for the carry (FP32-mixed)
+    const int warp = tid >> 5, nw = bs >> 5;
+    const bool carry = a.cell_carry != nullptr;
     if (R >= 2) {
         // one pass for the samples and their first and second moments:
-        // e = sum |z - zbar|^2 = sum |z|^2 - zbar . sum z
-        Sum<Real> qs[4];
-        for (int t = tid; t < R; t += bs) {
-            Real z0, z1, z2;
-            Math<Real>::normals(rng.draw(uint64_t(t), 0, 0, TAG_MAXW), z0, z1, z2);
-            const int sl = pslot(t);
-            Vx[sl] = z0; Vy[sl] = z1; Vz[sl] = z2;
-            qs[0].add(z0); qs[1].add(z1); qs[2].add(z2);
-            qs[3].add_sq3(z0, z1, z2);
+        // e = sum |z - zbar|^2 = sum |z|^2 - zbar . sum z (canonical sums)
+        for (int vw = warp; vw < kVW; vw += nw) {
+            Sum<Real> qs[4];
+            for (int t = 32 * vw + lane; t < R; t += 32 * kVW) {
+                Real z0, z1, z2;
+                Math<Real>::normals(rng.draw(uint64_t(t), 0, 0, TAG_MAXW), z0, z1, z2);
+                const int sl = pslot(t);
+                Vx[sl] = z0; Vy[sl] = z1; Vz[sl] = z2;
+                qs[0].add(z0); qs[1].add(z1); qs[2].add(z2);
+                qs[3].add_sq3(z0, z1, z2);
+            }
+            vw_put<4>(qs, sh.red, vw);
         }
         double s[4], zq[4];
-        block_sums<4>(qs, s, sh.red, double(R), zq);       // zq[0..2]: the samples' mean
+        vw_total<Real, 4>(sh.red, s, double(R), zq);       // zq[0..2]: the samples' mean
         const double zb0 = zq[0], zb1 = zq[1], zb2 = zq[2];
         const Real rz0 = Real(zb0), rz1 = Real(zb1), rz2 = Real(zb2);
         // target: what the set carried, minus the collisions' round-off change,
@@ -1621,38 +1712,39 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         }
         __syncthreads();
         const double sc = sh.msc[0], u0 = sh.msc[1], u1 = sh.msc[2], u2 = sh.msc[3];
-        const bool carry = a.cell_carry != nullptr;
-        if constexpr (sizeof(Real) == 8) {
-            for (int t = tid; t < R; t += bs) {
+        // FP32-mixed: FP64 scale and targets, applied in float (the stored
+        // result is a float either way); the stored set's canonical sums give
+        // the carry
+        const Real fs = Real(sc), f0 = Real(u0), f1 = Real(u1), f2 = Real(u2);
+        for (int vw = warp; vw < kVW; vw += nw) {
+            Sum<Real> rs[4];
+            for (int t = 32 * vw + lane; t < R; t += 32 * kVW) {
                 const int sl = pslot(t);
-                const double x = u0 + sc * (Vx[sl] - zb0), y = u1 + sc * (Vy[sl] - zb1), z = u2 + sc * (Vz[sl] - zb2);
+                Real x, y, z;
+                if constexpr (sizeof(Real) == 8) {
+                    x = u0 + sc * (Vx[sl] - zb0); y = u1 + sc * (Vy[sl] - zb1); z = u2 + sc * (Vz[sl] - zb2);
+                } else {
+                    x = f0 + fs * (Vx[sl] - rz0); y = f1 + fs * (Vy[sl] - rz1); z = f2 + fs * (Vz[sl] - rz2);
+                }
                 Vx[sl] = x; Vy[sl] = y; Vz[sl] = z;
                 if (carry) { rs[0].add(x); rs[1].add(y); rs[2].add(z); rs[3].add_sq3(x, y, z); }
             }
-        } else {
-            // FP64 scale and targets, applied in float: the stored result is a
-            // float either way
-            const Real fs = Real(sc), f0 = Real(u0), f1 = Real(u1), f2 = Real(u2);
-            for (int t = tid; t < R; t += bs) {
-                const int sl = pslot(t);
-                const Real x = f0 + fs * (Vx[sl] - rz0), y = f1 + fs * (Vy[sl] - rz1), z = f2 + fs * (Vz[sl] - rz2);
-                Vx[sl] = x; Vy[sl] = y; Vz[sl] = z;
-                if (carry) { rs[0].add(x); rs[1].add(y); rs[2].add(z); rs[3].add_sq3(x, y, z); }
+            if (carry) vw_put<4>(rs, sh.red, vw);
+        }
+        if (carry) {
+            // new carry: what the stored thermalised set misses of its target
+            double r[4];
+            vw_total<Real, 4>(sh.red, r);
+            if (tid == 0) {
+                sh.carry[0] = sh.Pt[0] - r[0]; sh.carry[1] = sh.Pt[1] - r[1]; sh.carry[2] = sh.Pt[2] - r[2];
+                sh.carry[3] = sh.Et - r[3];
             }
         }
     }
     __syncthreads();
     if (a.cell_carry) {
-        // new carry: what the stored thermalised set misses of its target
-        // (R >= 2), or the collisions' round-off change (R <= 1)
-        if (R >= 2) {
-            double r[4];
-            block_sums<4>(rs, r, sh.red);
-            if (tid == 0) {
-                sh.carry[0] = sh.Pt[0] - r[0]; sh.carry[1] = sh.Pt[1] - r[1]; sh.carry[2] = sh.Pt[2] - r[2];
-                sh.carry[3] = sh.Et - r[3];
-            }
-        } else if (tid == 0) {
+        // with R <= 1 the carry takes the collisions' round-off change
+        if (R < 2 && tid == 0) {
             sh.carry[0] -= sh.dP[0]; sh.carry[1] -= sh.dP[1]; sh.carry[2] -= sh.dP[2]; sh.carry[3] -= sh.dE;
         }
         if (tid == 0)
@@ -1795,6 +1887,19 @@ cudaError_t allow_max_smem(int device, int smem_optin)
     return e;
 }
 
+// Dynamic shared memory of one CTA when per_sm CTAs share an SM: the SM's
+// budget (226 KB where the device lets a CTA opt in to 200 KB or more, else
+// the opt-in limit) split evenly, less the static part and 1 KB per CTA that
+// the SM reserves; never more than one CTA may have.
+template <typename Real>
+int collide_smem(int smem_optin, int per_sm)
+{
+    const int budget = smem_optin >= 200 * 1024 ? 226 * 1024 : smem_optin;
+    int smem = budget / per_sm - int(sizeof(Sh<Real>)) - 1024;
+    if (smem > smem_optin - int(sizeof(Sh<Real>))) smem = smem_optin - int(sizeof(Sh<Real>));
+    return smem > 0 ? smem : 0;
+}
+
 template <typename Real>
 trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *prm, uint64_t step,
                      int64_t *report, trmc_stats *stats, cudaStream_t s)
@@ -1803,9 +1908,7 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     // cells per SM overlap one cell's serial phases with the others' work;
     // the shared-memory budget of an SM is split evenly between them
     const int threads = ctx->collide_threads, per_sm_target = ctx->collide_ctas_per_sm;
-    const int budget = ctx->smem_optin >= 200 * 1024 ? 226 * 1024 : int(ctx->smem_optin);
-    int smem = budget / per_sm_target - int(sizeof(Sh<Real>)) - 1024;
-    if (smem > int(ctx->smem_optin) - int(sizeof(Sh<Real>))) smem = int(ctx->smem_optin) - int(sizeof(Sh<Real>));
+    const int smem = collide_smem<Real>(int(ctx->smem_optin), per_sm_target);
     cudaError_t e = allow_max_smem<Real>(ctx->device, int(ctx->smem_optin));
     if (e != cudaSuccess) return cuda_error(ctx, e, "cudaFuncSetAttribute(collide)");
     int per_sm = 0;
@@ -1915,8 +2018,7 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
         D.scratch = static_cast<char *>(p);
         D.ready = true;
     }
-    const int smem = D.smem_optin >= 200 * 1024 ? (226 * 1024) / per_sm_target - int(sizeof(Sh<Real>)) - 1024
-                                                : D.smem_optin / 2 - int(sizeof(Sh<Real>)) - 1024;
+    const int smem = collide_smem<Real>(D.smem_optin, per_sm_target);
     if (allow_max_smem<Real>(dev, D.smem_optin) != cudaSuccess) return TRMC_ERR_CUDA;
     const size_t avail = size_t(TRMC_STATIC_SCRATCH_BYTES) - kStaticControl;
     const size_t need = static_cell_bytes(max_cell, sizeof(Real), prm->trunc == TRMC_TRUNC_WB);
@@ -1961,22 +2063,9 @@ extern "C" trmc_status trmc_collide_static(trmc_state *state, const trmc_collide
                                            int *status_dev, void *stream)
 {
     using namespace trmc;
-    if (!state || !p) return TRMC_ERR_ARG;
     if (precision != TRMC_FP64 && precision != TRMC_FP32_MIXED) return TRMC_ERR_ARG;
-    if (state->n_cells < 0 || (state->n_cells > 0 && (!state->vx || !state->vy || !state->vz || !state->cell_start)))
-        return TRMC_ERR_ARG;
+    if (check_collide_args(state, p)) return TRMC_ERR_ARG;          // the same checks as trmc_collide
     if (max_cell_particles < 0) return TRMC_ERR_ARG;
-    if (p->trunc < TRMC_TRUNC_FIXED || p->trunc > TRMC_TRUNC_WB) return TRMC_ERR_ARG;
-    if (p->trunc == TRMC_TRUNC_WB ? (p->wb_length < TRMC_LEN_K || p->wb_length > TRMC_LEN_MEAN || p->m_fixed < 0)
-                                  : p->wb_length != 0)
-        return TRMC_ERR_ARG;
-    if (p->m_cap < 1 || p->m_cap > TRMC_MCAP) return TRMC_ERR_ARG;
-    if (p->trunc == TRMC_TRUNC_FIXED && (p->m_fixed < 1 || p->m_fixed > p->m_cap)) return TRMC_ERR_ARG;
-    if (p->trunc == TRMC_TRUNC_RAD && (!state->m_max || p->m_min < 1 || p->m_min > p->m_cap ||
-                                       !(p->delta1 >= 0.0) || !(p->delta2 >= p->delta1)))
-        return TRMC_ERR_ARG;
-    if (!state->cell_param && (!(p->eps > 0.0) || !(p->dt >= 0.0) || !(p->alpha >= 0.0 && p->alpha <= 1.0)))
-        return TRMC_ERR_ARG;
     if (state->n_cells == 0) return TRMC_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (precision == TRMC_FP64) return launch_static<double>(state, p, seed, step, max_cell_particles, status_dev, s);

@@ -37,6 +37,9 @@ constexpr int kMC = TRMC_MCAP;
 constexpr int kThreads = 256;         // collide CTA size
 
 trmc_status set_error(trmc_ctx *ctx, trmc_status code, const std::string &msg);
+// Host checks of a collision step's state and parameters, shared by
+// trmc_collide and trmc_collide_static: NULL if they are valid, else why not.
+const char *check_collide_args(const trmc_state *state, const trmc_collide_params *p);
 trmc_status cuda_error(trmc_ctx *ctx, cudaError_t e, const char *where);
 
 trmc_status launch_collide(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *prm,

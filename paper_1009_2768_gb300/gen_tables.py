@@ -1,8 +1,15 @@
 """Writes csrc/fp64_tables.inc: the correctly rounded constants of the FP64
-angle and logarithm evaluations in trmc_device.cuh, computed here in 60-digit
-decimal arithmetic from their series (pi by Machin's formula, sin/cos by
-Taylor series, ln by the atanh series).  Run by build.py when the file is
-missing; the file is committed, so the build normally only reads it.
+angle and logarithm evaluations of the collision kernel (collide.cu), computed
+here in 60-digit decimal arithmetic from their series (pi by Machin's formula,
+sin/cos by Taylor series, ln by the atanh series).  Run by build.py when the
+file is missing; the file is committed, so the build normally only reads it.
+
+The evaluations are table-driven in the manner of P. T. P. Tang ("Table-driven
+implementation of the exponential function in IEEE floating-point
+arithmetic", ACM TOMS 15, 1989, and its logarithm companion, TOMS 16, 1990):
+the argument picks a breakpoint whose function value is tabulated to full
+precision, and a short series evaluates the function of the small remainder;
+the addition formulas (sin, cos) or a sum of logarithms (ln) combine the two.
 
   kSinCos256[i] = { sin(2 pi i / 256), cos(2 pi i / 256) },  i = 0..255
   kLnT128[j]    = { ln((1 + j/128) / 2), 2^-52 / (1 + j/128) }, j = 0..127

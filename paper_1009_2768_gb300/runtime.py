@@ -1,6 +1,9 @@
 """Runtime helpers around the C ABI: CUDA-graph stepping, the launch-shape
 autotuner and largest-first cell ordering.  Everything here only decides
-how the library's kernels are launched; results do not change.
+how the library's kernels are launched: the results are bit-identical for
+every launch shape and cell order (the library sums every cell's moments in
+one canonical order whatever the CTA size), and the autotuner puts the
+simulation back where it found it.
 
 * GraphStepper captures a fixed number of whole time steps (transport +
   sort + collide, or collide alone) into one CUDA graph and replays it.  The
@@ -10,7 +13,8 @@ how the library's kernels are launched; results do not change.
   the workload transports: the sort's ping-pong buffers are then back in
   their original roles at the end of every replay.
 * autotune_collide times candidate (CTA size, CTAs per SM) shapes on the
-  live workload and keeps the fastest.
+  live workload, keeps the fastest and then restores the state it stepped
+  (velocities, positions, cell starts, RAD depths, carries, step counters).
 * largest_first orders cells by particle count, biggest first, so the
   longest cells start early and the launch does not end on one of them.
 """
@@ -60,12 +64,41 @@ class GraphStepper:
             self.graph.replay()
 
 
+def _snapshot(sim):
+    """Copies of every tensor of the simulation's state and its step index."""
+    import torch
+    st = sim.state
+    keep = {k: v.clone() for k, v in vars(st).items() if isinstance(v, torch.Tensor)}
+    extra = {k: v.clone() for k, v in vars(sim).items() if isinstance(v, torch.Tensor)}
+    return keep, extra, getattr(sim, "step_index", None)
+
+
+def _restore(sim, snap):
+    """Copy the snapshot back.  Transport swaps the roles of a state's
+    primary and *_alt tensors; the data go back under the names they had, and
+    the C struct is refilled to match."""
+    keep, extra, step_index = snap
+    st = sim.state
+    for k, v in keep.items():
+        cur = getattr(st, k)
+        if cur.data_ptr() != v.data_ptr():
+            cur.copy_(v)
+    for k, v in extra.items():
+        getattr(sim, k).copy_(v)
+    if step_index is not None:
+        sim.step_index = step_index
+    st._fill()
+
+
 def autotune_collide(sim, shapes=DEFAULT_SHAPES, steps=6, flush_bytes=256 << 20):
     """Time `steps` collide launches of the live workload for every (threads,
     CTAs per SM) shape, with an L2 flush before each, and keep the fastest.
-    Returns {shape: mean collide ms} and leaves the best shape set."""
+    The simulation is put back in the state it had before tuning.  Returns
+    {shape: mean collide ms} and leaves the best shape set."""
     import torch
     flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    snap = _snapshot(sim)
     times = {}
     for shape in shapes:
         T.trmc_set_collide_launch(sim.ctx, *shape)
@@ -81,4 +114,6 @@ def autotune_collide(sim, shapes=DEFAULT_SHAPES, steps=6, flush_bytes=256 << 20)
     best = min(times, key=times.get)
     T.trmc_set_collide_launch(sim.ctx, *best)
     T.trmc_check(sim.ctx)
+    _restore(sim, snap)
+    torch.cuda.synchronize()
     return times, best

@@ -53,3 +53,28 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(trmc.Domain) == 88
     assert ctypes.sizeof(trmc.CellParam) == 32
     assert ctypes.sizeof(trmc.Stats) == 88
+
+
+def test_static_entry_point_checks_parameters_on_the_host():
+    """trmc_collide_static makes trmc_collide's host checks before any CUDA
+    call: invalid parameters come back as TRMC_ERR_ARG, on a machine without
+    a GPU too (valid ones get as far as the first CUDA call)."""
+    import ctypes
+    import math
+    from paper_1009_2768_gb300 import build, trmc as T
+    build.build()
+    lib = T.load()
+    st = T.State()
+    st.vx = st.vy = st.vz = st.cell_start = st.m_max = 256      # never dereferenced on the host
+    st.n_cells, st.capacity = 1, 10
+
+    def code(**kw):
+        p = T.collide_params(dt=0.05, eps=1.0, alpha=1.0, rho_scale=0.01, trunc=T.TRUNC_RAD, m=2)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return lib.trmc_collide_static(ctypes.byref(st), ctypes.byref(p), T.FP64, 0, 0, 100, None, None)
+
+    for bad in ({"rho_scale": -1.0}, {"rho_scale": math.nan}, {"indicator": 7}, {"eps": 0.0}, {"dt": -1.0},
+                {"alpha": 1.5}, {"m_cap": 0}, {"m_min": 0}, {"delta2": 0.001}, {"trunc": 9}, {"wb_length": 2}):
+        assert code(**bad) == T.ERR_ARG, bad
+    assert code() != T.ERR_ARG

@@ -1,0 +1,62 @@
+"""Results do not depend on the collide launch shape: every per-cell sum
+(moments, the collisions' change, the thermalised set, the Maxwellian
+samples, the carry) runs over the same 256 virtual lanes and 8 virtual warps
+in a fixed tree whatever the CTA size, so the bound, q, the split and every
+velocity have the same bits for every (threads per CTA, CTAs per SM)."""
+import numpy as np
+import pytest
+
+from paper_1009_2768_gb300 import synth
+from tests.gpu_common import T, need_gpu, torch, ensure_built
+
+pytestmark = pytest.mark.gpu
+
+COUNTS = [2, 3, 17, 64, 255, 257, 889, 2500, 6000]
+SHAPES = [(64, 8), (128, 4), (256, 2), (96, 3), (32, 8)]
+
+
+def run_shape(precision, shape, params, counts, steps=2, carry=False):
+    ensure_built()
+    g = synth.rng(77)
+    v = np.concatenate([synth.bimaxwellian(n, 2.0, 0.5, u=(0.3, -0.2, 0.1), g=g) for n in counts], axis=1)
+    cs = synth.starts(counts)
+    nc = len(counts)
+    cp = np.stack([np.geomspace(1e-3, 1.0, nc), np.full(nc, 0.05), 1.0 / np.asarray(counts, float) * 2.0,
+                   np.full(nc, params.alpha)], axis=1)
+    st = T.ParticleState(cs, precision=precision, rad=params.trunc == T.TRUNC_RAD, cell_param=cp, carry=carry)
+    st.set_velocities(v)
+    if st.m_max is not None:
+        st.m_max.fill_(2)
+    c = T.trmc_create(precision, 11, 1 << 30)
+    T.trmc_set_collide_launch(c, *shape)
+    rep = torch.zeros((nc, T.REPORT_LEN), dtype=torch.int64, device="cuda")
+    for s in range(steps):
+        T.trmc_collide(c, st, params, 3 + s, report=rep)
+    T.trmc_check(c)
+    T.trmc_destroy(c)
+    out = [st.v.cpu().numpy(), rep.cpu().numpy(), st.cell_vmax2.cpu().numpy()]
+    if st.m_max is not None:
+        out.append(st.m_max.cpu().numpy())
+    if carry:
+        out.append(st.cell_carry.cpu().numpy())
+    return out
+
+
+PARAMS = {
+    "rad hard spheres": T.collide_params(alpha=1.0, trunc=T.TRUNC_RAD, m=2, indicator=T.IND_PXX),
+    "rad M4, vhs 0.6": T.collide_params(alpha=0.6, trunc=T.TRUNC_RAD, m=2, indicator=T.IND_M4),
+    "fixed m=4, Maxwell": T.collide_params(alpha=0.0, trunc=T.TRUNC_FIXED, m=4),
+    "wb, 1 + min": T.collide_params(alpha=1.0, trunc=T.TRUNC_WB, m=3, m_cap=12, wb_length=T.LEN_MIN),
+}
+
+
+@pytest.mark.parametrize("precision", [T.FP64, T.FP32_MIXED])
+@pytest.mark.parametrize("name", sorted(PARAMS))
+def test_results_are_bit_identical_across_launch_shapes(precision, name):
+    need_gpu()
+    carry = precision == T.FP32_MIXED
+    ref = run_shape(precision, SHAPES[0], PARAMS[name], COUNTS, carry=carry)
+    for shape in SHAPES[1:]:
+        got = run_shape(precision, shape, PARAMS[name], COUNTS, carry=carry)
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b), f"launch shape {shape} differs from {SHAPES[0]} ({name})"

@@ -112,3 +112,26 @@ def test_adaptive_order_does_not_change_results(precision):
     assert cost.max() > 0
     a.close()
     b.close()
+
+
+def test_autotuner_puts_the_simulation_back():
+    """The autotuner steps the live workload once per candidate shape and
+    then restores it: the next step equals that of an untuned twin."""
+    need_gpu()
+    from paper_1009_2768_gb300.runtime import autotune_collide
+    from paper_1009_2768_gb300.workloads import ShockTubes
+    ref = ShockTubes((1e-2, 1e-3), n_cells=48, mean_per_cell=150, seed=9)
+    tun = ShockTubes((1e-2, 1e-3), n_cells=48, mean_per_cell=150, seed=9)
+    for _ in range(3):
+        ref.step()
+        tun.step()
+    before = snapshot(tun)
+    times, best = autotune_collide(tun, shapes=((64, 8), (128, 4), (96, 3)), steps=1)
+    assert best in times and same(before, snapshot(tun))
+    assert tun.step_index == ref.step_index
+    ref.step()
+    tun.step()
+    torch.cuda.synchronize()
+    assert same(snapshot(ref), snapshot(tun))
+    ref.close()
+    tun.close()

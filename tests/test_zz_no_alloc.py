@@ -76,6 +76,23 @@ def test_static_between_calls_of_a_wide_launch_shape():
         T.trmc_check(c_ref)
     T.trmc_destroy(c)
     n = int(cs[-1])
-    # the wider CTAs sum the moments in another order: equal to rounding
-    assert_velocity_parity(st.v[:, :n].cpu().numpy(), ref.v[:, :n].cpu().numpy(), cs)
+    # per-cell sums run in the same canonical order for every CTA size
+    assert torch.equal(st.v[:, :n], ref.v[:, :n])
     assert torch.equal(tmp.v[:, :n], ref.v[:, :n])
+
+
+def test_static_reports_a_cell_larger_than_its_bound():
+    """With max_cell_particles below the real largest cell, that cell can
+    overflow its slab: it is left unchanged and reported in status_dev as
+    (TRMC_ERR_CAPACITY, cell) while every other cell is collided."""
+    need_gpu()
+    counts = [50] * 700 + [6000]
+    cs, (_, st) = _states(T.FP64, counts, seed=34)
+    before = st.v.clone()
+    p = T.collide_params(dt=0.05, eps=0.05, alpha=1.0, rho_scale=1.0 / 500, trunc=T.TRUNC_RAD, m=2)
+    status = torch.zeros(2, dtype=torch.int32, device="cuda")
+    T.trmc_collide_static(st, p, T.FP64, 0, 1, 50, status)
+    torch.cuda.synchronize()
+    assert status.tolist() == [T.ERR_CAPACITY, len(counts) - 1]
+    assert torch.equal(st.v[:, cs[-2]:cs[-1]], before[:, cs[-2]:cs[-1]])
+    assert not torch.equal(st.v[:, :cs[-2]], before[:, :cs[-2]])
