@@ -1,26 +1,33 @@
 #!/usr/bin/env python
 """Benchmark of the TRMC-R hot path on GB300: one step = free transport with
-specular walls + stable cell sort + collision step (split, recursive trees,
-VHS hard-sphere acceptance, Maxwellian renormalisation, TRMC-RAD) over the
-1D Riemann shock-tube workload: four tubes on [0,1] (one per Knudsen number
-1e-1, 1e-2, 1e-3, 1e-4), 400 cells and 500 particles per cell on average
-each, CFL 0.5, FP64.  Prints one JSON line.
+inflow/outflow reservoirs + stable cell sort + collision step (split,
+recursive trees, VHS hard-sphere acceptance, Maxwellian renormalisation,
+TRMC-RAD) over the Mach 3 stationary normal shock: 4000 cells of 2500
+particles on average (1e7 particles), eps 1e-3, CFL 0.5, FP32 velocities
+with FP64 moments.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload shock|batched|bkw|stationary|serving]
+                  [--workload stationary|shock|batched|bkw|serving]
 
---workload selects the step timed (default shock, the benchmark line):
-  shock   the four-tube FP64 shock-tube step above;
+--workload selects the step timed (default stationary, the benchmark line):
+  stationary  the Mach 3 stationary shock above (FP32-mixed);
+  shock   four 1D Riemann shock tubes on [0,1] (one per Knudsen number 1e-1,
+          1e-2, 1e-3, 1e-4), 400 cells x 500 particles per cell, specular
+          walls, CFL 0.5, FP64;
   batched 4096 independent homogeneous cells, 64..8192 particles log-uniform,
           bi-Maxwellian, VHS alpha 0.6, eps log-uniform 1e-4..10, FP32-mixed;
   bkw     one homogeneous cell of 1e5 Maxwell molecules from BKW data, FP64;
-  stationary  Mach 3 stationary shock, 4000 cells x 2500 particles, reservoirs,
-          FP32-mixed;
   serving a stream of solve requests (shock tubes and homogeneous relaxations,
           1e5..2e7 particles log-uniform, eps 1e-4..1 log-uniform, FP32-mixed)
           arriving as a Poisson process, swept over --rates requests/s,
           admitted against a 150 GB HBM budget; reports p50/p99 latency and
           particle-steps/s per rate (value: the highest rate's throughput).
+
+Every line states the moment error of the timed form against the FP64 CPU
+oracle: the GPU form and the oracle step the same initial state with the same
+keys for a few steps, and the oracle with other keys gives the Monte Carlo
+noise floor of the same measure; the plain FP64 form of the same workload is
+measured beside it (forms).
 
 N > 1 runs N independent replicas (one per rank, launched by torchrun), each
 on its own problem ids; value is the total over ranks.  --impl reference
@@ -48,6 +55,8 @@ WORKLOAD = ("1D Riemann shock tube on [0,1] (rho 1/0.125, T 1/0.8, u 0), hard-sp
             "CFL 0.5, TRMC-RAD (P_xx indicator, delta 0.005/0.01, m0 2); 4 tubes x 400 cells x 500 "
             "particles/cell mean, eps 1e-1/1e-2/1e-3/1e-4, FP64")
 METRIC = "particle-steps/s"
+DEFAULT_WORKLOAD = "stationary"
+COMPARE_STEPS = 20          # steps of the oracle comparison (moment error, CPU baseline)
 
 # DRAM traffic per collide launch from `ncu` (dram__bytes_read.sum + dram__bytes_write.sum)
 # of the same command, keyed by the hash of csrc/collide.cu it was taken on; reported as
@@ -129,6 +138,25 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -181,14 +209,14 @@ def oracle_tube_rate(n_cells, mean, steps, threads, seed=0, budget_s=None):
     return n * done / el, n, done, el
 
 
-def oracle_workload_rate(workload, threads, budget_s=15.0, seed=0):
-    """Particle-steps/s of the FP64 CPU oracle on a bounded sample of a
-    workload other than the shock tubes: (rate, particles, steps, seconds,
-    sample description).  Same generators and parameters as workloads.py."""
+def oracle_workload(workload, threads, seed=0):
+    """The FP64 CPU oracle set up on a bounded sample of a workload other
+    than the shock tubes, with the oracle's own initial-data sampler: returns
+    (step function, particles, sample description, threads used).  Same
+    generators and parameters as workloads.py."""
     from oracle import oracle as O
     from paper_1009_2768_gb300 import synth
     from paper_1009_2768_gb300.workloads import rankine_hugoniot
-    t_setup = time.perf_counter()
     if workload == "batched":
         # the first 512 of the 4096 cells (same log-uniform counts, eps and anisotropy)
         g = synth.rng(seed)
@@ -256,38 +284,51 @@ def oracle_workload_rate(workload, threads, budget_s=15.0, seed=0):
         def step(s):
             nonlocal v, ms
             v, _, ms = O.collide(v, cs, prm, s, m_state=ms, threads=1)
-    setup = time.perf_counter() - t_setup
-    done, t0 = 0, time.perf_counter()
-    while True:
-        step(done)
-        done += 1
-        if time.perf_counter() - t0 > budget_s or done >= 1000:
-            break
-    el = time.perf_counter() - t0
-    return n * done / el, n, done, el, f"{desc}: {done} steps in {el:.1f} s (set-up {setup:.1f} s)", threads
+    return step, n, desc, threads
 
 
 def reference_arm(args):
+    """The CPU oracle, as it stands, on the machine's host cores, on a bounded
+    sample of the workload the GPU arm times: W untimed steps, then K timed."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     from oracle.build import build_oracle
     build_oracle()
     threads = os.cpu_count() or 1
-    # bounded sample: one tube, cells scaled so that W + K steps take about two minutes
-    rate, n, _, el = oracle_tube_rate(40, MEAN, 2, threads)
-    per_step = n / rate
-    cells = int(np.clip(40 * 120.0 / max(per_step * (args.steps + args.warmup) * 10, 1e-9), 8, N_CELLS))
-    cells -= cells % 2
-    oracle_tube_rate(cells, MEAN, args.warmup, threads)
-    rate, n, done, el = oracle_tube_rate(cells, MEAN, args.steps, threads)
-    sample = f"one tube (eps 1e-2) of {cells} cells x {MEAN}/cell mean ({n} particles), {done} steps"
+    wl = args.workload
+    if wl == "serving":
+        print(json.dumps({"impl": "reference", "unavailable": "the serving stream has no CPU-oracle form: "
+                          "requests are timed end to end on the GPU only"}))
+        return
+    if wl == "shock":
+        # one tube, cells scaled so that W + K steps take about two minutes
+        rate, n, _, el = oracle_tube_rate(40, MEAN, 2, threads)
+        per_step = n / rate
+        cells = int(np.clip(40 * 120.0 / max(per_step * (args.steps + args.warmup) * 10, 1e-9), 8, N_CELLS))
+        cells -= cells % 2
+        oracle_tube_rate(cells, MEAN, args.warmup, threads)
+        rate, n, done, el = oracle_tube_rate(cells, MEAN, args.steps, threads)
+        sample = f"one tube (eps 1e-2) of {cells} cells x {MEAN}/cell mean ({n} particles), {done} steps"
+        used = threads
+    else:
+        step, n, desc, used = oracle_workload(wl, threads)
+        for s in range(args.warmup):
+            step(s)
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            step(args.warmup + s)
+        el = time.perf_counter() - t0
+        done = args.steps
+        rate = n * done / el
+        sample = f"{desc}: {args.warmup} untimed + {done} timed steps in {el:.1f} s"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC, "n_gpus": args.gpus,
         "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": sample},
+        "config": {"workload": WORKLOADS[wl], "sample": sample},
+        "cpu_baseline": {"value": rate, "unit": METRIC, "cores": used, "cpu_model": cpu_model(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -306,17 +347,22 @@ WORKLOADS = {
 }
 
 
-def make_sim(workload, seed):
+def make_sim(workload, seed, precision=None):
+    """The workload's simulation on the GPU (its own precision unless one is
+    given), with its data type label."""
     from paper_1009_2768_gb300 import trmc as T
     from paper_1009_2768_gb300.workloads import BatchedRelaxation, HomogeneousBKW, ShockTubes, StationaryShock
+    own = {"stationary": T.FP32_MIXED, "shock": T.FP64, "batched": T.FP32_MIXED, "bkw": T.FP64}[workload]
+    prec = own if precision is None else precision
+    label = "f64" if prec == T.FP64 else "f32 velocities, f64 moments"
+    rb = 8 if prec == T.FP64 else 4
     if workload == "stationary":
-        return (StationaryShock(4000, 2500, precision=T.FP32_MIXED, seed=seed, order="adaptive"), 4,
-                "f32 velocities, f64 moments")
+        return StationaryShock(4000, 2500, precision=prec, seed=seed, order="adaptive"), rb, label
     if workload == "shock":
-        return ShockTubes(EPS, N_CELLS, MEAN, precision=T.FP64, seed=seed, order="adaptive"), 8, "f64"
+        return ShockTubes(EPS, N_CELLS, MEAN, precision=prec, seed=seed, order="adaptive"), rb, label
     if workload == "batched":
-        return BatchedRelaxation(precision=T.FP32_MIXED, seed=seed, order="adaptive"), 4, "f32 velocities, f64 moments"
-    return HomogeneousBKW(100000, precision=T.FP64, seed=seed), 8, "f64"
+        return BatchedRelaxation(precision=prec, seed=seed, order="adaptive"), rb, label
+    return HomogeneousBKW(100000, precision=prec, seed=seed), rb, label
 
 
 def time_steps(sim, K, flush, stats=None):
@@ -352,34 +398,85 @@ def time_graph_steps(sim, K, flush, stats):
     return np.zeros(K), co
 
 
-def compare_forms(flush, steps=60, warm=5):
-    """The plain single-problem FP64 form (one tube alone) against the batched
-    FP32-mixed form (the four tubes in one launch), on the same GPU, with the
-    moment difference between the forms after the same number of steps."""
+def gpu_moments(sim):
     import torch
     from paper_1009_2768_gb300 import trmc as T
-    from paper_1009_2768_gb300.workloads import ShockTubes
-    out = {}
-    temps = {}
-    for name, eps, prec in (("fp64_single_tube", (1e-2,), T.FP64), ("fp32_batched_tubes", EPS, T.FP32_MIXED)):
-        sim = ShockTubes(eps, N_CELLS, MEAN, precision=prec, seed=7)
-        for _ in range(warm):
-            sim.step()
-        tr, co = time_steps(sim, steps, flush)
-        T.trmc_check(sim.ctx)
-        out[name] = {"value": sim.n_particles / ((tr + co).mean() / 1e3), "unit": METRIC,
-                     "ms_per_step": float((tr + co).mean()), "particles": sim.n_particles}
-        mom = torch.zeros((sim.state.n_cells, T.MOM_COLS), dtype=torch.float64, device="cuda")
-        T.trmc_moments(sim.ctx, sim.state, mom)
-        temps[name] = mom[:N_CELLS, 5].cpu().numpy()        # the eps = 1e-2 tube's temperature profile
-        if name == "fp32_batched_tubes":
-            temps[name] = mom[N_CELLS:2 * N_CELLS, 5].cpu().numpy()
-        sim.close()
-    a, b = temps["fp64_single_tube"], temps["fp32_batched_tubes"]
-    out["moment_error"] = {"what": "L1 relative difference of the eps=1e-2 tube's temperature profile, FP32-mixed "
-                                   "batched vs FP64 single, same seed and step count (statistical noise included)",
-                           "value": float(np.abs(a - b).sum() / np.abs(a).sum()), "steps": warm + steps}
-    return out
+    mom = torch.zeros((sim.state.n_cells, T.MOM_COLS), dtype=torch.float64, device="cuda")
+    T.trmc_moments(sim.ctx, sim.state, mom)
+    return mom.cpu().numpy()
+
+
+def l1_rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    ok = np.isfinite(a) & np.isfinite(b)
+    den = np.abs(b[ok]).sum()
+    return float(np.abs(a[ok] - b[ok]).sum() / den) if den > 0 else 0.0
+
+
+def moment_measure(workload, got, ref, init):
+    """The moment error of one workload (per-cell moment tables
+    [N, rho, u, T, P_xx, M_4, E, max|v|^2]): density and temperature
+    profiles of the 1D problems (interior cells), the anisotropy
+    (P_xx - T)/T per cell of the batched relaxation relative to its initial
+    size, the fourth moment of the BKW cell."""
+    if workload in ("stationary", "shock"):
+        sl = slice(1, -1) if workload == "stationary" else slice(None)
+        return {"rho_L1": l1_rel(got[sl, 1], ref[sl, 1]), "T_L1": l1_rel(got[sl, 5], ref[sl, 5])}
+    if workload == "batched":
+        an = lambda m: (m[:, 6] - m[:, 5]) / m[:, 5]
+        return {"aniso_L1": float(np.abs(an(got) - an(ref)).sum() / np.abs(an(init)).sum())}
+    return {"M4_abs": float(abs(got[0, 7] - ref[0, 7])), "M4": float(got[0, 7])}
+
+
+MEASURE_TEXT = {
+    "stationary": "L1 relative difference of the interior cells' density and temperature profiles",
+    "shock": "L1 relative difference of the four tubes' density and temperature profiles",
+    "batched": "sum over cells of |a_gpu - a_oracle| / sum of |a_initial|, a = (P_xx - T)/T per cell",
+    "bkw": "|M_4 difference| of the cell (M_4 = <|v|^4>)",
+}
+
+
+def oracle_compare(workload, precision, steps, threads, flush=None, seed=0):
+    """The GPU form of `workload` at `precision` and the FP64 oracle step the
+    same initial state (the GPU's own initial data, copied) for `steps`
+    steps with the same keys; the oracle with the next seed gives the Monte
+    Carlo noise floor of the same measure.  Also times the GPU form (median
+    step, CUDA events, L2 flushed before each step) and the oracle."""
+    import torch
+    from paper_1009_2768_gb300 import trmc as T
+    sim, rb, label = make_sim(workload, seed, precision)
+    if workload in LAUNCH:
+        T.trmc_set_collide_launch(sim.ctx, *LAUNCH[workload])
+    from oracle.stepper import OracleSim
+    orc, orc_b = OracleSim(sim, seed), OracleSim(sim, seed + 1)
+    init = gpu_moments(sim)
+    ms = []
+    for _ in range(steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        if flush is not None:
+            flush.zero_()
+        sim.step(events=ev)
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[2]))
+    T.trmc_check(sim.ctx)
+    got = gpu_moments(sim)
+    n = sim.n_particles
+    sim.close()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        orc.step(threads)
+    t_orc = time.perf_counter() - t0
+    ref = orc.moments()
+    for _ in range(steps):
+        orc_b.step(threads)
+    other = orc_b.moments()
+    step_ms = float(np.median(ms))
+    return {"precision": label, "steps": steps,
+            "error": moment_measure(workload, got, ref, init),
+            "noise_floor": moment_measure(workload, other, ref, init),
+            "gpu": {"value": n / (step_ms / 1e3), "unit": METRIC, "ms_per_step": step_ms, "particles": n},
+            "oracle": {"value": orc.n * steps / t_orc, "unit": METRIC, "seconds": t_orc, "steps": steps,
+                       "particles": orc.n, "threads": threads}}
 
 
 def ours(args):
@@ -490,22 +587,32 @@ def ours(args):
         e2e = {"value": n * world * Ke / (e_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": h2d, "steps": Ke}
 
-    cpu = None
+    # the moment error against the FP64 oracle (same initial state and keys,
+    # COMPARE_STEPS steps), the oracle's own rate on that sample (the CPU
+    # baseline), and the other precision's form of the same workload
+    cpu, moment_error, forms = None, None, None
     if rank == 0 and world == 1 and not args.no_cpu:
         from oracle.build import build_oracle
         build_oracle()
-        threads = os.cpu_count() or 1
-        if args.workload == "shock":
-            rate, nn, done, el = oracle_tube_rate(N_CELLS, MEAN, 1000, threads, budget_s=15.0)
-            cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
-                   "sample": f"one full tube (eps 1e-2, {nn} particles), {done} steps in {el:.1f} s"}
-        else:
-            rate, nn, done, el, desc, used = oracle_workload_rate(args.workload, threads)
-            cpu = {"value": rate, "unit": METRIC, "cores": used, "kind": "oracle", "sample": desc}
-
-    forms = None
-    if rank == 0 and args.workload == "shock" and not args.no_forms:
-        forms = compare_forms(flush)
+        threads = 1 if args.workload == "bkw" else (os.cpu_count() or 1)
+        own = oracle_compare(args.workload, None, COMPARE_STEPS, threads, flush)
+        o = own["oracle"]
+        cpu = {"value": o["value"], "unit": METRIC, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
+               "sample": f"the whole workload ({o['particles']} particles) from the GPU's initial state, "
+                         f"{o['steps']} steps in {o['seconds']:.1f} s"}
+        moment_error = {"what": f"{MEASURE_TEXT[args.workload]}, GPU {own['precision']} vs the FP64 CPU oracle "
+                                f"from the same initial state with the same keys, after {COMPARE_STEPS} steps; "
+                                f"noise_floor: the same measure between the oracle and the oracle with other keys",
+                        "error": own["error"], "noise_floor": own["noise_floor"], "steps": COMPARE_STEPS}
+        forms = {"timed_form": {"precision": own["precision"], "value": own["gpu"]["value"],
+                                "ms_per_step": own["gpu"]["ms_per_step"], "error": own["error"]}}
+        if not args.no_forms:
+            other = T.FP64 if args.workload in ("stationary", "batched") else T.FP32_MIXED
+            alt = oracle_compare(args.workload, other, COMPARE_STEPS, threads, flush)
+            forms["fp64_form" if other == T.FP64 else "fp32_mixed_form"] = {
+                "precision": alt["precision"], "value": alt["gpu"]["value"], "ms_per_step": alt["gpu"]["ms_per_step"],
+                "error": alt["error"], "noise_floor": alt["noise_floor"],
+                "note": f"same workload, {COMPARE_STEPS} eager steps from its initial state, median step time"}
 
     if rank == 0:
         print(json.dumps({
@@ -517,7 +624,7 @@ def ours(args):
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
                        "cuda_graph": args.workload == "batched",
                        "collide_launch": launch},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "moment_error": moment_error,
             "gpu_launches": sim.launches_per_step * K, "clocks": clk, "forms": forms,
             "step_stats": {k: st[k] / K for k in ("collisions", "dummy", "maxwell", "changed", "passes")},
             "wall_s": t_wall}))
@@ -526,25 +633,64 @@ def ours(args):
         dist.destroy_process_group()
 
 
+def served_vs_oracle(reqs, precision, seed, threads, per_kind=1):
+    """The smallest completed requests of each kind against the FP64 oracle:
+    the request's initial state is built again (it is deterministic in the
+    request id and seed), the oracle steps it as many steps as the request
+    ran, with the same keys and with the next seed (the noise floor), and
+    the served moment table is compared with both."""
+    from oracle.stepper import OracleSim
+    from paper_1009_2768_gb300 import trmc as T
+    from paper_1009_2768_gb300.serving import shock_mean
+    from paper_1009_2768_gb300.workloads import BatchedRelaxation, ShockTubes
+    rows = []
+    for kind in ("shock", "relax"):
+        done = sorted([r for r in reqs if r.kind == kind and r.result is not None and r.error is None],
+                      key=lambda r: r.particles)[:per_kind]
+        for r in done:
+            ctx = T.trmc_create(precision, seed, 64 << 20)
+            if kind == "shock":
+                sim = ShockTubes((r.eps,), n_cells=len(r.counts), mean_per_cell=shock_mean(r), precision=precision,
+                                 seed=seed, ctx=ctx, problem_base=r.rid)
+            else:
+                sim = BatchedRelaxation(counts=r.counts, eps_lo=r.eps, eps_hi=r.eps, precision=precision, seed=r.rid,
+                                        ctx=ctx, problem_base=r.rid, problem_per_cell=False)
+            orc, alt = OracleSim(sim, seed), OracleSim(sim, seed + 1)
+            T.trmc_destroy(ctx)
+            init = orc.moments()
+            for _ in range(r.steps):
+                orc.step(threads)
+                alt.step(threads)
+            ref, oth = orc.moments(), alt.moments()
+            wl = "shock" if kind == "shock" else "batched"
+            rows.append({"rid": r.rid, "kind": kind, "particles": r.particles, "steps": r.steps,
+                         "t_reached": r.t_reached, "error": moment_measure(wl, r.result, ref, init),
+                         "noise_floor": moment_measure(wl, oth, ref, init)})
+    return rows
+
+
 def serving_bench(args):
-    """Rate sweep of the continuous-batching serving loop.  Every request's
-    latency runs from its arrival to its moments table landing in host
-    memory: set-up of its cell tables (host -> device), its steps, the
-    moments kernel and the copy back."""
+    """Rate sweep of the continuous-batching serving loop.  Every request is
+    a solve to its physical end time (shock tubes to t = 0.2, relaxations to
+    t = 1; --req-steps K runs K steps instead), and its latency runs from its
+    arrival to its moments table landing in host memory: set-up of its cell
+    tables (host -> device), its steps, the moments kernel and the copy
+    back."""
     import torch
     from paper_1009_2768_gb300 import build, synth
     from paper_1009_2768_gb300 import trmc as T
-    from paper_1009_2768_gb300.serving import GpuEngine, ServingLoop, requests_from, summary
+    from paper_1009_2768_gb300.serving import T_END, GpuEngine, ServingLoop, requests_from, summary
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     build.build()
+    steps = args.req_steps or None
     budget = int(args.budget_gb * (1 << 30))
     eng = GpuEngine(n_slots=args.slots, precision=T.FP32_MIXED, seed=rank, workspace_bytes=512 << 20,
                     chunk=args.chunk, depth=2)
     rates = [float(r) for r in args.rates.split(",")]
     # warm-up: a few small requests through the same engine (allocator, module load, pinned pool)
     warm = requests_from(synth.poisson_requests(max(args.warmup, 3), 1e4, n_hi=1_000_000, g=synth.rng(99)),
-                         steps=args.req_steps, first_id=1 << 20)
+                         steps=steps, first_id=1 << 20, t_end={"shock": 0.01})
     ServingLoop(eng, budget - eng.fixed_bytes).run(warm)
     clocks = Clocks(local)
     clocks.start()
@@ -553,7 +699,7 @@ def serving_bench(args):
     t_wall = time.perf_counter()
     for i, rate in enumerate(rates):
         n_req = args.requests or int(min(48, max(8, 8 * rate)))
-        reqs = requests_from(synth.poisson_requests(n_req, rate, g=synth.rng(1000 * rank + i)), steps=args.req_steps,
+        reqs = requests_from(synth.poisson_requests(n_req, rate, g=synth.rng(1000 * rank + i)), steps=steps,
                              first_id=rid)
         rid += n_req
         torch.cuda.synchronize()
@@ -564,44 +710,43 @@ def serving_bench(args):
         s.update(rate=rate, requests=n_req, resident_peak_gb=(loop.peak_bytes + eng.fixed_bytes) / 2 ** 30,
                  torch_peak_gb=torch.cuda.max_memory_allocated() / 2 ** 30,
                  mean_particles=float(np.mean([r.particles for r in out])),
+                 mean_steps=float(np.mean([r.steps for r in out if r.done is not None])),
                  errors=[r.error for r in out if r.error][:3])
         sweep.append(s)
         last = (i, n_req, rid - n_req, out)
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     eng.close()
-    # The plain single-problem FP64 form on the same stream as the highest rate:
-    # one slot, FP64 contexts, the same requests (same problem ids and seed), so
-    # its latencies and throughput stand beside the served FP32-mixed ones, and
-    # the moment tables of the two forms give their difference (Monte Carlo
-    # noise included: the two forms draw their trees from different arithmetic).
+    # The plain single-problem FP64 form on the first requests of the highest
+    # rate's stream: one slot, FP64 contexts, the same requests (same problem
+    # ids and seed), so its latencies and throughput stand beside the served
+    # FP32-mixed ones; both forms' moment tables are compared with the FP64
+    # oracle on the smallest requests of each kind.
     i, n_req, first, out32 = last
-    reqs64 = requests_from(synth.poisson_requests(n_req, rates[i], g=synth.rng(1000 * rank + i)),
-                           steps=args.req_steps, first_id=first)
+    n64 = min(n_req, args.fp64_requests)
+    reqs64 = requests_from(synth.poisson_requests(n_req, rates[i], g=synth.rng(1000 * rank + i))[:n64],
+                           steps=steps, first_id=first)
     eng64 = GpuEngine(n_slots=1, precision=T.FP64, seed=rank, workspace_bytes=512 << 20, chunk=args.chunk, depth=2)
     out64 = ServingLoop(eng64, budget - eng64.fixed_bytes).run(reqs64)
     eng64.close()
     s64 = summary(out64)
     svc = np.array([(r.done - r.admitted) * 1e3 for r in out64 if r.done is not None and r.error is None])
-    by_id = {r.rid: r for r in out32 if r.result is not None}
-    diffs = []
-    for r in out64:
-        a = by_id.get(r.rid)
-        if r.result is None or a is None or a.result.shape != r.result.shape:
-            continue
-        t32, t64 = a.result[:, 5], r.result[:, 5]
-        ok = np.isfinite(t32) & np.isfinite(t64) & (np.abs(t64) > 0)
-        if ok.any():
-            diffs.append(float(np.abs(t32[ok] - t64[ok]).sum() / np.abs(t64[ok]).sum()))
-    fp64_single = {"rate": rates[i], "slots": 1, "p50_ms": s64.get("p50_ms"), "p99_ms": s64.get("p99_ms"),
+    moment_error = None
+    if rank == 0 and not args.no_cpu:
+        from oracle.build import build_oracle
+        build_oracle()
+        threads = os.cpu_count() or 1
+        moment_error = {"what": "per compared request: density and temperature profiles (shock tubes) or the cells' "
+                                "anisotropy (relaxations) after the request's last step, served form vs the FP64 "
+                                "CPU oracle stepping the same initial state with the same keys; noise_floor: the "
+                                "oracle against itself with other keys",
+                        "fp32_mixed_served": served_vs_oracle(out32, T.FP32_MIXED, rank, threads),
+                        "fp64_single": served_vs_oracle(out64, T.FP64, rank, threads)}
+    fp64_single = {"rate": rates[i], "slots": 1, "requests": n64, "p50_ms": s64.get("p50_ms"),
+                   "p99_ms": s64.get("p99_ms"),
                    "service_p50_ms": float(np.percentile(svc, 50)) if svc.size else None,
                    "service_p99_ms": float(np.percentile(svc, 99)) if svc.size else None,
-                   "particle_steps_per_s": s64.get("particle_steps_per_s"), "completed": s64.get("completed"),
-                   "moment_error": {"what": "per request, L1 relative difference of the cells' temperature "
-                                            "after the last step, FP32-mixed served vs FP64 single-problem, "
-                                            "same requests and seed (statistical noise included)",
-                                    "median": float(np.median(diffs)) if diffs else None,
-                                    "max": float(np.max(diffs)) if diffs else None, "requests": len(diffs)}}
+                   "particle_steps_per_s": s64.get("particle_steps_per_s"), "completed": s64.get("completed")}
     top = sweep[-1]
     value = top.get("particle_steps_per_s") or 0.0
     peak, peak_kind = peaks()
@@ -611,12 +756,16 @@ def serving_bench(args):
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.req_steps,
             "warmup": len(warm), "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 velocities, f64 moments", "data": "synthetic",
-            "config": {"workload": WORKLOADS["serving"], "rates_per_s": rates, "steps_per_request": args.req_steps,
+            "config": {"workload": WORKLOADS["serving"], "rates_per_s": rates,
+                       "requests": ("solves: shock tubes (400 cells, specular walls, CFL 0.5) to t = %g, "
+                                    "relaxations (dt 0.05) to t = %g" % (T_END["shock"], T_END["relax"]))
+                       if steps is None else f"{steps} steps each",
                        "slots": args.slots, "chunk": args.chunk, "budget_gb": args.budget_gb,
                        "l2": "requests far larger than L2 on average (mean 3.8e6 particles)",
                        "parallelism": f"replicas x{world}"},
             "serving": sweep,
             "fp64_single": fp64_single,
+            "moment_error": moment_error,
             "roofline": {"bound": "hbm", "kernel": "all kernels of the served mix", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": None},
@@ -637,10 +786,13 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--tune", action="store_true", help="choose the collide launch shape with the autotuner")
     ap.add_argument("--launch", default="", help="collide launch shape THREADSxCTAS_PER_SM (default: per workload)")
-    ap.add_argument("--workload", default="shock", choices=["shock", "batched", "bkw", "stationary", "serving"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=["stationary", "shock", "batched", "bkw", "serving"])
     ap.add_argument("--rates", default="1,10,50,200", help="serving: arrival rates (requests/s) to sweep")
     ap.add_argument("--requests", type=int, default=0, help="serving: requests per rate (default 8*rate in [8, 48])")
-    ap.add_argument("--req-steps", type=int, default=20, help="serving: time steps per request")
+    ap.add_argument("--req-steps", type=int, default=0,
+                    help="serving: time steps per request (0: each request is a solve to its physical end time)")
+    ap.add_argument("--fp64-requests", type=int, default=16,
+                    help="serving: requests of the highest rate run again as FP64 single-problem solves")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent requests (contexts + streams)")
     ap.add_argument("--chunk", type=int, default=4, help="serving: steps issued per chunk")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: HBM budget (GiB)")

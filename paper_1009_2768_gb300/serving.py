@@ -15,6 +15,12 @@ Layout of the loop:
 * Admission is first come, first served: the head of the queue enters when a
   slot is free and its resident bytes fit in what the budget has left.  A
   request larger than the whole budget is rejected, never queued.
+* A request is a solve to a physical end time t_end (or, if it names none,
+  a fixed number of steps): a homogeneous relaxation runs t_end / dt steps
+  of its fixed dt; a shock tube runs ceil(t_end / dt_0) steps, dt_0 its
+  first CFL step, which the GPU computes from the initial data and the
+  host reads back without blocking; the simulated time actually reached
+  (the sum of the CFL steps) comes back with the result.
 * Each admitted request advances in chunks of steps issued on its stream,
   at most `depth` chunks ahead of the GPU, so the host keeps every active
   request fed without blocking on any of them.  After the last step the
@@ -37,6 +43,9 @@ import numpy as np
 from . import trmc as T
 
 MEAN_RELAX_CELL = (8192 - 64) / np.log(8192 / 64)     # mean of a log-uniform cell size in [64, 8192]
+SHOCK_CELLS = 400          # cells of a shock-tube request on [0, 1] (the shock-tube workload's geometry)
+RELAX_DT = 0.05            # time step of a relaxation request
+T_END = {"shock": 0.2, "relax": 1.0}   # end times of solve requests: Sec. 5.1's tube; relaxation to t = 1
 
 
 @dataclass
@@ -45,7 +54,7 @@ class Request:
     kind: str                  # "shock" (1D Riemann tube, specular walls) or "relax" (homogeneous cells)
     n_particles: int
     eps: float
-    steps: int
+    steps: int                 # time steps (fixed when t_end is None, else set once known)
     arrival: float = 0.0       # seconds after the loop starts
     admitted: float = None
     done: float = None
@@ -56,14 +65,21 @@ class Request:
     counts: np.ndarray = field(default=None, repr=False)   # particles per cell (set by plan())
     particles: int = 0         # particles actually placed (rounding of the cell layout)
     result: np.ndarray = field(default=None, repr=False)   # moments per cell after the last step
+    t_end: float = None        # a solve to this physical time (None: run `steps` steps)
+    t_reached: float = None    # simulated time after the last step (solves)
 
     @property
     def latency(self):
         return None if self.done is None else self.done - self.arrival
 
 
-def requests_from(stream, steps, first_id=0):
-    """Requests from the dicts of synth.poisson_requests."""
+def requests_from(stream, steps=None, first_id=0, t_end=None):
+    """Requests from the dicts of synth.poisson_requests: `steps` steps each,
+    or, with steps None, solves to the end time t_end[kind] (default T_END)."""
+    if steps is None:
+        ends = dict(T_END, **(t_end or {}))
+        return [Request(first_id + i, d["kind"], d["n_particles"], d["eps"], 0, d["arrival"], t_end=ends[d["kind"]])
+                for i, d in enumerate(stream)]
     return [Request(first_id + i, d["kind"], d["n_particles"], d["eps"], steps, d["arrival"])
             for i, d in enumerate(stream)]
 
@@ -78,22 +94,29 @@ def _alloc(nbytes):
     return (nbytes + (2 << 20) - 1) // (2 << 20) * (2 << 20)
 
 
+def shock_mean(req):
+    """Mean particles per cell of a shock-tube request."""
+    return req.n_particles / SHOCK_CELLS
+
+
 def plan(req):
     """Fix the cell layout of a request on the host (deterministic in its
-    id): a shock tube of 500 particles per cell on average, density-weighted
+    id): a shock tube of SHOCK_CELLS cells, its particles density-weighted
     across the interface, or homogeneous cells of log-uniform size in
-    [64, 8192].  Sets req.counts and req.particles."""
+    [64, 8192].  Sets req.counts and req.particles (and, for a relaxation
+    solve, req.steps)."""
     from . import synth
     if req.counts is None:
         if req.kind == "shock":
-            nc = max(2, int(round(req.n_particles / 500.0)))
-            req.counts = synth.shock_tube_counts(nc, 500)
+            req.counts = synth.shock_tube_counts(SHOCK_CELLS, shock_mean(req))
         elif req.kind == "relax":
             nc = max(1, int(round(req.n_particles / MEAN_RELAX_CELL)))
             req.counts = synth.loguniform_ints(nc, 64, 8192, g=synth.rng((1 << 40) + req.rid))
         else:
             raise ValueError(f"unknown request kind {req.kind!r}")
         req.particles = int(req.counts.sum())
+        if req.kind == "relax" and req.t_end is not None:
+            req.steps = int(np.ceil(req.t_end / RELAX_DT - 1e-9))
     return req
 
 
@@ -111,6 +134,7 @@ def footprint(kind, n_cells, n_particles, precision=T.FP32_MIXED):
         b += 2 * _alloc(8 * (nc + 1))                                # cell_start, cell_start_alt
         b += _alloc(8 * tubes) + _alloc(88 * tubes)                  # dt, domains
         b += _alloc(8 * 3 * nc) + _alloc(8 * (nc + 1))               # the sort's counters in the context
+        b += 3 * _alloc(16)                                          # a solve's first CFL speed, clock and read-back
     else:
         b += _alloc(3 * n * rb)
         b += _alloc(8 * (nc + 1))
@@ -238,35 +262,78 @@ class _GpuJob:
         self.ctx = ctx
         plan(req)
         nc = len(req.counts)
+        self.dt0 = None
+        self.t_sim = None
         with torch.cuda.stream(stream):
             if req.kind == "shock":
-                self.sim = ShockTubes((req.eps,), n_cells=nc, mean_per_cell=500, precision=engine.precision,
-                                      seed=engine.seed, ctx=ctx, problem_base=req.rid)
+                self.sim = ShockTubes((req.eps,), n_cells=nc, mean_per_cell=shock_mean(req),
+                                      precision=engine.precision, seed=engine.seed, ctx=ctx, problem_base=req.rid)
+                if req.t_end is not None:
+                    # the first CFL step from the initial data, read back without blocking
+                    vm = self.sim.state.cell_vmax2[:nc].max()
+                    self.vm_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
+                    self.vm_host.copy_(vm.reshape(1), non_blocking=True)
+                    self.dt0 = torch.cuda.Event()
+                    self.dt0.record(stream)
+                    self.t_sim = torch.zeros(1, dtype=torch.float64, device="cuda")
             else:
                 self.sim = BatchedRelaxation(counts=req.counts, eps_lo=req.eps, eps_hi=req.eps,
                                              precision=engine.precision, seed=req.rid, ctx=ctx,
-                                             problem_base=req.rid, problem_per_cell=False)
+                                             problem_base=req.rid, problem_per_cell=False, dt=RELAX_DT)
         assert self.sim.n_particles == req.particles
         self.issued = 0
         self.inflight = collections.deque()
         self.final = None
+        self.t_check = None
+
+    def _steps_known(self):
+        if self.dt0 is None:
+            return True
+        if not self.dt0.query():
+            return False
+        dt = self.sim.cfl * (1.0 / len(self.req.counts)) / float(np.sqrt(self.vm_host.item()))
+        self.req.steps = max(1, int(np.ceil(self.req.t_end / dt - 1e-9)))
+        self.dt0 = None
+        return True
 
     def pump(self):
         import torch
         issued = False
         while self.inflight and self.inflight[0].query():
             self.inflight.popleft()
+        if not self._steps_known():
+            return False
         with torch.cuda.stream(self.stream):
             while len(self.inflight) < self.engine.depth and self.issued < self.req.steps:
                 k = min(self.engine.chunk, self.req.steps - self.issued)
                 for _ in range(k):
                     self.sim.step()
+                    if self.t_sim is not None:
+                        self.t_sim += self.sim.dt[0]
                 self.issued += k
                 ev = torch.cuda.Event()
                 ev.record(self.stream)
                 self.inflight.append(ev)
                 issued = True
-            if self.issued == self.req.steps and self.final is None:
+            if self.issued == self.req.steps and self.final is None and self.t_sim is not None:
+                # a solve ends at the first step that reaches t_end: read the
+                # simulated time (and the last CFL step) back without blocking
+                # and, if the CFL steps shrank on the way, add the steps still
+                # missing
+                if self.t_check is None:
+                    self.t_host = torch.empty(2, dtype=torch.float64, pin_memory=True)
+                    self.t_host.copy_(torch.cat([self.t_sim, self.sim.dt[:1]]), non_blocking=True)
+                    self.t_check = torch.cuda.Event()
+                    self.t_check.record(self.stream)
+                    return True
+                if not self.t_check.query():
+                    return issued
+                t, dt = (float(x) for x in self.t_host.tolist())
+                if t < self.req.t_end:
+                    self.req.steps += max(1, int(np.ceil((self.req.t_end - t) / dt - 1e-9)))
+                    self.t_check = None
+                    return True
+            if self.issued == self.req.steps and self.final is None and (self.t_sim is None or self.t_check is not None):
                 st = self.sim.state
                 self.out = torch.empty((st.n_cells, T.MOM_COLS), dtype=torch.float64, device="cuda")
                 T.trmc_moments(self.ctx, st, self.out, stream=self.stream)
@@ -285,6 +352,8 @@ class _GpuJob:
         except T.TrmcError as e:
             self.req.error = str(e)
         self.req.result = self.host.numpy().copy()
+        if self.req.t_end is not None:
+            self.req.t_reached = float(self.t_host[0]) if self.t_sim is not None else self.req.steps * RELAX_DT
         return True
 
 

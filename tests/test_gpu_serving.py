@@ -35,15 +35,15 @@ def test_alone_equals_in_mix():
 def test_served_result_equals_direct_stepping():
     need_gpu()
     ensure_built()
-    from paper_1009_2768_gb300.serving import Request, plan, serve
+    from paper_1009_2768_gb300.serving import Request, plan, serve, shock_mean
     from paper_1009_2768_gb300.workloads import BatchedRelaxation, ShockTubes
     for rid, (k, n, e) in enumerate(SPECS[:2]):
         req = plan(Request(rid, k, n, e, steps=5))
         serve([req], n_slots=1, workspace_bytes=64 << 20, chunk=2)
         ctx = T.trmc_create(T.FP32_MIXED, 0, 64 << 20)
         if k == "shock":
-            sim = ShockTubes((e,), n_cells=len(req.counts), mean_per_cell=500, precision=T.FP32_MIXED, ctx=ctx,
-                             problem_base=rid)
+            sim = ShockTubes((e,), n_cells=len(req.counts), mean_per_cell=shock_mean(req), precision=T.FP32_MIXED,
+                             ctx=ctx, problem_base=rid)
         else:
             sim = BatchedRelaxation(counts=req.counts, eps_lo=e, eps_hi=e, precision=T.FP32_MIXED, seed=rid, ctx=ctx,
                                     problem_base=rid, problem_per_cell=False)

@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 from paper_1009_2768_gb300 import synth
-from paper_1009_2768_gb300.serving import Admission, Request, ServingLoop, footprint, plan, summary
+from paper_1009_2768_gb300.serving import (RELAX_DT, SHOCK_CELLS, T_END, Admission, Request, ServingLoop, footprint,
+                                           plan, requests_from, summary)
 
 
 class Clock:
@@ -154,7 +155,13 @@ def test_plan_and_footprint():
     assert np.array_equal(a.counts, b.counts) and a.particles == int(a.counts.sum())
     assert a.counts.min() >= 64 and a.counts.max() <= 8192
     s = plan(Request(8, "shock", 1_000_000, 1e-2, 1))
-    assert len(s.counts) == 2000 and abs(s.particles - 1_000_000) < 2000
+    assert len(s.counts) == SHOCK_CELLS and abs(s.particles - 1_000_000) < SHOCK_CELLS
+    # a solve request: relaxation to t_end = 1 runs 20 steps of dt 0.05; a shock
+    # tube's step count waits for its first CFL step (set on the GPU)
+    r = plan(Request(9, "relax", 300_000, 1e-2, 0, t_end=T_END["relax"]))
+    assert r.steps == round(T_END["relax"] / RELAX_DT) == 20
+    sol = requests_from(synth.poisson_requests(6, 10.0, g=synth.rng(3)))
+    assert all(q.t_end == T_END[q.kind] for q in sol)
     # resident bytes grow with the particle count and cover the FP32 particle arrays
     f1 = footprint("shock", 2000, 1_000_000)
     assert f1 >= 2 * (12 + 4) * 1_000_000
