@@ -72,7 +72,7 @@ NCU_TRAFFIC = {
 
 # Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
 # runtime.autotune_collide's candidates on GB300 (--tune measures them again).
-LAUNCH = {"shock": (128, 3), "stationary": (256, 2), "batched": (256, 2), "bkw": (128, 4)}
+LAUNCH = {"shock": (128, 3), "stationary": (256, 2), "batched": (256, 2), "bkw": (256, 2)}
 
 
 def collide_sha():
@@ -685,7 +685,7 @@ def serving_bench(args):
     build.build()
     steps = args.req_steps or None
     budget = int(args.budget_gb * (1 << 30))
-    eng = GpuEngine(n_slots=args.slots, precision=T.FP32_MIXED, seed=rank, workspace_bytes=512 << 20,
+    eng = GpuEngine(n_slots=args.slots, precision=T.FP32_MIXED, seed=rank, workspace_bytes=1 << 30,
                     chunk=args.chunk, depth=2)
     rates = [float(r) for r in args.rates.split(",")]
     # warm-up: a few small requests through the same engine (allocator, module load, pinned pool)
@@ -726,7 +726,7 @@ def serving_bench(args):
     n64 = min(n_req, args.fp64_requests)
     reqs64 = requests_from(synth.poisson_requests(n_req, rates[i], g=synth.rng(1000 * rank + i))[:n64],
                            steps=steps, first_id=first)
-    eng64 = GpuEngine(n_slots=1, precision=T.FP64, seed=rank, workspace_bytes=512 << 20, chunk=args.chunk, depth=2)
+    eng64 = GpuEngine(n_slots=1, precision=T.FP64, seed=rank, workspace_bytes=2 << 30, chunk=args.chunk, depth=2)
     out64 = ServingLoop(eng64, budget - eng64.fixed_bytes).run(reqs64)
     eng64.close()
     s64 = summary(out64)

@@ -100,6 +100,17 @@ trmc_status trmc_create(trmc_ctx **out, int32_t precision, uint64_t seed, size_t
     if (e != cudaSuccess) { cudaFree(ctx->workspace); delete ctx; return TRMC_ERR_CUDA; }
     ctx->status = reinterpret_cast<int *>(ctx->workspace);
     ctx->tickets = reinterpret_cast<unsigned int *>(ctx->workspace + 64);
+    // the largest cell of the last collide launch, written by the device into
+    // host-mapped memory and read by the next launch without a copy
+    unsigned int *h = nullptr;
+    e = cudaHostAlloc(reinterpret_cast<void **>(&h), sizeof(unsigned int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *h = ~0u;
+        e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&ctx->n_max_dev), h, 0);
+        if (e != cudaSuccess) { cudaFreeHost(h); h = nullptr; ctx->n_max_dev = nullptr; }
+    }
+    if (e != cudaSuccess) { cudaFree(ctx->workspace); delete ctx; return TRMC_ERR_CUDA; }
+    ctx->n_max_host = h;
     ctx->slabs = ctx->workspace + kControlBytes;
     ctx->slabs_bytes = workspace_bytes;
     *out = ctx;
@@ -110,6 +121,7 @@ trmc_status trmc_destroy(trmc_ctx *ctx)
 {
     if (!ctx) return TRMC_ERR_ARG;
     if (ctx->workspace) cudaFree(ctx->workspace);
+    if (ctx->n_max_host) cudaFreeHost(const_cast<unsigned int *>(ctx->n_max_host));
     if (ctx->tr_counts) cudaFree(ctx->tr_counts);
     if (ctx->tr_dom) cudaFree(ctx->tr_dom);
     delete ctx;

@@ -68,7 +68,8 @@ struct Args {
     int64_t *report;
     trmc_stats *stats;
     int *status;
-    unsigned int *tickets;
+    unsigned int *tickets;           // [0] next cell, [1] CTAs done, [2] largest cell so far
+    volatile unsigned int *n_max_host;   // NULL, or host-mapped: the last launch's largest cell
     char *slabs;
     size_t slab_bytes;
     int smem_bytes;
@@ -95,9 +96,14 @@ struct Sh {
     double alpha, dt, eps, rho_scale;
     uint64_t problem, lcell;
     U64x4 keyP0;                     // key of the pass's role permutation
-    Real *V;
-    uint32_t *flags;
-    int32_t *inv[2];
+    // Velocities being changed: with `full` every particle staged, Vc[slot];
+    // otherwise only the changed ones (pass-0 ranks from n0 on), compact,
+    // Vc[rank - n0].  [3][nVc]
+    Real *Vc;
+    int32_t nVc, full;
+    uint32_t *flags;                 // staged whole: the changed slots (the write-back is coalesced)
+    int32_t *inv0;                   // pass 0: slot of each rank (the ranks from n0 on are filled)
+    int32_t *posA[2];                // passes >= 1: position in Vc of each rank (ping-pong between passes)
     int32_t *Mt, *St;
     Real *IBuf, *OBuf;
     double *ILBuf, *OLBuf;           // TRMC-WB: tree length of every consumer slot / output
@@ -118,6 +124,7 @@ struct Sh {
     Real *prnd;
     int32_t *ext;                    // TRMC-WB: slots of rejected outputs, appended to the pool
     char *smem_rest, *slab_rest;
+    char *slab_hi;                   // end of the slab bytes this cell wrote (discarded after it)
     size_t smem_rest_cap, slab_rest_cap;
     char *pass_smem, *pass_slab;
     size_t pass_smem_cap, pass_slab_cap;
@@ -542,11 +549,23 @@ __device__ __forceinline__ void raise_status(int *status, int code, int cell)
     if (atomicCAS(status, 0, code) == 0) status[1] = cell;
 }
 
-template <typename Real>
-__device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigned char *dsm, char *slab, int cell,
-                             int (&cnt)[3])
+// One cell, by the whole CTA; returns the thread's collision counts
+// (collisions, dummy, exceed).
+// Mode kWhole: the cell is staged whole, in shared memory, or in the CTA's
+// slab when it does not fit.  Mode kDual: a cell that fits in shared memory is
+// staged whole, a larger one compact (only the particles that change).  The
+// two modes are separate kernels: the compact path costs the whole path a few
+// per cent in registers and code size, so a launch takes it only when it has
+// a cell too large for shared memory.
+enum { kWhole = 0, kDual = 1 };
+struct Counts { int c[3]; };
+
+template <typename Real, int Mode>
+__device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigned char *dsm,
+                                               char *slab, int cell)
 {
     const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
+    int cnt[3] = {0, 0, 0};
     Real *gx = static_cast<Real *>(a.vx), *gy = static_cast<Real *>(a.vy), *gz = static_cast<Real *>(a.vz);
     const int64_t base = a.cell_start[cell];
     const int n = int(a.cell_start[cell + 1] - base);
@@ -577,23 +596,37 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         sh.n0_prev = 0; sh.D0_prev = 0; sh.nrej = 0;
         sh.dP[0] = sh.dP[1] = sh.dP[2] = 0.0; sh.dE = 0.0; sh.dS = 0.0;
         for (int j = 0; j < 4; ++j) sh.carry[j] = a.cell_carry ? a.cell_carry[4 * int64_t(cell) + j] : 0.0;
-        // persistent layout: V, flags, inv[2]
+        // persistent layout: a cell whose particles fit in shared memory with
+        // the slot table is staged whole (Vc, then inv0); a larger one keeps
+        // only inv0 and stages the particles that change once pass 0 has
+        // planned (the later passes' position tables follow when needed)
         char *smem = reinterpret_cast<char *>(dsm);
         size_t scap = size_t(a.smem_bytes);
         char *gs = slab;
         size_t gcap = a.slab_bytes;
-        const size_t pb = al16(3 * size_t(n) * sizeof(Real)) + al16(4 * size_t((n + 31) / 32)) + 2 * al16(4 * size_t(n));
-        char *p;
-        if (pb <= scap) { p = smem; smem += pb; scap -= pb; }
-        else if (pb <= gcap) { p = gs; gs += pb; gcap -= pb; }
-        else { p = nullptr; sh.skip = 1; }
-        if (p) {
-            sh.V = reinterpret_cast<Real *>(p); p += al16(3 * size_t(n) * sizeof(Real));
-            sh.flags = reinterpret_cast<uint32_t *>(p); p += al16(4 * size_t((n + 31) / 32));
-            sh.inv[0] = reinterpret_cast<int32_t *>(p); p += al16(4 * size_t(n));
-            sh.inv[1] = reinterpret_cast<int32_t *>(p);
+        const size_t pv = al16(3 * size_t(n) * sizeof(Real)), pb = al16(4 * size_t(n));
+        const size_t pf = al16(4 * size_t((n + 31) / 32));
+        sh.Vc = nullptr; sh.nVc = 0; sh.flags = nullptr; sh.full = 1;
+        char *p = nullptr;
+        if (pv + pf + pb <= scap) { p = smem; smem += pv + pf + pb; scap -= pv + pf + pb; }
+        else if (Mode == kWhole) {
+            if (pv + pf + pb <= gcap) { p = gs; gs += pv + pf + pb; gcap -= pv + pf + pb; }
+            else sh.skip = 1;
+        } else {
+            sh.full = 0;
+            if (pb <= scap) { p = smem; smem += pb; scap -= pb; }
+            else if (pb <= gcap) { p = gs; gs += pb; gcap -= pb; }
+            else sh.skip = 1;
         }
+        if (p && sh.full) {
+            sh.nVc = n;
+            sh.Vc = reinterpret_cast<Real *>(p);
+            sh.flags = reinterpret_cast<uint32_t *>(p + pv);
+            p += pv + pf;
+        }
+        sh.inv0 = reinterpret_cast<int32_t *>(p);
         sh.smem_rest = smem; sh.smem_rest_cap = scap; sh.slab_rest = gs; sh.slab_rest_cap = gcap;
+        sh.slab_hi = gs;
     }
     __syncthreads();
     if (n < 2 || sh.skip) {
@@ -619,10 +652,11 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             vm = block_max_nonneg(vm, sh.red);
             if (tid == 0) a.cell_vmax2[cell] = vm;
         }
-        return;
+        return Counts{{cnt[0], cnt[1], cnt[2]}};
     }
-    Real *Vx = sh.V, *Vy = sh.V + n, *Vz = sh.V + 2 * n;
-    const CellRng rng{a.seed, sh.problem, sh.lcell, step};
+    // the cell's random stream, rebuilt at each draw from shared memory (four
+    // 64-bit values held across the whole cell would cost registers)
+    auto rng = [&]() { return CellRng{a.seed, sh.problem, sh.lcell, step}; };
 
     // ---- 1. stage + moments -------------------------------------------------
     // (the indicator sums only for TRMC-RAD; the speed bound only for VHS; on
@@ -632,10 +666,14 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         const bool rad = prm.trunc == TRMC_TRUNC_RAD;
         const bool need_m4 = rad && prm.indicator == TRMC_IND_M4, need_pxx = rad && prm.indicator == TRMC_IND_PXX;
         const bool need_d2 = sh.alpha != 0.0;
-        // every particle is staged; the sums run over the canonical virtual
-        // warps (for 256 threads one per warp, as the particles are loaded)
+        // the particles are read from global memory and, for a cell staged
+        // whole, stored in shared memory (a larger cell stages the changed ones
+        // once the plan names them); the sums run over the canonical virtual
+        // warps (for 256 threads one per warp)
         const int nw = bs >> 5, warp = tid >> 5;
-        constexpr int U = 4;      // loads issued together, ahead of the stores they feed
+        const bool full = Mode == kWhole || sh.full;
+        Real *Vx = sh.Vc, *Vy = sh.Vc + n, *Vz = sh.Vc + 2 * n;
+        constexpr int U = 4;      // loads issued together, ahead of the sums they feed
         for (int vw = warp; vw < kVW; vw += nw) {
             Sum<Real> acc[5];
             for (int i0 = 32 * vw + lane; i0 < n; i0 += U * 32 * kVW) {
@@ -649,7 +687,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 for (int u = 0; u < U; ++u) {
                     const int i = i0 + u * 32 * kVW;
                     if (i < n) {
-                        Vx[i] = x[u]; Vy[i] = y[u]; Vz[i] = z[u];
+                        if (full) { Vx[i] = x[u]; Vy[i] = y[u]; Vz[i] = z[u]; }
                         acc[0].add(x[u]); acc[1].add(y[u]); acc[2].add(z[u]);
                         acc[3].add_sq3(x[u], y[u], z[u]);
                         if (need_m4) {
@@ -662,7 +700,8 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             if (need_m4) vw_put<5>(acc, sh.red, vw);
             else vw_put<4>(acc, sh.red, vw);
         }
-        for (int w = tid; w < (n + 31) >> 5; w += bs) sh.flags[w] = 0u;     // change flags, set by the roles
+        if (full)
+            for (int w = tid; w < (n + 31) >> 5; w += bs) sh.flags[w] = 0u;     // change flags, set after the plan
         // totals, and the mean velocity (warp 0 divides, once per cell)
         double s[5] = {0, 0, 0, 0, 0}, su[5];
         if (need_m4) {
@@ -680,16 +719,34 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         double t[1] = {0.0};
         double dmax = 0.0;
         if (need_d2 || need_pxx) {
+            // a second pass over the cell: from shared memory, or, for a cell
+            // not staged whole, from L2 (it was just read)
             for (int vw = warp; vw < kVW; vw += nw) {
                 Sum<Real> pxx[1];
-                for (int i = 32 * vw + lane; i < n; i += 32 * kVW) {
-                    const Real ax = Vx[i] - u0, ay = Vy[i] - u1, az = Vz[i] - u2;
+                auto dev = [&](Real x, Real y, Real z) {
+                    const Real ax = x - u0, ay = y - u1, az = z - u2;
                     if (need_d2) {
                         const Real q = ax * ax + ay * ay + az * az;
                         if constexpr (sizeof(Real) == 8) d2b = max(d2b, __double_as_longlong(q));
                         else d2 = fmaxf(d2, q);
                     }
                     if (need_pxx) pxx[0].add(ax * ax);
+                };
+                if (full) {
+                    for (int i = 32 * vw + lane; i < n; i += 32 * kVW) dev(Vx[i], Vy[i], Vz[i]);
+                } else {
+                    constexpr int U = 2;
+                    for (int i0 = 32 * vw + lane; i0 < n; i0 += U * 32 * kVW) {
+                        Real x[U], y[U], z[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int i = i0 + u * 32 * kVW;
+                            if (i < n) { x[u] = gx[base + i]; y[u] = gy[base + i]; z[u] = gz[base + i]; }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            if (i0 + u * 32 * kVW < n) dev(x[u], y[u], z[u]);
+                    }
                 }
                 vw_put<1>(pxx, sh.red, vw);
             }
@@ -719,9 +776,17 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
     // ---- pass loop (pass 0, then TRMC-RAD continuations) --------------------
     for (;;) {
         const int pass = sh.pass, warp = tid >> 5, npart = sh.npart;
-        int32_t *inv = sh.inv[pass & 1];
-        const int32_t *invp = sh.inv[(pass + 1) & 1];
+        // the roles write, for each rank from n0 on, the particle's slot
+        // (pass 0) or its position in Vc (later passes, from the previous
+        // pass's table: the participants of a continuation are the previous
+        // pass's thermalised set, ranks poolp.. of that pass)
+        int32_t *inv = pass == 0 ? sh.inv0 : sh.posA[pass & 1];
+        const int32_t *invp = sh.posA[(pass + 1) & 1];
         const int poolp = sh.n0_prev + sh.D0_prev;
+        auto role_of = [&](int i) -> int {
+            return pass == 0 ? i : pass == 1 ? (Mode == kWhole || sh.full ? sh.inv0[poolp + i] : poolp - sh.n0_prev + i)
+                                             : invp[poolp + i];
+        };
 
         // One attempt of the tree plan (warp 0) on depth sh.m_top, then, if the
         // trees find enough leaves, the layout of the pass's buffers; otherwise
@@ -793,7 +858,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     if (k0 >= 0 && __ffs(g0) - 1 == lane) atomicAdd(&row[k0], __popc(g0));
                     if (k1 >= 0 && __ffs(g1) - 1 == lane) atomicAdd(&row[k1], __popc(g1));
                     for (int g = (np >> 2) + lane; g < (Cn + 3) >> 2; g += 32) {
-                        const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
+                        const U64x4 w = rng().draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
                             if (4 * g + j < Cn) atomicAdd(&row[below(w.w[j], uint32_t(lv))], 1);
@@ -896,6 +961,15 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 // the arenas' bump pointers in registers while the buffers are laid out
                 char *ps = sh.pass_smem, *pg = sh.pass_slab;
                 size_t pcs = sh.pass_smem_cap, pcg = sh.pass_slab_cap;
+                if (Mode == kDual && !sh.full && pass == 0) {
+                    // persistent from here on: the changed particles' velocities;
+                    // later passes lay out after them
+                    sh.nVc = npart - n0;
+                    sh.Vc = static_cast<Real *>(take(ps, pcs, pg, pcg, 3 * size_t(sh.nVc + 1) * sizeof(Real)));
+                    if (!sh.Vc) sh.skip = 1;
+                    sh.posA[0] = sh.posA[1] = nullptr;
+                    sh.smem_rest = ps; sh.smem_rest_cap = pcs; sh.slab_rest = pg; sh.slab_rest_cap = pcg;
+                }
                 sh.IBuf = static_cast<Real *>(take(ps, pcs, pg, pcg,
                                                    3 * size_t(Dge1 + 1) * sizeof(Real)));
                 sh.OBuf = static_cast<Real *>(take(ps, pcs, pg, pcg,
@@ -947,6 +1021,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     }
                 }
                 sh.pass_smem = ps; sh.pass_slab = pg; sh.pass_smem_cap = pcs; sh.pass_slab_cap = pcg;
+                if (pg > sh.slab_hi) sh.slab_hi = pg;
                 if (!ok) sh.skip = 2;
                 if (pass == 0) sh.n0_first = n0;
             }
@@ -969,10 +1044,10 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         {
             const int lo = sh.lo, m = sh.m;
             for (int t = tid; t <= m - lo; t += bs)
-                sh.uSK[lo + t] = rng.draw(uint64_t(lo + t), 0, uint32_t(pass), TAG_SPLIT).w[0] >> 11;
+                sh.uSK[lo + t] = rng().draw(uint64_t(lo + t), 0, uint32_t(pass), TAG_SPLIT).w[0] >> 11;
             for (int j = tid; j < NLEV; j += bs) sh.Nq[j] = 0;
             if (tid < 3) sh.coin[tid] = 0u;
-            if (tid == bs - 1) sh.keyP0 = rng.draw(0, 0, uint32_t(pass), TAG_PERM0);
+            if (tid == bs - 1) sh.keyP0 = rng().draw(0, 0, uint32_t(pass), TAG_PERM0);
         }
         __syncthreads();
         int m_split;
@@ -1067,6 +1142,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     sh.Mt = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
                     sh.St = static_cast<int32_t *>(take(sh.pass_smem, sh.pass_smem_cap, sh.pass_slab, sh.pass_slab_cap, 4 * (T + 1)));
                     if (!sh.Mt || !sh.St) sh.skip = 1;
+                    if (sh.pass_slab > sh.slab_hi) sh.slab_hi = sh.pass_slab;
                 }
             }
             __syncthreads();
@@ -1087,7 +1163,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const uint64_t idx = kind == 0 ? uint64_t(lv) : kind == 1 ? 0ull : uint64_t(kind - 2);
                 const uint64_t aux = kind == 0 ? 0ull : uint64_t(lv);
                 const uint32_t tag = kind == 0 ? TAG_PARITY : kind == 1 ? TAG_PERMK : TAG_KSEL;
-                const U64x4 w = rng.draw(idx, aux, uint32_t(pass), tag);
+                const U64x4 w = rng().draw(idx, aux, uint32_t(pass), tag);
                 if (kind == 0) {
                     if ((w.w[0] >> 63) == 0) atomicOr(&sh.coin[lv >> 5], 1u << (lv & 31));   // u < 1/2
                 } else if (kind == 1) {
@@ -1099,121 +1175,149 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             }
         }
         __syncthreads();
-        if (warp == 0) plan_attempt();
         // 4. roles (the "random choice" of Alg. 4.3): a permutation pi of the
         //    participants gives slot pi^-1(r) the rank r.  Only ranks from n0 on
         //    (leaves, then the thermalised set) are ever looked up, so only they
         //    are computed, with the inverse permutation: the ranks from the
         //    level-0 quota on by warps 1.. while warp 0 plans (warp 0 afterwards
         //    in a single-warp CTA), those the leaf rule borrows from level 0
-        //    once the plan is known.
+        //    once the plan is known.  The plan is attempted once, and once more
+        //    after the leaf rule has lowered the depth (one call site: the
+        //    plan is long code, and one copy of it keeps the kernel small).
         Perm perm;
         perm.init(uint32_t(npart), sh.keyP0);
         const int nq0 = sh.Nq[0];
-        if (warp > 0 || bs == 32) {
-            const int t0 = bs == 32 ? tid : tid - 32, st = bs == 32 ? bs : bs - 32;
-            for (int r = nq0 + t0; r < npart; r += st) {
-                const int i = int(perm.inv(uint32_t(r)));
-                inv[r] = (pass == 0) ? i : invp[poolp + i];
-            }
-        }
-        __syncthreads();
-        if (!sh.skip && sh.cont) {
-            // The first plan needs more leaves than the participants can give.
-            // The rule then lowers the depth to just below one quota level
-            // after another; those depths follow from the quotas alone, so up
-            // to four warps test the next ones at once (feasibility only), and
-            // warp 0 then plans the first feasible one in full.
-            const int nsw = (bs >> 5) < 4 ? (bs >> 5) : 4;
-            auto feasible_at = [&](int ct) -> bool {
-                int32_t *Dw = reinterpret_cast<int32_t *>(sh.red) + warp * 130, *rw = Dw + NLEV;
-                for (int j = lane; j < NLEV; j += 32) Dw[j] = 0;
-                __syncwarp();
-                int lv = ct;
-                while (lv >= 1 && sh.Nq[lv] + Dw[lv] == 0) --lv;
-                while (lv >= 1) {
-                    int T = sh.Nq[lv] + Dw[lv];
-                    if (T & 1) T += (sh.Nq[lv] >= 1 && ((sh.coin[lv >> 5] >> (lv & 31)) & 1u)) ? -1 : 1;
-                    const int Cn = T >> 1;
-                    if (lv == 1) {
-                        if (lane == 0) Dw[0] += 2 * Cn;
-                    } else if (Cn <= kPreLabels) {
-                        if (lane < Cn) {
-                            const int k = sh.lab[lv][lane];
-                            atomicAdd(&Dw[k], 1);
-                            atomicAdd(&Dw[lv - 1 - k], 1);
-                        }
-                    } else {
-                        for (int k = lane; k < lv; k += 32) rw[k] = 0;
-                        __syncwarp();
-                        const int np = sh.npre[lv], cpre = Cn < np ? Cn : np;
-                        for (int c = lane; c < cpre; c += 32) atomicAdd(&rw[sh.lab[lv][c]], 1);
-                        for (int g = (np >> 2) + lane; g < (Cn + 3) >> 2; g += 32) {
-                            const U64x4 w = rng.draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
-#pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                if (4 * g + j < Cn) atomicAdd(&rw[below(w.w[j], uint32_t(lv))], 1);
-                        }
-                        __syncwarp();
-                        for (int k = lane; k < lv; k += 32) Dw[k] += rw[k] + rw[lv - 1 - k];
-                    }
-                    __syncwarp();
-                    --lv;
-                    while (lv >= 1 && sh.Nq[lv] + Dw[lv] == 0) --lv;
-                }
-                const int n0q = sh.Nq[0], A = npart - n0q, d0 = Dw[0];
-                return d0 <= A || d0 - A <= n0q;
-            };
-            while (sh.cont) {
-                if (tid == 0) {
-                    int c = sh.m_top;
-                    for (int w = 0; w < nsw; ++w) sh.cand[w] = -1;
-                    for (int w = 0; w < nsw; ++w) {
-                        sh.cand[w] = c;
-                        if (c == 0) break;                 // depth 0 needs no leaf: always feasible
-                        int h = c;
-                        while (h >= 1 && sh.Nq[h] == 0) --h;
-                        c = (h >= 1 ? h : 1) - 1;
-                    }
-                    sh.cand_next = c;
-                }
-                __syncthreads();
-                if (warp < nsw) {
-                    const int ct = sh.cand[warp];
-                    const bool ok = ct >= 0 && feasible_at(ct);
-                    if (lane == 0) sh.cand_ok[warp] = ok ? 1 : 0;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    int chosen = -1;
-                    for (int w = 0; w < nsw; ++w)
-                        if (sh.cand[w] >= 0 && sh.cand_ok[w]) { chosen = sh.cand[w]; break; }
-                    const int next = chosen >= 0 ? chosen : sh.cand_next;
-                    sh.feas += sh.m_top - next;
-                    sh.m_top = next;
-                    sh.cont = chosen >= 0 ? 0 : 1;
-                }
-                __syncthreads();
-            }
+        for (int attempt = 0;; ++attempt) {
             if (warp == 0) plan_attempt();
+            if (attempt == 0 && (warp > 0 || bs == 32)) {
+                const int t0 = bs == 32 ? tid : tid - 32, st = bs == 32 ? bs : bs - 32;
+                for (int r = nq0 + t0; r < npart; r += st) inv[r] = role_of(int(perm.inv(uint32_t(r))));
+            }
             __syncthreads();
+            if (attempt > 0 || sh.skip || !sh.cont) break;
+            {
+                // The first plan needs more leaves than the participants can give.
+                // The rule then lowers the depth to just below one quota level
+                // after another; those depths follow from the quotas alone, so up
+                // to four warps test the next ones at once (feasibility only), and
+                // warp 0 then plans the first feasible one in full.
+                const int nsw = (bs >> 5) < 4 ? (bs >> 5) : 4;
+                auto feasible_at = [&](int ct) -> bool {
+                    int32_t *Dw = reinterpret_cast<int32_t *>(sh.red) + warp * 130, *rw = Dw + NLEV;
+                    for (int j = lane; j < NLEV; j += 32) Dw[j] = 0;
+                    __syncwarp();
+                    int lv = ct;
+                    while (lv >= 1 && sh.Nq[lv] + Dw[lv] == 0) --lv;
+                    while (lv >= 1) {
+                        int T = sh.Nq[lv] + Dw[lv];
+                        if (T & 1) T += (sh.Nq[lv] >= 1 && ((sh.coin[lv >> 5] >> (lv & 31)) & 1u)) ? -1 : 1;
+                        const int Cn = T >> 1;
+                        if (lv == 1) {
+                            if (lane == 0) Dw[0] += 2 * Cn;
+                        } else if (Cn <= kPreLabels) {
+                            if (lane < Cn) {
+                                const int k = sh.lab[lv][lane];
+                                atomicAdd(&Dw[k], 1);
+                                atomicAdd(&Dw[lv - 1 - k], 1);
+                            }
+                        } else {
+                            for (int k = lane; k < lv; k += 32) rw[k] = 0;
+                            __syncwarp();
+                            const int np = sh.npre[lv], cpre = Cn < np ? Cn : np;
+                            for (int c = lane; c < cpre; c += 32) atomicAdd(&rw[sh.lab[lv][c]], 1);
+                            for (int g = (np >> 2) + lane; g < (Cn + 3) >> 2; g += 32) {
+                                const U64x4 w = rng().draw(uint64_t(g), uint64_t(lv), uint32_t(pass), TAG_KSEL);
+    #pragma unroll
+                                for (int j = 0; j < 4; ++j)
+                                    if (4 * g + j < Cn) atomicAdd(&rw[below(w.w[j], uint32_t(lv))], 1);
+                            }
+                            __syncwarp();
+                            for (int k = lane; k < lv; k += 32) Dw[k] += rw[k] + rw[lv - 1 - k];
+                        }
+                        __syncwarp();
+                        --lv;
+                        while (lv >= 1 && sh.Nq[lv] + Dw[lv] == 0) --lv;
+                    }
+                    const int n0q = sh.Nq[0], A = npart - n0q, d0 = Dw[0];
+                    return d0 <= A || d0 - A <= n0q;
+                };
+                while (sh.cont) {
+                    if (tid == 0) {
+                        int c = sh.m_top;
+                        for (int w = 0; w < nsw; ++w) sh.cand[w] = -1;
+                        for (int w = 0; w < nsw; ++w) {
+                            sh.cand[w] = c;
+                            if (c == 0) break;                 // depth 0 needs no leaf: always feasible
+                            int h = c;
+                            while (h >= 1 && sh.Nq[h] == 0) --h;
+                            c = (h >= 1 ? h : 1) - 1;
+                        }
+                        sh.cand_next = c;
+                    }
+                    __syncthreads();
+                    if (warp < nsw) {
+                        const int ct = sh.cand[warp];
+                        const bool ok = ct >= 0 && feasible_at(ct);
+                        if (lane == 0) sh.cand_ok[warp] = ok ? 1 : 0;
+                    }
+                    __syncthreads();
+                    if (tid == 0) {
+                        int chosen = -1;
+                        for (int w = 0; w < nsw; ++w)
+                            if (sh.cand[w] >= 0 && sh.cand_ok[w]) { chosen = sh.cand[w]; break; }
+                        const int next = chosen >= 0 ? chosen : sh.cand_next;
+                        sh.feas += sh.m_top - next;
+                        sh.m_top = next;
+                        sh.cont = chosen >= 0 ? 0 : 1;
+                    }
+                    __syncthreads();
+                }
+            }
         }
         if (sh.skip) break;
         const int m_eff = sh.m_eff, n0 = sh.n0, D0 = sh.D0, Dge1 = sh.Dge1;
         if (n0 < nq0) {
-            for (int r = n0 + tid; r < nq0; r += bs) {
-                const int i = int(perm.inv(uint32_t(r)));
-                inv[r] = (pass == 0) ? i : invp[poolp + i];
-            }
+            for (int r = n0 + tid; r < nq0; r += bs) inv[r] = role_of(int(perm.inv(uint32_t(r))));
             __syncthreads();
         }
-        if (pass == 0) {
+        // the stage's three components, from shared memory at each use (three
+        // pointers held across the pass would cost registers)
+        auto Vcx = [&]() { return sh.Vc; };
+        auto Vcy = [&]() { return sh.Vc + sh.nVc; };
+        auto Vcz = [&]() { return sh.Vc + 2 * sh.nVc; };
+        if ((Mode == kWhole || sh.full) && pass == 0) {
             // which slots change: every rank from n0 on (leaves and thermalised)
-            for (int r = n0 + tid; r < npart; r += bs) {          // (flags cleared with the staging)
+            for (int r = n0 + tid; r < npart; r += bs) {
                 const int i = inv[r];
                 atomicOr(&sh.flags[i >> 5], 1u << (i & 31));
             }
         }
+        if (Mode == kDual && !sh.full && pass == 0) {
+            // stage the particles that change (every rank from n0 on: the
+            // leaves, then the thermalised set) in rank order, Vc[r - n0]
+            constexpr int U = 4;
+            const int nv = sh.nVc;
+            for (int j0 = tid; j0 < nv; j0 += U * bs) {
+                Real x[U], y[U], z[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = j0 + u * bs;
+                    if (j < nv) {
+                        const int64_t g = base + inv[n0 + j];
+                        x[u] = gx[g]; y[u] = gy[g]; z[u] = gz[g];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = j0 + u * bs;
+                    if (j < nv) { Vcx()[j] = x[u]; Vcy()[j] = y[u]; Vcz()[j] = z[u]; }
+                }
+            }
+            __syncthreads();
+        }
+        // position in Vc of the particle of rank r of this pass (r >= n0)
+        const bool full = Mode == kWhole || sh.full;
+        auto pos = [&](int r) -> int { return pass == 0 && !full ? r - n0 : inv[r]; };
 
         // 5. collision waves, level 1 first.  Levels of at most warp_level
         //    collisions (the deep ones) run in warp 0 alone, with warp-level
@@ -1241,7 +1345,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
         auto collide_one = [&](int lv, int c, const Perm &pk) {
             // the draw and the product slots do not depend on the inputs:
             // issue them first so their latency overlaps the loads
-            const U64x4 w = rng.draw(uint64_t(c), uint64_t(lv), uint32_t(pass), TAG_COLL);
+            const U64x4 w = rng().draw(uint64_t(c), uint64_t(lv), uint32_t(pass), TAG_COLL);
             const int t0 = int(pk.fwd(uint32_t(2 * c))), t1 = int(pk.fwd(uint32_t(2 * c + 1)));
             const int Dn = sh.D[lv], On = sh.O[lv], IBn = sh.IB[lv];
             const int32_t *row = sh.Mt + tri(lv), *srow = sh.St + tri(lv);
@@ -1254,9 +1358,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             const int k = lo_, j = lv - 1 - k, off = c - sh.Pn[k];
             const int s0 = srow[k] + off, s1 = srow[j] + row[j] + off;
             Real ax, ay, az, bx, by, bz;
-            if (k == 0) { const int sl = inv[n0 + s0]; ax = Vx[sl]; ay = Vy[sl]; az = Vz[sl]; }
+            if (k == 0) { const int sl = pos(n0 + s0); ax = Vcx()[sl]; ay = Vcy()[sl]; az = Vcz()[sl]; }
             else { const int q = sh.IB[k] + s0; ax = IBx[q]; ay = IBy[q]; az = IBz[q]; }
-            if (j == 0) { const int sl = inv[n0 + s1]; bx = Vx[sl]; by = Vy[sl]; bz = Vz[sl]; }
+            if (j == 0) { const int sl = pos(n0 + s1); bx = Vcx()[sl]; by = Vcy()[sl]; bz = Vcz()[sl]; }
             else { const int q = sh.IB[j] + s1; bx = IBx[q]; by = IBy[q]; bz = IBz[q]; }
             const Real dx = ax - bx, dy = ay - by, dz = az - bz;
             const Real g2 = dx * dx + dy * dy + dz * dz;
@@ -1354,15 +1458,15 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const int k = ka, j = lv - 1 - k, off = c - pr[k];
                 const int s0 = srow[k] + off, s1 = srow[j] + row[j] + off;
                 int2 sr, ds;
-                sr.x = k == 0 ? ~inv[n0 + s0] : sh.IB[k] + s0;
-                sr.y = j == 0 ? ~inv[n0 + s1] : sh.IB[j] + s1;
+                sr.x = k == 0 ? ~pos(n0 + s0) : sh.IB[k] + s0;
+                sr.y = j == 0 ? ~pos(n0 + s1) : sh.IB[j] + s1;
                 Perm pk;
                 pk.init(uint32_t(2 * sh.C[lv]), sh.keys[lv]);
                 const int t0 = int(pk.fwd(uint32_t(2 * c))), t1 = int(pk.fwd(uint32_t(2 * c + 1)));
                 const int Dn = sh.D[lv];
                 ds.x = t0 < Dn ? sh.IB[lv] + t0 : ~(sh.O[lv] + t0 - Dn);
                 ds.y = t1 < Dn ? sh.IB[lv] + t1 : ~(sh.O[lv] + t1 - Dn);
-                const U64x4 w = rng.draw(uint64_t(c), uint64_t(lv), uint32_t(pass), TAG_COLL);
+                const U64x4 w = rng().draw(uint64_t(c), uint64_t(lv), uint32_t(pass), TAG_COLL);
                 const Real xs = alpha != Real(0) ? Math<Real>::uni(w.w[0]) * Sigma : Real(0);
                 const Real ct = Real(2) * Math<Real>::uni(w.w[1]) - Real(1);
                 const Real st = Math<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
@@ -1386,9 +1490,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             const Real xs = rr[0], sx = rr[1], sy = rr[2], sz = rr[3];
             Real ax, ay, az, bx, by, bz;
             if (sr.x >= 0) { ax = IBx[sr.x]; ay = IBy[sr.x]; az = IBz[sr.x]; }
-            else { const int sl = ~sr.x; ax = Vx[sl]; ay = Vy[sl]; az = Vz[sl]; }
+            else { const int sl = ~sr.x; ax = Vcx()[sl]; ay = Vcy()[sl]; az = Vcz()[sl]; }
             if (sr.y >= 0) { bx = IBx[sr.y]; by = IBy[sr.y]; bz = IBz[sr.y]; }
-            else { const int sl = ~sr.y; bx = Vx[sl]; by = Vy[sl]; bz = Vz[sl]; }
+            else { const int sl = ~sr.y; bx = Vcx()[sl]; by = Vcy()[sl]; bz = Vcz()[sl]; }
             const Real dx = ax - bx, dy = ay - by, dz = az - bz;
             const Real g2 = dx * dx + dy * dy + dz * dz;
             Real g = Real(0);
@@ -1528,10 +1632,10 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             const bool rad = prm.trunc == TRMC_TRUNC_RAD;
             const Real Ux = Real(sh.U[0]);
             auto place = [&](Sum<Real> (&cs)[10], int jx) {
-                const int sl = inv[n0 + jx];
-                const Real ox = Vx[sl], oy = Vy[sl], oz = Vz[sl];
+                const int sl = pos(n0 + jx);
+                const Real ox = Vcx()[sl], oy = Vcy()[sl], oz = Vcz()[sl];
                 const Real x = OBx[jx], y = OBy[jx], z = OBz[jx];
-                Vx[sl] = x; Vy[sl] = y; Vz[sl] = z;
+                Vcx()[sl] = x; Vcy()[sl] = y; Vcz()[sl] = z;
                 if constexpr (sizeof(Real) == 8) {
                     cs[0].add(x - ox); cs[1].add(y - oy); cs[2].add(z - oz);
                     cs[3].add((x * x + y * y + z * z) - (ox * ox + oy * oy + oz * oz));
@@ -1543,7 +1647,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 }
             };
             auto pool_add = [&](Sum<Real> (&cs)[10], int sl) {
-                const Real x = Vx[sl], y = Vy[sl], z = Vz[sl];
+                const Real x = Vcx()[sl], y = Vcy()[sl], z = Vcz()[sl];
                 cs[4].add(x); cs[5].add(y); cs[6].add(z);
                 cs[7].add_sq3(x, y, z);
                 if (rad) {
@@ -1573,10 +1677,10 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             for (int vw = warp; vw < kVW; vw += nw) {
                 Sum<Real> cs[10];
                 for (int jx = 32 * vw + lane; jx < D0; jx += 32 * kVW) {
-                    if (wbm && !keep_all && OL[jx] > mmax) pool_add(cs, inv[n0 + jx]);
+                    if (wbm && !keep_all && OL[jx] > mmax) pool_add(cs, pos(n0 + jx));
                     else place(cs, jx);
                 }
-                for (int t = 32 * vw + lane; t < R; t += 32 * kVW) pool_add(cs, inv[pool0 + t]);
+                for (int t = 32 * vw + lane; t < R; t += 32 * kVW) pool_add(cs, pos(pool0 + t));
                 if (rad) vw_put<10>(cs, sh.red, vw);
                 else vw_put<8>(cs, sh.red, vw);
             }
@@ -1588,7 +1692,7 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                     const bool rj = !keep_all && jx < D0 && OL[jx] > mmax;
                     int ex;
                     const int tot = block_flag_scan(rj, ex, sh.scan);
-                    if (rj) sh.ext[nrej + ex] = inv[n0 + jx];
+                    if (rj) sh.ext[nrej + ex] = pos(n0 + jx);
                     nrej += tot;
                 }
             }
@@ -1619,8 +1723,8 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const int R = sh.R;
                 double Sth = 0.0;
                 if (R == 1) {
-                    const int sl = inv[n0 + D0];
-                    Sth = indicator(double(Vx[sl]), double(Vy[sl]), double(Vz[sl]), sh.U, prm.indicator);
+                    const int sl = pos(n0 + D0);
+                    Sth = indicator(double(Vcx()[sl]), double(Vcy()[sl]), double(Vcz()[sl]), sh.U, prm.indicator);
                 } else if (R >= 2) {
                     const double Pt0 = sh.Pp[0] - sh.dP[0], Pt1 = sh.Pp[1] - sh.dP[1], Pt2 = sh.Pp[2] - sh.dP[2];
                     const double Et = sh.Ep - sh.dE;
@@ -1640,6 +1744,16 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const double E1 = (sh.S_pre != 0.0) ? fabs(dS_total) / fabs(double(sh.n) * sh.S_pre) : 0.0;
                 const int m = sh.m;
                 if (E1 > prm.delta2 && R > 0 && 2 * m <= prm.m_cap) {
+                    if (pass == 0) {
+                        // the continuation passes' position tables (at most R
+                        // entries each), persistent: pass 0's buffers are done
+                        sh.posA[0] = static_cast<int32_t *>(take(sh.smem_rest, sh.smem_rest_cap, sh.slab_rest,
+                                                                 sh.slab_rest_cap, 4 * size_t(R)));
+                        sh.posA[1] = static_cast<int32_t *>(take(sh.smem_rest, sh.smem_rest_cap, sh.slab_rest,
+                                                                 sh.slab_rest_cap, 4 * size_t(R)));
+                        if (!sh.posA[0] || !sh.posA[1]) sh.skip = 1;
+                        if (sh.slab_rest > sh.slab_hi) sh.slab_hi = sh.slab_rest;
+                    }
                     sh.cont = 1;
                     sh.n0_prev = n0; sh.D0_prev = D0;
                     sh.npart = R;
@@ -1663,15 +1777,23 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             raise_status(a.status, sh.skip == 2 ? TRMC_ERR_STATE : TRMC_ERR_CAPACITY, cell);
             if (a.stats) atomicAdd(&a.stats->capacity_skips, 1ull);
         }
-        return;
+        return Counts{{cnt[0], cnt[1], cnt[2]}};
     }
 
     // ---- 7. Maxwellian resampling of the thermalised set + renormalisation --
     const int pass = sh.pass, R = sh.R, R0 = sh.R - sh.nrej;
-    const int32_t *inv = sh.inv[pass & 1];
-    const int pool0 = sh.n0 + sh.D0;
+    const int32_t *posl = sh.posA[pass & 1];
+    const int pool0 = sh.n0 + sh.D0, n0l = sh.n0;
     const int32_t *ext = sh.ext;
-    auto pslot = [&](int t) { return t < R0 ? inv[pool0 + t] : ext[t - R0]; };
+    auto Vcx = [&]() { return sh.Vc; };
+    auto Vcy = [&]() { return sh.Vc + sh.nVc; };
+    auto Vcz = [&]() { return sh.Vc + 2 * sh.nVc; };
+    // position in Vc of thermalised member t (the set's own ranks, then the
+    // leaves TRMC-WB sent to it)
+    const bool full = Mode == kWhole || sh.full;
+    auto pslot = [&](int t) {
+        return t < R0 ? (pass == 0 ? (full ? sh.inv0[pool0 + t] : pool0 + t - n0l) : posl[pool0 + t]) : ext[t - R0];
+    };
     const int warp = tid >> 5, nw = bs >> 5;
     const bool carry = a.cell_carry != nullptr;
     if (R >= 2) {
@@ -1681,9 +1803,9 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             Sum<Real> qs[4];
             for (int t = 32 * vw + lane; t < R; t += 32 * kVW) {
                 Real z0, z1, z2;
-                Math<Real>::normals(rng.draw(uint64_t(t), 0, 0, TAG_MAXW), z0, z1, z2);
+                Math<Real>::normals(rng().draw(uint64_t(t), 0, 0, TAG_MAXW), z0, z1, z2);
                 const int sl = pslot(t);
-                Vx[sl] = z0; Vy[sl] = z1; Vz[sl] = z2;
+                Vcx()[sl] = z0; Vcy()[sl] = z1; Vcz()[sl] = z2;
                 qs[0].add(z0); qs[1].add(z1); qs[2].add(z2);
                 qs[3].add_sq3(z0, z1, z2);
             }
@@ -1722,11 +1844,11 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
                 const int sl = pslot(t);
                 Real x, y, z;
                 if constexpr (sizeof(Real) == 8) {
-                    x = u0 + sc * (Vx[sl] - zb0); y = u1 + sc * (Vy[sl] - zb1); z = u2 + sc * (Vz[sl] - zb2);
+                    x = u0 + sc * (Vcx()[sl] - zb0); y = u1 + sc * (Vcy()[sl] - zb1); z = u2 + sc * (Vcz()[sl] - zb2);
                 } else {
-                    x = f0 + fs * (Vx[sl] - rz0); y = f1 + fs * (Vy[sl] - rz1); z = f2 + fs * (Vz[sl] - rz2);
+                    x = f0 + fs * (Vcx()[sl] - rz0); y = f1 + fs * (Vcy()[sl] - rz1); z = f2 + fs * (Vcz()[sl] - rz2);
                 }
-                Vx[sl] = x; Vy[sl] = y; Vz[sl] = z;
+                Vcx()[sl] = x; Vcy()[sl] = y; Vcz()[sl] = z;
                 if (carry) { rs[0].add(x); rs[1].add(y); rs[2].add(z); rs[3].add_sq3(x, y, z); }
             }
             if (carry) vw_put<4>(rs, sh.red, vw);
@@ -1751,24 +1873,54 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             for (int j = 0; j < 4; ++j) a.cell_carry[4 * int64_t(cell) + j] = sh.carry[j];
     }
 
-    // ---- 8. write back the changed particles; cell max |v|^2 ----------------
-    if (a.cell_vmax2) {
-        Real vm = 0;
-        long long vmb = 0;
+    // ---- 8. write back the changed particles; cell max |v|^2 over the final
+    //         velocities ------------------------------------------------------
+    Real vm = 0;
+    long long vmb = 0;
+    auto vq = [&](Real x, Real y, Real z) {
+        if constexpr (sizeof(Real) == 8)       // rounded exactly as the CPU reference rounds it
+            vmb = max(vmb, __double_as_longlong(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z))));
+        else
+            vm = fmaxf(vm, __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z)));
+    };
+    const bool vmx = a.cell_vmax2 != nullptr;
+    if (full) {
+        // coalesced: every slot in order, the changed ones written
         for (int i = tid; i < n; i += bs) {
-            const Real x = Vx[i], y = Vy[i], z = Vz[i];
+            const Real x = Vcx()[i], y = Vcy()[i], z = Vcz()[i];
             if ((sh.flags[i >> 5] >> (i & 31)) & 1u) { gx[base + i] = x; gy[base + i] = y; gz[base + i] = z; }
-            if constexpr (sizeof(Real) == 8)       // rounded exactly as the CPU reference rounds it
-                vmb = max(vmb, __double_as_longlong(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z))));
-            else
-                vm = fmaxf(vm, __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z)));
+            if (vmx) vq(x, y, z);
         }
+    } else {
+        // scattered from the compact stage to the changed slots, then (for the
+        // maximum) every particle from global memory, the changed ones as just
+        // written (L2 holds the cell: it was read at the start of the step)
+        const int n0f = sh.n0_first, nch = n - n0f;
+        const int32_t *inv0 = sh.inv0;
+        for (int j = tid; j < nch; j += bs) {
+            const int64_t g = base + inv0[n0f + j];
+            gx[g] = Vcx()[j]; gy[g] = Vcy()[j]; gz[g] = Vcz()[j];
+        }
+        if (vmx) {
+            __syncthreads();
+            constexpr int U = 2;
+            for (int i0 = tid; i0 < n; i0 += U * bs) {
+                Real x[U], y[U], z[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * bs;
+                    if (i < n) { x[u] = gx[base + i]; y[u] = gy[base + i]; z[u] = gz[base + i]; }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (i0 + u * bs < n) vq(x[u], y[u], z[u]);
+            }
+        }
+    }
+    if (vmx) {
         if constexpr (sizeof(Real) == 8) vm = __longlong_as_double(vmb);
         const double vmax = block_max_nonneg(double(vm), sh.red);
         if (tid == 0) a.cell_vmax2[cell] = vmax;
-    } else {
-        for (int i = tid; i < n; i += bs)
-            if ((sh.flags[i >> 5] >> (i & 31)) & 1u) { gx[base + i] = Vx[i]; gy[base + i] = Vy[i]; gz[base + i] = Vz[i]; }
     }
     if (tid == 0) {
         if (prm.trunc == TRMC_TRUNC_RAD) a.m_max[cell] = sh.m_next;
@@ -1779,9 +1931,10 @@ __device__ void process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigne
             r[11] = sh.feas; r[12] = sh.pdrop_tot; r[13] = sh.psurp_tot; r[15] = sh.nrej;
         }
     }
+    return Counts{{cnt[0], cnt[1], cnt[2]}};
 }
 
-template <typename Real>
+template <typename Real, int Mode>
 __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -1791,6 +1944,7 @@ __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
     // the device step counter is read before any CTA can finish: it is
     // advanced only after every CTA of this launch has retired its last cell
     const uint64_t step = a.step_dev ? *a.step_dev : a.step;
+    unsigned int n_max = 0;          // the largest cell this CTA met (thread 0)
     for (;;) {
         if (threadIdx.x == 0) s_cell = int(atomicAdd(&a.tickets[0], 1u));
         __syncthreads();
@@ -1798,13 +1952,20 @@ __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
         __syncthreads();
         if (ticket >= a.n_cells) break;
         const int cell = a.cell_order ? a.cell_order[ticket] : ticket;
-        int cnt[3] = {0, 0, 0};      // collisions, dummy, exceed
         const long long t_start = clock64();
-        process_cell<Real>(a, step, sh, dsm, slab, cell, cnt);
+        const Counts k = process_cell<Real, Mode>(a, step, sh, dsm, slab, cell);
+        int cnt[3] = {k.c[0], k.c[1], k.c[2]};      // collisions, dummy, exceed
+        if (threadIdx.x == 0 && unsigned(sh.n) > n_max) n_max = unsigned(sh.n);
         if (a.cell_cost && threadIdx.x == 0) {
             const unsigned long long dt = (unsigned long long)(clock64() - t_start) >> 4;
             a.cell_cost[cell] = dt > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(dt);
         }
+        __syncthreads();
+        // The slab is scratch that the next cell writes again before it reads
+        // it: drop the lines this cell dirtied from L2 without writing them
+        // back to DRAM (its 128-byte lines; the slab starts 256-byte aligned)
+        for (char *p = slab + size_t(threadIdx.x) * 128; p < sh.slab_hi; p += size_t(blockDim.x) * 128)
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
         __syncthreads();
         if (a.report || a.stats) {
             block_sum_int<3>(cnt, sh.red);
@@ -1830,9 +1991,14 @@ __global__ void __launch_bounds__(kThreads, 2) collide_kernel(Args a)
         }
     }
     if (threadIdx.x == 0) {
+        if (n_max) atomicMax(&a.tickets[2], n_max);
         __threadfence();
         const unsigned done = atomicAdd(&a.tickets[1], 1u);
         if (done == gridDim.x - 1) {
+            // the last CTA: publish the launch's largest cell (the host picks the
+            // next launch's mode from it) and reset the counters
+            const unsigned biggest = atomicExch(&a.tickets[2], 0u);
+            if (a.n_max_host) *a.n_max_host = biggest;
             a.tickets[0] = 0u;
             a.tickets[1] = 0u;
             if (a.step_dev) *a.step_dev = step + 1;
@@ -1872,19 +2038,28 @@ __global__ void __launch_bounds__(1024) order_kernel(const uint32_t *cost, int n
 // The kernel's dynamic shared-memory limit, set once per device to the most a
 // CTA can have, so that every launch shape (and the allocation-free entry
 // point) fits under it whatever order they come in.
-template <typename Real>
+template <typename Real, int Mode>
 cudaError_t allow_max_smem(int device, int smem_optin)
 {
     constexpr int kDev = 64;
     static bool done[kDev] = {};
     if (device >= 0 && device < kDev && done[device]) return cudaSuccess;
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, collide_kernel<Real>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, collide_kernel<Real, Mode>);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(collide_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(collide_kernel<Real, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smem_optin - int(fa.sharedSizeBytes));
     if (e == cudaSuccess && device >= 0 && device < kDev) done[device] = true;
     return e;
+}
+
+// Does a cell of n particles fit in one CTA's shared memory staged whole
+// (velocities, change bitmap, slot table)?  The same test as the kernel's.
+template <typename Real>
+bool fits_whole(uint64_t n, int smem)
+{
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    return a16(3 * size_t(n) * sizeof(Real)) + a16(4 * size_t((n + 31) / 32)) + a16(4 * size_t(n)) <= size_t(smem);
 }
 
 // Dynamic shared memory of one CTA when per_sm CTAs share an SM: the SM's
@@ -1909,10 +2084,15 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     // the shared-memory budget of an SM is split evenly between them
     const int threads = ctx->collide_threads, per_sm_target = ctx->collide_ctas_per_sm;
     const int smem = collide_smem<Real>(int(ctx->smem_optin), per_sm_target);
-    cudaError_t e = allow_max_smem<Real>(ctx->device, int(ctx->smem_optin));
+    // the mode: staged whole, unless the previous launch met a cell too large
+    // for shared memory (the first launch of a context does not know: dual)
+    const bool dual = !ctx->n_max_host || !fits_whole<Real>(*ctx->n_max_host, smem);
+    cudaError_t e = dual ? allow_max_smem<Real, kDual>(ctx->device, int(ctx->smem_optin))
+                         : allow_max_smem<Real, kWhole>(ctx->device, int(ctx->smem_optin));
     if (e != cudaSuccess) return cuda_error(ctx, e, "cudaFuncSetAttribute(collide)");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_kernel<Real>, threads, smem);
+    e = dual ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_kernel<Real, kDual>, threads, smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_kernel<Real, kWhole>, threads, smem);
     if (e != cudaSuccess) return cuda_error(ctx, e, "occupancy(collide)");
     if (per_sm < 1) per_sm = 1;
     int grid = ctx->num_sms * per_sm;
@@ -1938,12 +2118,14 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     a.stats = stats;
     a.status = ctx->status;
     a.tickets = ctx->tickets;
+    a.n_max_host = ctx->n_max_dev;
     a.slabs = ctx->slabs;
     a.slab_bytes = (ctx->slabs_bytes / size_t(grid)) & ~size_t(255);
     a.smem_bytes = smem;
     a.warp_level = sizeof(Real) == 8 ? kWarpLevel64 : kWarpLevel32;
     if (st->cell_cost && st->cell_order) order_kernel<<<1, 1024, 0, s>>>(st->cell_cost, st->n_cells, st->cell_order);
-    collide_kernel<Real><<<grid, threads, smem, s>>>(a);
+    if (dual) collide_kernel<Real, kDual><<<grid, threads, smem, s>>>(a);
+    else collide_kernel<Real, kWhole><<<grid, threads, smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "collide launch");
     return TRMC_OK;
@@ -1986,14 +2168,15 @@ constexpr int kMaxDevices = 64;
 StaticDevice g_static_dev[kMaxDevices];
 
 // Working-set bound of one cell of n particles in the overflow slab: the
-// staged velocities, flags and role tables, the triangular plan tables at the
-// deepest level, and product buffers for up to 4n consumers and n outputs
-// (with TRMC-WB also their tree lengths and the rejected outputs' slots).
+// slot table, the staged changed particles (at most n) and the continuation
+// passes' position tables, the triangular plan tables at the deepest level,
+// and product buffers for up to 4n consumers and n outputs (with TRMC-WB also
+// their tree lengths and the rejected outputs' slots).
 size_t static_cell_bytes(int64_t n, size_t real, bool wb)
 {
     auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
     const size_t N = size_t(n), T = size_t(TRMC_MCAP) * (TRMC_MCAP + 1) / 2 + 1;
-    size_t b = a16(3 * N * real) + a16(4 * ((N + 31) / 32)) + 2 * a16(4 * N) + 2 * a16(4 * T) +
+    size_t b = a16(4 * N) + a16(3 * (N + 1) * real) + 2 * a16(4 * N) + 2 * a16(4 * T) +
                a16(3 * (3 * N + 1) * real) + a16(3 * (N + 1) * real) + 256;
     if (wb) b += a16(8 * (3 * N + 1)) + a16(8 * (N + 1)) + a16(4 * (N + 1));
     return b;
@@ -2019,7 +2202,7 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
         D.ready = true;
     }
     const int smem = collide_smem<Real>(D.smem_optin, per_sm_target);
-    if (allow_max_smem<Real>(dev, D.smem_optin) != cudaSuccess) return TRMC_ERR_CUDA;
+    if (allow_max_smem<Real, kDual>(dev, D.smem_optin) != cudaSuccess) return TRMC_ERR_CUDA;
     const size_t avail = size_t(TRMC_STATIC_SCRATCH_BYTES) - kStaticControl;
     const size_t need = static_cell_bytes(max_cell, sizeof(Real), prm->trunc == TRMC_TRUNC_WB);
     int grid = int(std::min<size_t>(avail / need, size_t(D.num_sms) * per_sm_target));
@@ -2047,11 +2230,12 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
     a.stats = nullptr;
     a.status = status_dev ? status_dev : reinterpret_cast<int *>(D.scratch);
     a.tickets = reinterpret_cast<unsigned int *>(D.scratch + 64);
+    a.n_max_host = nullptr;
     a.slabs = D.scratch + kStaticControl;
     a.slab_bytes = (avail / size_t(grid)) & ~size_t(255);
     a.smem_bytes = smem;
     a.warp_level = sizeof(Real) == 8 ? kWarpLevel64 : kWarpLevel32;
-    collide_kernel<Real><<<grid, threads, smem, s>>>(a);
+    collide_kernel<Real, kDual><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? TRMC_OK : TRMC_ERR_CUDA;
 }
 

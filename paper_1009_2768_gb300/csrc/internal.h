@@ -17,7 +17,11 @@ struct trmc_ctx {
     char *workspace = nullptr;
     size_t workspace_bytes = 0;
     int *status = nullptr;            // [0] error code, [1] detail (cell), [2..3] spare
-    unsigned int *tickets = nullptr;  // [0] next cell, [1] CTAs done (collide)
+    unsigned int *tickets = nullptr;  // [0] next cell, [1] CTAs done, [2] largest cell (collide)
+    // host-mapped word: the largest cell of the last collide launch (written by
+    // its last CTA; UINT_MAX until the first launch), and its device address
+    volatile unsigned int *n_max_host = nullptr;
+    unsigned int *n_max_dev = nullptr;
     char *slabs = nullptr;
     size_t slabs_bytes = 0;
     // transport scratch, grown on demand

@@ -42,10 +42,12 @@ __device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_
 }
 
 // Keyed stream of one cell: key = (seed, problem); the fourth counter word
-// packs step, pass and purpose tag.
+// packs step, pass and purpose tag.  A draw is about 300 instructions and the
+// collision kernel makes them in many places: one shared copy (not inlined)
+// keeps the kernel's code small enough for the instruction caches.
 struct CellRng {
     uint64_t seed, problem, cell, step;
-    __device__ __forceinline__ U64x4 draw(uint64_t index, uint64_t aux, uint32_t pass, uint32_t tag) const
+    __device__ __noinline__ U64x4 draw(uint64_t index, uint64_t aux, uint32_t pass, uint32_t tag) const
     {
         const uint64_t c3 = (step << 16) | (uint64_t(pass & 0xFFu) << 8) | uint64_t(tag & 0xFFu);
         return philox4x64_10(index, aux, cell, c3, seed, problem);
@@ -110,16 +112,16 @@ struct Perm {
         }
         return (L << h) | R;
     }
-    // pi(x) for x < n
-    __device__ __forceinline__ uint32_t fwd(uint32_t x) const
+    // pi(x) for x < n (not inlined: one copy serves every call site)
+    __device__ __noinline__ uint32_t fwd(uint32_t x) const
     {
         if (n <= 1) return 0;
         uint32_t y = enc(x);
         while (y >= n) y = enc(y);
         return y;
     }
-    // pi^-1(y) for y < n: the cycle through y walked backwards
-    __device__ __forceinline__ uint32_t inv(uint32_t y) const
+    // pi^-1(y) for y < n: the cycle through y walked backwards (not inlined)
+    __device__ __noinline__ uint32_t inv(uint32_t y) const
     {
         if (n <= 1) return 0;
         uint32_t x = dec(y);

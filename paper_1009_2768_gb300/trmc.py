@@ -218,7 +218,7 @@ class ParticleState:
     *_alt arrays swap; after_transport() keeps the tensors in step."""
 
     def __init__(self, cell_start, capacity=None, precision=FP64, with_x=False, rad=False,
-                 cell_param=None, cell_key=None, problem_id=0, carry=False, device="cuda"):
+                 cell_param=None, cell_key=None, problem_id=0, carry=False, vmax=True, device="cuda"):
         import torch
         cs = torch.as_tensor(np.asarray(cell_start, dtype=np.int64)).to(device)
         n_cells = cs.numel() - 1
@@ -238,7 +238,11 @@ class ParticleState:
             self.cell_param = torch.as_tensor(cp).to(device)
         self.cell_key = None if cell_key is None else torch.as_tensor(
             np.asarray(cell_key, dtype=np.uint64).view(np.int64)).to(device)
-        self.cell_vmax2 = torch.zeros(max(n_cells, 1), dtype=torch.float64, device=device)
+        # per-cell max |v|^2 after each collide: the CFL time step of a transport
+        # needs it; homogeneous problems can leave it out (vmax=False) and save
+        # the collide step its pass over the final velocities
+        self.cell_vmax2 = torch.zeros(max(n_cells, 1), dtype=torch.float64, device=device) if vmax else None
+        self.device = device
         self.cell_carry = torch.zeros((max(n_cells, 1), 4), dtype=torch.float64, device=device) if carry else None
         self.step_dev = None           # device step counter (use_device_step)
         self.cell_order = None         # cell processing order (set_cell_order)
@@ -263,7 +267,7 @@ class ParticleState:
         c.m_max = self.m_max.data_ptr() if self.m_max is not None else None
         c.cell_param = self.cell_param.data_ptr() if self.cell_param is not None else None
         c.cell_key = self.cell_key.data_ptr() if self.cell_key is not None else None
-        c.cell_vmax2 = self.cell_vmax2.data_ptr()
+        c.cell_vmax2 = self.cell_vmax2.data_ptr() if self.cell_vmax2 is not None else None
         c.cell_carry = self.cell_carry.data_ptr() if self.cell_carry is not None else None
         c.step_dev = self.step_dev.data_ptr() if self.step_dev is not None else None
         c.cell_order = self.cell_order.data_ptr() if self.cell_order is not None else None
@@ -273,21 +277,21 @@ class ParticleState:
         """Key the collision draws with a device counter that each trmc_collide
         advances, so that captured CUDA graphs step on replay."""
         import torch
-        self.step_dev = torch.full((1,), start, dtype=torch.int64, device=self.cell_vmax2.device)
+        self.step_dev = torch.full((1,), start, dtype=torch.int64, device=self.device)
         self._fill()
 
     def use_adaptive_order(self):
         """Let every collide launch hand out the cells longest first, by the
         times the previous launch measured (identity order at the start)."""
         import torch
-        dev = self.cell_vmax2.device
+        dev = self.device
         self.cell_cost = torch.zeros(max(self.n_cells, 1), dtype=torch.int32, device=dev)
         self.cell_order = torch.arange(max(self.n_cells, 1), dtype=torch.int32, device=dev)
         self._fill()
 
     def set_cell_order(self, order):
         import torch
-        self.cell_order = torch.as_tensor(np.asarray(order, dtype=np.int32)).to(self.cell_vmax2.device)
+        self.cell_order = torch.as_tensor(np.asarray(order, dtype=np.int32)).to(self.device)
         self._fill()
 
     def after_transport(self):

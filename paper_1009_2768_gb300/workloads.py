@@ -91,7 +91,7 @@ class HomogeneousBKW:
                  workspace=256 << 20):
         cs = np.array([0, n], np.int64)
         self.n_particles = n
-        self.state = T.ParticleState(cs, precision=precision, rad=trunc == T.TRUNC_RAD)
+        self.state = T.ParticleState(cs, precision=precision, rad=trunc == T.TRUNC_RAD, vmax=False)
         if trunc == T.TRUNC_RAD:
             self.state.m_max.fill_(m_init)
         self.ctx = T.trmc_create(precision, seed, workspace)
@@ -139,7 +139,7 @@ class BatchedRelaxation:
         else:                                 # one problem, cells numbered within it
             keys = (np.uint64(problem_base) << np.uint64(32)) | c
         self.state = T.ParticleState(cs, capacity=self.n_particles, precision=precision, rad=trunc == T.TRUNC_RAD,
-                                     cell_param=cp, cell_key=keys, carry=precision == T.FP32_MIXED)
+                                     cell_param=cp, cell_key=keys, carry=precision == T.FP32_MIXED, vmax=False)
         if trunc == T.TRUNC_RAD:
             self.state.m_max.fill_(m_init)
         self.own_ctx = ctx is None
