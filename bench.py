@@ -72,7 +72,7 @@ NCU_TRAFFIC = {
 
 # Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
 # runtime.autotune_collide's candidates on GB300 (--tune measures them again).
-LAUNCH = {"shock": (128, 3), "stationary": (256, 2), "batched": (256, 2), "bkw": (256, 2)}
+LAUNCH = {"shock": (128, 3), "stationary": (256, 3), "batched": (256, 2), "bkw": (256, 2)}
 
 
 def collide_sha():

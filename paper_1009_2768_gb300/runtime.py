@@ -22,7 +22,7 @@ import numpy as np
 
 from . import trmc as T
 
-DEFAULT_SHAPES = ((128, 4), (96, 4), (96, 5), (128, 3), (160, 3), (192, 2), (256, 2), (64, 8))
+DEFAULT_SHAPES = ((256, 3), (256, 2), (128, 4), (128, 3), (160, 3), (192, 2), (64, 8))
 
 
 def largest_first(cell_start):

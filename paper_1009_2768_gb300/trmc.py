@@ -223,6 +223,9 @@ class ParticleState:
         cs = torch.as_tensor(np.asarray(cell_start, dtype=np.int64)).to(device)
         n_cells = cs.numel() - 1
         n = int(cs[-1].item()) if capacity is None else int(capacity)
+        # a whole number of 16-byte vectors per array (every row of v then starts
+        # 16-byte aligned, and the transport reads the particles as vectors)
+        n = -(-n // 4) * 4
         dt = torch.float64 if precision == FP64 else torch.float32
         self.precision = precision
         self.v = torch.zeros((3, max(n, 1)), dtype=dt, device=device)
