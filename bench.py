@@ -72,7 +72,7 @@ NCU_TRAFFIC = {
 
 # Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
 # runtime.autotune_collide's candidates on GB300 (--tune measures them again).
-LAUNCH = {"shock": (128, 3), "stationary": (256, 3), "batched": (256, 2), "bkw": (256, 2)}
+LAUNCH = {"shock": (128, 4), "stationary": (256, 3), "batched": (256, 2), "bkw": (256, 2)}
 
 
 def collide_sha():
@@ -502,9 +502,12 @@ def ours(args):
         # the collide launch shape for this workload's cell sizes, measured on
         # the live state before timing
         from paper_1009_2768_gb300 import runtime as RT
-        times, best = RT.autotune_collide(sim, steps=3)
-        launch = {"threads": best[0], "ctas_per_sm": best[1], "tuned_ms": {f"{k[0]}x{k[1]}": round(v, 4)
-                                                                          for k, v in times.items()}}
+        tuned = RT.autotune(sim, steps=3)
+        best = tuned["collide_best"]
+        launch = {"threads": best[0], "ctas_per_sm": best[1],
+                  "tuned_ms": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in tuned["collide"].items()},
+                  "sort_threads": tuned["sort_best"],
+                  "sort_tuned_ms": {str(k): round(v, 4) for k, v in tuned["sort"].items()}}
         for _ in range(2):
             sim.step()
         T.trmc_check(sim.ctx)
@@ -784,7 +787,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--tune", action="store_true", help="choose the collide launch shape with the autotuner")
+    ap.add_argument("--tune", action="store_true", help="choose the collide launch shape and the sort schedule with the autotuner")
     ap.add_argument("--launch", default="", help="collide launch shape THREADSxCTAS_PER_SM (default: per workload)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=["stationary", "shock", "batched", "bkw", "serving"])
     ap.add_argument("--rates", default="1,10,50,200", help="serving: arrival rates (requests/s) to sweep")

@@ -184,6 +184,14 @@ trmc_status trmc_check(trmc_ctx *ctx, void *stream);
  * only speed does (the autotuner in the binding sweeps it). */
 trmc_status trmc_set_collide_launch(trmc_ctx *ctx, int32_t threads, int32_t ctas_per_sm);
 
+/* Launch shape of the transport's counting sort (the count and scatter
+ * kernels, one CTA per old cell): threads per CTA, a multiple of 32 in
+ * [32, 256], or 0 (the default) for a size picked from the mean cell size
+ * (64 up to 1024 particles, 128 up to 4096, else 256).  The paper has no
+ * counterpart; results do not depend on it (the sort is stable whatever the
+ * CTA size), only speed does. */
+trmc_status trmc_set_transport_launch(trmc_ctx *ctx, int32_t threads);
+
 /* Sample initial velocities (and positions, if state->x != NULL) for every
  * particle of every cell, from the synthetic closed-form laws listed in
  * trmc_init_kind.  cell_init_dev: [n_cells][TRMC_INIT_COLS] doubles on the

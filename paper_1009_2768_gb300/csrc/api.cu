@@ -166,6 +166,15 @@ trmc_status trmc_set_collide_launch(trmc_ctx *ctx, int32_t threads, int32_t ctas
     return TRMC_OK;
 }
 
+trmc_status trmc_set_transport_launch(trmc_ctx *ctx, int32_t threads)
+{
+    if (!ctx) return TRMC_ERR_ARG;
+    if (threads != 0 && (threads < 32 || threads > 256 || threads % 32 != 0))
+        return set_error(ctx, TRMC_ERR_ARG, "transport threads must be 0 or a multiple of 32 in [32, 256]");
+    ctx->transport_threads = threads;
+    return TRMC_OK;
+}
+
 trmc_status trmc_init_cells(trmc_ctx *ctx, trmc_state *state, const double *cell_init_dev, void *stream)
 {
     if (!ctx) return TRMC_ERR_ARG;

@@ -32,6 +32,8 @@ struct trmc_ctx {
     // collide launch shape (trmc_set_collide_launch)
     int collide_threads = 128;
     int collide_ctas_per_sm = 4;
+    // transport sort launch shape (trmc_set_transport_launch; 0: by mean cell size)
+    int transport_threads = 0;
     std::string last_error;
 };
 

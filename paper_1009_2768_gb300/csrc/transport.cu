@@ -543,7 +543,8 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_domain *doms, int
     // for cells of about 500 particles move them 11 % faster than 256, which
     // suit cells of thousands); the order the scatter writes does not depend on it
     const int64_t per_cell = st->capacity / (nc > 0 ? nc : 1);
-    const int tt = per_cell <= 1024 ? 64 : per_cell <= 4096 ? 128 : kTT;
+    const int tt = ctx->transport_threads ? ctx->transport_threads
+                                          : per_cell <= 1024 ? 64 : per_cell <= 4096 ? 128 : kTT;
     // 16-byte vector loads (four floats) in the count kernel where x and v_x
     // start on a 16-byte boundary and the capacity is a whole number of
     // vectors.  Measured on GB300: as fast as one float per thread on the

@@ -15,6 +15,10 @@ simulation back where it found it.
 * autotune_collide times candidate (CTA size, CTAs per SM) shapes on the
   live workload, keeps the fastest and then restores the state it stepped
   (velocities, positions, cell starts, RAD depths, carries, step counters).
+  The CTA size also sets how many particles of a cell each warp handles
+  (cell size / warps per CTA).  autotune_transport does the same for the
+  sort schedule (threads per CTA of the counting sort's count and scatter
+  kernels, one CTA per cell), and autotune runs both.
 * largest_first orders cells by particle count, biggest first, so the
   longest cells start early and the launch does not end on one of them.
 """
@@ -23,6 +27,7 @@ import numpy as np
 from . import trmc as T
 
 DEFAULT_SHAPES = ((256, 3), (256, 2), (128, 4), (128, 3), (160, 3), (192, 2), (64, 8))
+SORT_SCHEDULES = (0, 64, 128, 256)     # transport threads per cell CTA (0: by mean cell size)
 
 
 def largest_first(cell_start):
@@ -94,7 +99,7 @@ def autotune_collide(sim, shapes=DEFAULT_SHAPES, steps=6, flush_bytes=256 << 20)
     """Time `steps` collide launches of the live workload for every (threads,
     CTAs per SM) shape, with an L2 flush before each, and keep the fastest.
     The simulation is put back in the state it had before tuning.  Returns
-    {shape: mean collide ms} and leaves the best shape set."""
+    {shape: median collide ms} and leaves the best shape set."""
     import torch
     flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
@@ -117,3 +122,43 @@ def autotune_collide(sim, shapes=DEFAULT_SHAPES, steps=6, flush_bytes=256 << 20)
     _restore(sim, snap)
     torch.cuda.synchronize()
     return times, best
+
+
+def autotune_transport(sim, choices=SORT_SCHEDULES, steps=6, flush_bytes=256 << 20):
+    """Time `steps` transports of the live workload for every sort schedule
+    (threads per CTA of the count and scatter kernels; 0 lets the library
+    pick from the mean cell size), with an L2 flush before each, keep the
+    fastest and restore the simulation.  Returns ({threads: median transport ms}, best);
+    a workload without transport returns ({}, None)."""
+    import torch
+    if not getattr(sim, "transports", False):
+        return {}, None
+    flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    snap = _snapshot(sim)
+    times = {}
+    for tt in choices:
+        T.trmc_set_transport_launch(sim.ctx, tt)
+        sim.step()
+        ms = []
+        for _ in range(steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            flush.zero_()
+            sim.step(events=ev)
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        times[tt] = float(np.median(ms))
+    best = min(times, key=times.get)
+    T.trmc_set_transport_launch(sim.ctx, best)
+    T.trmc_check(sim.ctx)
+    _restore(sim, snap)
+    torch.cuda.synchronize()
+    return times, best
+
+
+def autotune(sim, shapes=DEFAULT_SHAPES, schedules=SORT_SCHEDULES, steps=6):
+    """The collide launch shape and the sort schedule for the live workload
+    (both left set; the simulation is restored)."""
+    collide_times, shape = autotune_collide(sim, shapes, steps)
+    sort_times, sched = autotune_transport(sim, schedules, steps)
+    return {"collide": collide_times, "collide_best": shape, "sort": sort_times, "sort_best": sched}

@@ -27,6 +27,7 @@ REPORT_FIELDS = ["N", "passes", "m_first", "m_last", "m_next", "R_final", "N0", 
                  "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "wbrej"]
 EXPORTS = ["trmc_create", "trmc_destroy", "trmc_last_error", "trmc_check", "trmc_init_cells",
            "trmc_collide", "trmc_transport", "trmc_moments", "trmc_collide_static", "trmc_set_collide_launch",
+           "trmc_set_transport_launch",
            "trmc_fp64_selftest", "trmc_split_selftest"]
 STATIC_SCRATCH_BYTES = 32 << 20
 
@@ -111,6 +112,7 @@ def load():
         lib.trmc_transport.argtypes = [P, C.POINTER(State), P, C.c_int32, C.c_double, P, C.c_uint64, P]
         lib.trmc_moments.argtypes = [P, C.POINTER(State), P, P]
         lib.trmc_set_collide_launch.argtypes = [P, C.c_int32, C.c_int32]
+        lib.trmc_set_transport_launch.argtypes = [P, C.c_int32]
         lib.trmc_collide_static.argtypes = [C.POINTER(State), C.POINTER(CollideParams), C.c_int32, C.c_uint64,
                                             C.c_uint64, C.c_int32, P, P]
         lib.trmc_fp64_selftest.argtypes = [P, C.c_int32, P, P]
@@ -157,6 +159,10 @@ def trmc_check(ctx, stream=None):
 
 def trmc_set_collide_launch(ctx, threads, ctas_per_sm):
     _raise(ctx, load().trmc_set_collide_launch(ctx, threads, ctas_per_sm))
+
+
+def trmc_set_transport_launch(ctx, threads):
+    _raise(ctx, load().trmc_set_transport_launch(ctx, threads))
 
 
 def trmc_init_cells(ctx, state, cell_init, stream=None):

@@ -60,3 +60,26 @@ def test_results_are_bit_identical_across_launch_shapes(precision, name):
         got = run_shape(precision, shape, PARAMS[name], COUNTS, carry=carry)
         for a, b in zip(ref, got):
             assert np.array_equal(a, b), f"launch shape {shape} differs from {SHAPES[0]} ({name})"
+
+
+def test_sort_schedule_does_not_change_transport():
+    """The counting sort is stable whatever its CTA size: shock tubes stepped
+    with 64, 128 or 256 threads per cell CTA (and the library's own pick) end
+    in bit-identical states."""
+    need_gpu()
+    ensure_built()
+    from paper_1009_2768_gb300.workloads import ShockTubes
+    out = []
+    for tt in (0, 64, 128, 256):
+        sim = ShockTubes((1e-2, 1e-3), n_cells=64, mean_per_cell=300, precision=T.FP64, seed=4)
+        T.trmc_set_transport_launch(sim.ctx, tt)
+        for _ in range(4):
+            sim.step()
+        torch.cuda.synchronize()
+        T.trmc_check(sim.ctx)
+        st = sim.state
+        out.append([st.v.cpu().numpy(), st.x.cpu().numpy(), st.cell_start.cpu().numpy(), st.m_max.cpu().numpy()])
+        sim.close()
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
