@@ -33,7 +33,9 @@ def ctx(precision=T.FP64, seed=0, workspace=256 << 20):
 
 
 def gpu_collide(v, cell_start, params, step, precision=T.FP64, seed=0, m_state=None, cell_param=None,
-                cell_key=None, problem_id=0, workspace=256 << 20, want_report=True, stats=False):
+                cell_key=None, problem_id=0, workspace=256 << 20, want_report=True, stats=False, launch=None):
+    """One trmc_collide on a cached context; launch = (threads, CTAs per SM)
+    for this call only (the context's default, 128 x 4, otherwise)."""
     st = T.ParticleState(cell_start, precision=precision, rad=m_state is not None, cell_param=cell_param,
                          cell_key=cell_key, problem_id=problem_id)
     st.set_velocities(v)
@@ -42,8 +44,14 @@ def gpu_collide(v, cell_start, params, step, precision=T.FP64, seed=0, m_state=N
     c = ctx(precision, seed, workspace)
     rep = torch.zeros((max(st.n_cells, 1), T.REPORT_LEN), dtype=torch.int64, device="cuda") if want_report else None
     stt = torch.zeros(len(T.STATS_FIELDS), dtype=torch.int64, device="cuda") if stats else None
-    T.trmc_collide(c, st, params, step, report=rep, stats=stt)
-    T.trmc_check(c)
+    if launch is not None:
+        T.trmc_set_collide_launch(c, *launch)
+    try:
+        T.trmc_collide(c, st, params, step, report=rep, stats=stt)
+        T.trmc_check(c)
+    finally:
+        if launch is not None:
+            T.trmc_set_collide_launch(c, 128, 4)
     out = {"v": st.v[:, :int(cell_start[-1])].double().cpu().numpy(),
            "report": rep.cpu().numpy()[:st.n_cells] if want_report else None,
            "m_state": st.m_max.cpu().numpy() if m_state is not None else None,

@@ -25,9 +25,10 @@ def cells(counts, seed, kind="bimax"):
     return v, synth.starts(counts)
 
 
-def compare(v, cs, p, step, m_state=None, cell_param=None, cell_key=None, workspace=256 << 20):
+def compare(v, cs, p, step, m_state=None, cell_param=None, cell_key=None, workspace=256 << 20, launch=None):
     need_gpu()
-    g = gpu_collide(v, cs, p, step, m_state=m_state, cell_param=cell_param, cell_key=cell_key, workspace=workspace)
+    g = gpu_collide(v, cs, p, step, m_state=m_state, cell_param=cell_param, cell_key=cell_key, workspace=workspace,
+                    launch=launch)
     vo, rep, ms = O.collide(v, cs, oracle_params(O, p), step, m_state=m_state,
                             cell_param=None if cell_param is None else np.asarray(cell_param, np.float64).ravel(),
                             cell_key=cell_key)
@@ -72,7 +73,13 @@ def test_collide_parity_wb(length, m_max, alpha, eps):
         assert np.array_equal(rep[:, 15], np.where(lone, 0, rep[:, 7]))
 
 
-def test_collide_parity_wb_large_cells():
+# Cells too large for shared memory, at the default launch (128 x 4) and at
+# 256 x 2, the shape of the large-cell workloads.
+BIG_LAUNCH = [None, (256, 2)]
+
+
+@pytest.mark.parametrize("launch", BIG_LAUNCH)
+def test_collide_parity_wb_large_cells(launch):
     """Deep trees (q near 1/2 over many levels) in cells that run from the
     overflow slab; enough rejections under every definition."""
     counts = [20000, 9000, 30000]
@@ -80,7 +87,7 @@ def test_collide_parity_wb_large_cells():
     for length, m_max in ((T.LEN_MIN, 2), (T.LEN_MEAN, 2), (T.LEN_K, 3)):
         p = T.collide_params(dt=0.7, eps=1.0, alpha=0.0, rho_scale=1.0 / np.array(counts).mean(), trunc=T.TRUNC_WB,
                              m=m_max, wb_length=length)
-        g, vo, rep = compare(v, cs, p, step=2, workspace=512 << 20)
+        g, vo, rep = compare(v, cs, p, step=2, workspace=512 << 20, launch=launch)
         assert rep[:, 15].sum() > 50
 
 
@@ -93,22 +100,39 @@ def test_collide_parity_rad_continuations():
     assert rep[:, 1].max() >= 2, "expected at least one continuation pass"
 
 
-def test_collide_parity_bkw_m4_indicator():
+@pytest.mark.parametrize("launch", BIG_LAUNCH)
+def test_collide_parity_bkw_m4_indicator(launch):
     v, cs = cells([5000, 20000], seed=4, kind="bkw")
     p = T.collide_params(dt=0.05, eps=1.0, alpha=0.0, rho_scale=1.0 / 20000, trunc=T.TRUNC_RAD, m=2,
                          indicator=T.IND_M4)
     ms = np.array([2, 4], np.int32)
     for step in range(3):
-        g, v, rep = compare(v, cs, p, step=step, m_state=ms)
+        g, v, rep = compare(v, cs, p, step=step, m_state=ms, launch=launch)
         ms = g["m_state"]
 
 
-def test_collide_parity_single_cell_1e5():
+@pytest.mark.parametrize("launch", BIG_LAUNCH)
+def test_collide_parity_single_cell_1e5(launch):
     """The homogeneous single-cell workload size (N = 1e5, BKW data): the
-    cell does not fit in shared memory and runs from the device slab."""
+    cell does not fit in shared memory; its changed particles are staged
+    compact and the rest stays in global memory."""
     v, cs = cells([100000], seed=5, kind="bkw")
     p = T.collide_params(dt=0.05, eps=1.0, alpha=0.0, rho_scale=1e-5, trunc=T.TRUNC_RAD, m=2, indicator=T.IND_M4)
-    compare(v, cs, p, step=0, m_state=np.array([2], np.int32))
+    compare(v, cs, p, step=0, m_state=np.array([2], np.int32), launch=launch)
+
+
+@pytest.mark.parametrize("launch", BIG_LAUNCH)
+@pytest.mark.parametrize("alpha,ind", [(1.0, T.IND_PXX), (0.6, T.IND_M4)])
+def test_collide_parity_large_cells_vhs(launch, alpha, ind):
+    """Cells too large for shared memory with the VHS bound and the P_xx
+    indicator (a second pass over the cell), next to small cells staged
+    whole, at every alignment of a cell's first and last particle against
+    16 bytes."""
+    counts = [13001, 7, 24577, 30002, 8195, 3, 41003]
+    v, cs = cells(counts, seed=12)
+    p = T.collide_params(dt=0.05, eps=0.02, alpha=alpha, rho_scale=1.0 / 20000, trunc=T.TRUNC_RAD, m=2,
+                         indicator=ind)
+    compare(v, cs, p, step=4, m_state=np.full(len(counts), 2, np.int32), workspace=512 << 20, launch=launch)
 
 
 def test_collide_per_cell_params_and_keys():
