@@ -557,17 +557,22 @@ __device__ __forceinline__ void raise_status(int *status, int code, int cell)
 // two modes are separate kernels: the compact path costs the whole path a few
 // per cent in registers and code size, so a launch takes it only when it has
 // a cell too large for shared memory.
-// WB: the kernel carries TRMC-WB (tree lengths, Sec. 4.4); the other
-// truncations run an instantiation without that code, about 5 % faster on
-// GB300 (smaller code in the hot loops, fewer instruction-cache misses).
+// TV: the truncation the instantiation serves -- TRMC-RAD with the P_xx or
+// the M4 indicator (Sec. 4.3), TRMC-WB (Sec. 4.4), or a fixed or unlimited
+// depth -- so that a kernel carries none of the other truncations' code in
+// its hot loops: on GB300 the smaller code runs 5-10 % faster (fewer
+// instruction-cache misses).
 enum { kWhole = 0, kDual = 1 };
+enum { kPlain = 0, kRadPxx = 1, kRadM4 = 2, kWb = 3 };
 struct Counts { int c[3]; };
 
-template <typename Real, int Mode, bool WB>
+template <typename Real, int Mode, int TV>
 __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<Real> &sh, unsigned char *dsm,
                                                char *slab, int cell)
 {
     const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
+    constexpr bool kRad = TV == kRadPxx || TV == kRadM4;
+    constexpr int kInd = TV == kRadM4 ? TRMC_IND_M4 : TRMC_IND_PXX;
     int cnt[3] = {0, 0, 0};
     Real *gx = static_cast<Real *>(a.vx), *gy = static_cast<Real *>(a.vy), *gz = static_cast<Real *>(a.vz);
     const int64_t base = a.cell_start[cell];
@@ -591,7 +596,7 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
         if (a.cell_key) { sh.problem = a.cell_key[cell] >> 32; sh.lcell = a.cell_key[cell] & 0xFFFFFFFFull; }
         else { sh.problem = a.problem_id; sh.lcell = uint64_t(cell); }
         int m0 = prm.trunc == TRMC_TRUNC_FIXED ? prm.m_fixed
-                 : prm.trunc == TRMC_TRUNC_RAD ? a.m_max[cell] : prm.m_cap;
+                 : kRad ? a.m_max[cell] : prm.m_cap;
         if (m0 < 1) m0 = 1;
         if (m0 > prm.m_cap) m0 = prm.m_cap;
         sh.m = m0; sh.m_next = m0; sh.m_first = m0; sh.lo = 0; sh.pass = 0; sh.npart = n; sh.skip = 0;
@@ -642,7 +647,7 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
                 int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
                 for (int j = 0; j < TRMC_REPORT_LEN; ++j) r[j] = 0;
                 r[0] = n;
-                r[4] = prm.trunc == TRMC_TRUNC_RAD ? sh.m : 0;
+                r[4] = kRad ? sh.m : 0;
                 r[6] = n;
             }
         }
@@ -666,8 +671,8 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
     // GB300 every FP64 instruction counts, so maxima of non-negative doubles
     // are taken on their bit patterns)
     {
-        const bool rad = prm.trunc == TRMC_TRUNC_RAD;
-        const bool need_m4 = rad && prm.indicator == TRMC_IND_M4, need_pxx = rad && prm.indicator == TRMC_IND_PXX;
+        const bool rad = kRad;
+        const bool need_m4 = rad && kInd == TRMC_IND_M4, need_pxx = rad && kInd == TRMC_IND_PXX;
         const bool need_d2 = sh.alpha != 0.0;
         // the particles are read from global memory and, for a cell staged
         // whole, stored in shared memory (a larger cell stages the changed ones
@@ -979,7 +984,7 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
                                                    3 * size_t(d0 + 1) * sizeof(Real)));
                 if (!sh.IBuf || !sh.OBuf) sh.skip = 1;
                 sh.ILBuf = sh.OLBuf = nullptr; sh.ext = nullptr;
-                if (WB) {
+                if (TV == kWb) {
                     sh.ILBuf = static_cast<double *>(take(ps, pcs, pg, pcg,
                                                           8 * size_t(Dge1 + 1)));
                     sh.OLBuf = static_cast<double *>(take(ps, pcs, pg, pcg,
@@ -1330,7 +1335,7 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
         Real *OBx = sh.OBuf, *OBy = sh.OBuf + (D0 + 1), *OBz = sh.OBuf + 2 * (D0 + 1);
         const Real alpha = Real(sh.alpha), Sigma = Real(sh.Sigma);
         const double Sigma2 = double(Sigma) * double(Sigma);
-        const int wb = WB ? prm.wb_length : 0;
+        const int wb = TV == kWb ? prm.wb_length : 0;
         double *IL = sh.ILBuf, *OL = sh.OLBuf;
         auto level_setup = [&](int lv) {          // warp 0: label prefix and product key
             const int32_t *row = sh.Mt + tri(lv);
@@ -1632,7 +1637,7 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
             // cs[0..3]: change of momentum and energy over the leaves, cs[4..7]: the
             // thermalised set's momentum and energy, cs[8], cs[9]: the indicator's
             // change and the set's indicator (TRMC-RAD only)
-            const bool rad = prm.trunc == TRMC_TRUNC_RAD;
+            const bool rad = kRad;
             const Real Ux = Real(sh.U[0]);
             auto place = [&](Sum<Real> (&cs)[10], int jx) {
                 const int sl = pos(n0 + jx);
@@ -1642,11 +1647,11 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
                 if constexpr (sizeof(Real) == 8) {
                     cs[0].add(x - ox); cs[1].add(y - oy); cs[2].add(z - oz);
                     cs[3].add((x * x + y * y + z * z) - (ox * ox + oy * oy + oz * oz));
-                    if (rad) cs[8].add(indicator(x, y, z, sh.U, prm.indicator) - indicator(ox, oy, oz, sh.U, prm.indicator));
+                    if (rad) cs[8].add(indicator(x, y, z, sh.U, kInd) - indicator(ox, oy, oz, sh.U, kInd));
                 } else {
                     cs[0].add(x); cs[0].add(-ox); cs[1].add(y); cs[1].add(-oy); cs[2].add(z); cs[2].add(-oz);
                     cs[3].add_sq3(x, y, z); cs[3].sub_sq3(ox, oy, oz);
-                    if (rad) cs[8].add(indicator_r(x, y, z, Ux, prm.indicator) - indicator_r(ox, oy, oz, Ux, prm.indicator));
+                    if (rad) cs[8].add(indicator_r(x, y, z, Ux, kInd) - indicator_r(ox, oy, oz, Ux, kInd));
                 }
             };
             auto pool_add = [&](Sum<Real> (&cs)[10], int sl) {
@@ -1654,8 +1659,8 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
                 cs[4].add(x); cs[5].add(y); cs[6].add(z);
                 cs[7].add_sq3(x, y, z);
                 if (rad) {
-                    if constexpr (sizeof(Real) == 8) cs[9].add(indicator(x, y, z, sh.U, prm.indicator));
-                    else cs[9].add(indicator_r(x, y, z, Ux, prm.indicator));
+                    if constexpr (sizeof(Real) == 8) cs[9].add(indicator(x, y, z, sh.U, kInd));
+                    else cs[9].add(indicator_r(x, y, z, Ux, kInd));
                 }
             };
             // TRMC-WB (Alg. 4.6): an output whose tree is longer than m_max is
@@ -1663,7 +1668,7 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
             // own members, in output order.  A lone rejected output with no
             // thermalised set is kept: its only Maxwellian resample with the
             // same momentum and energy is itself.
-            const bool wbm = WB;
+            const bool wbm = TV == kWb;
             const double mmax = double(prm.m_fixed);
             const double *OL = sh.OLBuf;
             bool keep_all = false;
@@ -1722,19 +1727,19 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
         // TRMC-RAD test (Sec. 4.3)
         if (tid == 0) {
             sh.cont = 0;
-            if (prm.trunc == TRMC_TRUNC_RAD) {
+            if (kRad) {
                 const int R = sh.R;
                 double Sth = 0.0;
                 if (R == 1) {
                     const int sl = pos(n0 + D0);
-                    Sth = indicator(double(Vcx()[sl]), double(Vcy()[sl]), double(Vcz()[sl]), sh.U, prm.indicator);
+                    Sth = indicator(double(Vcx()[sl]), double(Vcy()[sl]), double(Vcz()[sl]), sh.U, kInd);
                 } else if (R >= 2) {
                     const double Pt0 = sh.Pp[0] - sh.dP[0], Pt1 = sh.Pp[1] - sh.dP[1], Pt2 = sh.Pp[2] - sh.dP[2];
                     const double Et = sh.Ep - sh.dE;
                     double et = Et - (Pt0 * Pt0 + Pt1 * Pt1 + Pt2 * Pt2) / double(R);
                     if (et < 0.0) et = 0.0;
                     const double u0 = Pt0 / double(R), u1 = Pt1 / double(R), u2 = Pt2 / double(R);
-                    if (prm.indicator == TRMC_IND_M4) {
+                    if (kInd == TRMC_IND_M4) {
                         const double Tp = et / (3.0 * double(R));
                         const double uu = u0 * u0 + u1 * u1 + u2 * u2;
                         Sth = double(R) * (uu * uu + 10.0 * uu * Tp + 15.0 * Tp * Tp);
@@ -1926,7 +1931,7 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
         if (tid == 0) a.cell_vmax2[cell] = vmax;
     }
     if (tid == 0) {
-        if (prm.trunc == TRMC_TRUNC_RAD) a.m_max[cell] = sh.m_next;
+        if (kRad) a.m_max[cell] = sh.m_next;
         if (a.report) {
             int64_t *r = a.report + int64_t(cell) * TRMC_REPORT_LEN;
             r[0] = n; r[1] = sh.pass + 1; r[2] = sh.m_first; r[3] = sh.m; r[4] = sh.m_next; r[5] = R;
@@ -1941,7 +1946,7 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
 // per SM (at most 85 registers a thread; it then spills a few bytes), which
 // runs the stationary shock's 2500-particle cells 4 % faster than two; the
 // others, with more live FP64 state or the compact path, for two.
-template <typename Real, int Mode, bool WB>
+template <typename Real, int Mode, int TV>
 __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 && Mode == kWhole ? 3 : 2) collide_kernel(Args a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -1960,7 +1965,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 && Mode == kWhole 
         if (ticket >= a.n_cells) break;
         const int cell = a.cell_order ? a.cell_order[ticket] : ticket;
         const long long t_start = clock64();
-        const Counts k = process_cell<Real, Mode, WB>(a, step, sh, dsm, slab, cell);
+        const Counts k = process_cell<Real, Mode, TV>(a, step, sh, dsm, slab, cell);
         int cnt[3] = {k.c[0], k.c[1], k.c[2]};      // collisions, dummy, exceed
         if (threadIdx.x == 0 && unsigned(sh.n) > n_max) n_max = unsigned(sh.n);
         if (a.cell_cost && threadIdx.x == 0) {
@@ -2045,35 +2050,50 @@ __global__ void __launch_bounds__(1024) order_kernel(const uint32_t *cost, int n
 // The kernel's dynamic shared-memory limit, set once per device to the most a
 // CTA can have, so that every launch shape (and the allocation-free entry
 // point) fits under it whatever order they come in.
-template <typename Real, int Mode, bool WB>
+template <typename Real, int Mode, int TV>
 cudaError_t allow_max_smem(int device, int smem_optin)
 {
     constexpr int kDev = 64;
     static bool done[kDev] = {};
     if (device >= 0 && device < kDev && done[device]) return cudaSuccess;
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, collide_kernel<Real, Mode, WB>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, collide_kernel<Real, Mode, TV>);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(collide_kernel<Real, Mode, WB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(collide_kernel<Real, Mode, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smem_optin - int(fa.sharedSizeBytes));
     if (e == cudaSuccess && device >= 0 && device < kDev) done[device] = true;
     return e;
 }
 
-// The instantiation for a launch: staging mode and TRMC-WB support, with its
+// The instantiation for a launch (staging mode, truncation), with its
 // shared-memory limit raised.
 using CollideFn = void (*)(Args);
-template <typename Real>
-cudaError_t collide_fn(int device, int smem_optin, bool dual, bool wb, CollideFn &fn)
+template <typename Real, int Mode, int TV>
+cudaError_t pick(int device, int smem_optin, CollideFn &fn)
 {
-    if (dual) {
-        fn = wb ? collide_kernel<Real, kDual, true> : collide_kernel<Real, kDual, false>;
-        return wb ? allow_max_smem<Real, kDual, true>(device, smem_optin)
-                  : allow_max_smem<Real, kDual, false>(device, smem_optin);
+    fn = collide_kernel<Real, Mode, TV>;
+    return allow_max_smem<Real, Mode, TV>(device, smem_optin);
+}
+
+int variant_of(const trmc_collide_params *prm)
+{
+    if (prm->trunc == TRMC_TRUNC_RAD) return prm->indicator == TRMC_IND_M4 ? kRadM4 : kRadPxx;
+    return prm->trunc == TRMC_TRUNC_WB ? kWb : kPlain;
+}
+
+template <typename Real>
+cudaError_t collide_fn(int device, int smem_optin, bool dual, const trmc_collide_params *prm, CollideFn &fn)
+{
+    switch (variant_of(prm) + (dual ? 4 : 0)) {
+    case kPlain: return pick<Real, kWhole, kPlain>(device, smem_optin, fn);
+    case kRadPxx: return pick<Real, kWhole, kRadPxx>(device, smem_optin, fn);
+    case kRadM4: return pick<Real, kWhole, kRadM4>(device, smem_optin, fn);
+    case kWb: return pick<Real, kWhole, kWb>(device, smem_optin, fn);
+    case 4 + kPlain: return pick<Real, kDual, kPlain>(device, smem_optin, fn);
+    case 4 + kRadPxx: return pick<Real, kDual, kRadPxx>(device, smem_optin, fn);
+    case 4 + kRadM4: return pick<Real, kDual, kRadM4>(device, smem_optin, fn);
+    default: return pick<Real, kDual, kWb>(device, smem_optin, fn);
     }
-    fn = wb ? collide_kernel<Real, kWhole, true> : collide_kernel<Real, kWhole, false>;
-    return wb ? allow_max_smem<Real, kWhole, true>(device, smem_optin)
-              : allow_max_smem<Real, kWhole, false>(device, smem_optin);
 }
 
 // Does a cell of n particles fit in one CTA's shared memory staged whole
@@ -2111,7 +2131,7 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     // for shared memory (the first launch of a context does not know: dual)
     const bool dual = !ctx->n_max_host || !fits_whole<Real>(*ctx->n_max_host, smem);
     CollideFn fn = nullptr;
-    cudaError_t e = collide_fn<Real>(ctx->device, int(ctx->smem_optin), dual, prm->trunc == TRMC_TRUNC_WB, fn);
+    cudaError_t e = collide_fn<Real>(ctx->device, int(ctx->smem_optin), dual, prm, fn);
     if (e != cudaSuccess) return cuda_error(ctx, e, "cudaFuncSetAttribute(collide)");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
@@ -2224,7 +2244,7 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
     }
     const int smem = collide_smem<Real>(D.smem_optin, per_sm_target);
     CollideFn fn = nullptr;
-    if (collide_fn<Real>(dev, D.smem_optin, true, prm->trunc == TRMC_TRUNC_WB, fn) != cudaSuccess) return TRMC_ERR_CUDA;
+    if (collide_fn<Real>(dev, D.smem_optin, true, prm, fn) != cudaSuccess) return TRMC_ERR_CUDA;
     const size_t avail = size_t(TRMC_STATIC_SCRATCH_BYTES) - kStaticControl;
     const size_t need = static_cell_bytes(max_cell, sizeof(Real), prm->trunc == TRMC_TRUNC_WB);
     int grid = int(std::min<size_t>(avail / need, size_t(D.num_sms) * per_sm_target));
