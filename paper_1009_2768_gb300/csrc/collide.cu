@@ -2099,11 +2099,25 @@ cudaError_t collide_fn(int device, int smem_optin, bool dual, const trmc_collide
 // Does a cell of n particles fit in one CTA's shared memory staged whole
 // (velocities, change bitmap, slot table)?  The same test as the kernel's.
 template <typename Real>
-bool fits_whole(uint64_t n, int smem)
+size_t whole_bytes(uint64_t n)
 {
     auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
-    return a16(3 * size_t(n) * sizeof(Real)) + a16(4 * size_t((n + 31) / 32)) + a16(4 * size_t(n)) <= size_t(smem);
+    return a16(3 * size_t(n) * sizeof(Real)) + a16(4 * size_t((n + 31) / 32)) + a16(4 * size_t(n));
 }
+
+template <typename Real>
+bool fits_whole(uint64_t n, int smem) { return whole_bytes<Real>(n) <= size_t(smem); }
+
+size_t static_cell_bytes(int64_t n, size_t real, bool wb);
+
+// A launch whose largest cell needs at most 5/4 of a CTA's shared memory
+// stays in the whole-staging mode when the cell fits its CTA's slab: the few
+// cells that do not fit are staged whole in global memory, and every other
+// cell keeps the faster kernel (more CTAs per SM).  Cells larger still are on
+// the launch's critical path, and the dual kernel's compact staging serves
+// them better.
+template <typename Real>
+bool near_whole(uint64_t n, int smem) { return whole_bytes<Real>(n) * 4 <= size_t(smem) * 5; }
 
 // Dynamic shared memory of one CTA when per_sm CTAs share an SM: the SM's
 // budget (226 KB where the device lets a CTA opt in to 200 KB or more, else
@@ -2128,10 +2142,13 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     const int threads = ctx->collide_threads, per_sm_target = ctx->collide_ctas_per_sm;
     const int smem = collide_smem<Real>(int(ctx->smem_optin), per_sm_target);
     // the mode: staged whole, unless the previous launch met a cell too large
-    // for shared memory (the first launch of a context does not know: dual)
-    const bool dual = !ctx->n_max_host || !fits_whole<Real>(*ctx->n_max_host, smem);
+    // for shared memory and for the whole-mode rule above (the first launch
+    // of a context does not know: dual)
+    const uint64_t nmax = ctx->n_max_host ? *ctx->n_max_host : ~0ull;
+    bool dual = !fits_whole<Real>(nmax, smem);
+    const bool near = dual && near_whole<Real>(nmax, smem);
     CollideFn fn = nullptr;
-    cudaError_t e = collide_fn<Real>(ctx->device, int(ctx->smem_optin), dual, prm, fn);
+    cudaError_t e = collide_fn<Real>(ctx->device, int(ctx->smem_optin), dual && !near, prm, fn);
     if (e != cudaSuccess) return cuda_error(ctx, e, "cudaFuncSetAttribute(collide)");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
@@ -2140,6 +2157,21 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     int grid = ctx->num_sms * per_sm;
     if (grid > st->n_cells) grid = st->n_cells;
     if (grid < 1) return TRMC_OK;
+    if (near) {
+        // whole mode if the largest cell, with room for its plan, fits a slab
+        const size_t slab = (ctx->slabs_bytes / size_t(grid)) & ~size_t(255);
+        dual = whole_bytes<Real>(nmax) + static_cell_bytes(int64_t(nmax), sizeof(Real), prm->trunc == TRMC_TRUNC_WB) >
+               slab;
+        if (dual) {
+            e = collide_fn<Real>(ctx->device, int(ctx->smem_optin), true, prm, fn);
+            if (e != cudaSuccess) return cuda_error(ctx, e, "cudaFuncSetAttribute(collide)");
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+            if (e != cudaSuccess) return cuda_error(ctx, e, "occupancy(collide)");
+            if (per_sm < 1) per_sm = 1;
+            grid = ctx->num_sms * per_sm;
+            if (grid > st->n_cells) grid = st->n_cells;
+        }
+    }
     Args a;
     a.vx = st->vx; a.vy = st->vy; a.vz = st->vz;
     a.cell_start = st->cell_start;

@@ -62,6 +62,23 @@ def test_results_are_bit_identical_across_launch_shapes(precision, name):
             assert np.array_equal(a, b), f"launch shape {shape} differs from {SHAPES[0]} ({name})"
 
 
+@pytest.mark.parametrize("precision,shape", [(T.FP32_MIXED, (256, 3)), (T.FP64, (256, 2))])
+def test_whole_mode_with_cells_in_the_slab(precision, shape):
+    """Cells a little too large for shared memory (here up to 4100 particles,
+    against room for about 3950 FP32 or 3640 FP64 ones) keep the launch in
+    the whole-staging kernel, those cells staged in global memory, from the
+    second launch of a context on: the same bits as the dual kernel, which
+    the smallest CTAs run."""
+    need_gpu()
+    counts = [3000, 3950, 4100, 2500, 3700, 17]
+    params = PARAMS["rad hard spheres"]
+    carry = precision == T.FP32_MIXED
+    ref = run_shape(precision, (64, 8), params, counts, steps=3, carry=carry)
+    got = run_shape(precision, shape, params, counts, steps=3, carry=carry)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
 def test_sort_schedule_does_not_change_transport():
     """The counting sort is stable whatever its CTA size: shock tubes stepped
     with 64, 128 or 256 threads per cell CTA (and the library's own pick) end
