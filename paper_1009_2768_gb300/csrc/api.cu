@@ -24,7 +24,7 @@ trmc_status cuda_error(trmc_ctx *ctx, cudaError_t e, const char *where)
 
 namespace {
 
-constexpr size_t kControlBytes = 4096;
+constexpr size_t kControlBytes = 4096 + 32768;     // status, tickets; large-cell table
 
 trmc_status check_state(trmc_ctx *ctx, const trmc_state *st)
 {
@@ -100,6 +100,8 @@ trmc_status trmc_create(trmc_ctx **out, int32_t precision, uint64_t seed, size_t
     if (e != cudaSuccess) { cudaFree(ctx->workspace); delete ctx; return TRMC_ERR_CUDA; }
     ctx->status = reinterpret_cast<int *>(ctx->workspace);
     ctx->tickets = reinterpret_cast<unsigned int *>(ctx->workspace + 64);
+    ctx->big = reinterpret_cast<trmc::BigEntry *>(ctx->workspace + 4096);
+    static_assert(sizeof(trmc::BigEntry) * trmc::kBigSlots <= 32768, "large-cell table");
     // the largest cell of the last collide launch, written by the device into
     // host-mapped memory and read by the next launch without a copy
     unsigned int *h = nullptr;

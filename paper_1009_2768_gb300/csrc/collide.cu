@@ -74,6 +74,8 @@ struct Args {
     size_t slab_bytes;
     int smem_bytes;
     int warp_level;
+    const BigEntry *big;             // NULL, or the pre-pass's sums of this launch's large cells
+    uint64_t big_stamp;              // this launch's number in big[].stamp
 };
 
 template <typename Real>
@@ -682,7 +684,16 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
         const bool full = Mode == kWhole || sh.full;
         Real *Vx = sh.Vc, *Vy = sh.Vc + n, *Vz = sh.Vc + 2 * n;
         constexpr int U = 4;      // loads issued together, ahead of the sums they feed
-        for (int vw = warp; vw < kVW; vw += nw) {
+        // a large cell not staged whole: its virtual warps' partial sums, when
+        // the pre-pass of this launch made them (the same values), else here
+        const BigEntry *pre = nullptr;
+        if (Mode == kDual && !full && a.big && n >= kBigCell) {
+            const BigEntry *e = a.big + cell % kBigSlots;
+            if (e->cell == cell && e->stamp == a.big_stamp) pre = e;
+        }
+        if (pre)
+            for (int j = tid; j < kVW * (need_m4 ? 5 : 4); j += bs) sh.red[j] = pre->part[j];
+        for (int vw = warp; !pre && vw < kVW; vw += nw) {
             Sum<Real> acc[5];
             for (int i0 = 32 * vw + lane; i0 < n; i0 += U * 32 * kVW) {
                 Real x[U], y[U], z[U];
@@ -1946,6 +1957,60 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
 // per SM (at most 85 registers a thread; it then spills a few bytes), which
 // runs the stationary shock's 2500-particle cells 4 % faster than two; the
 // others, with more live FP64 state or the compact path, for two.
+// Pre-pass of the large cells' moment sums: CTA (slot, vw) of one warp finds
+// the slot's cell -- the first cell c = slot (mod kBigSlots) of at least
+// kBigCell particles -- and sums virtual warp vw's lanes over it exactly as the
+// collide kernel would (same loop, same vw_put), so the eight virtual warps of
+// a large cell run on eight SMs.  GB300 issues FP64 at 2 lanes per clock and
+// SM: alone, the one CTA of a cell of 1e5 FP64 particles spends about half its
+// time here.
+template <typename Real, bool M4>
+__global__ void __launch_bounds__(32) bigsum_kernel(const Real *__restrict__ gx, const Real *__restrict__ gy,
+                                                    const Real *__restrict__ gz, const int64_t *__restrict__ cell_start,
+                                                    int n_cells, BigEntry *big, uint64_t stamp)
+{
+    // one warp per SM: many loads in flight per lane (same order of the sums)
+    constexpr int K = M4 ? 5 : 4, U = 16;
+    __shared__ double scr[kVW * 5];
+    const int slot = blockIdx.x / kVW, vw = blockIdx.x % kVW, lane = threadIdx.x;
+    int cell = -1;
+    for (int c0 = slot; c0 < n_cells && cell < 0; c0 += 32 * kBigSlots) {
+        const int c = c0 + lane * kBigSlots;
+        const bool large = c < n_cells && cell_start[c + 1] - cell_start[c] >= kBigCell;
+        const unsigned b = __ballot_sync(0xffffffffu, large);
+        if (b) cell = c0 + (__ffs(b) - 1) * kBigSlots;
+    }
+    if (cell < 0) return;
+    const int64_t base = cell_start[cell];
+    const int n = int(cell_start[cell + 1] - base);
+    Sum<Real> acc[5];
+    for (int i0 = 32 * vw + lane; i0 < n; i0 += U * 32 * kVW) {
+        Real x[U], y[U], z[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * 32 * kVW;
+            if (i < n) { x[u] = gx[base + i]; y[u] = gy[base + i]; z[u] = gz[base + i]; }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * 32 * kVW;
+            if (i < n) {
+                acc[0].add(x[u]); acc[1].add(y[u]); acc[2].add(z[u]);
+                acc[3].add_sq3(x[u], y[u], z[u]);
+                if (M4) {
+                    const Real e = x[u] * x[u] + y[u] * y[u] + z[u] * z[u];
+                    acc[4].add(e * e);
+                }
+            }
+        }
+    }
+    vw_put<K>(acc, scr, vw);
+    __syncwarp();
+    BigEntry *e = big + slot;
+    if (lane < K) e->part[vw * K + lane] = scr[vw * K + lane];
+    if (vw == 0 && lane == 0) { e->cell = cell; e->stamp = stamp; }
+}
+
 template <typename Real, int Mode, int TV>
 __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 && Mode == kWhole ? 3 : 2) collide_kernel(Args a)
 {
@@ -2193,6 +2258,20 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     a.status = ctx->status;
     a.tickets = ctx->tickets;
     a.n_max_host = ctx->n_max_dev;
+    a.big = nullptr;
+    a.big_stamp = 0;
+    if (dual && nmax >= uint64_t(kBigCell) && ctx->big) {
+        // the large cells' moment sums over eight SMs each, first
+        a.big = ctx->big;
+        a.big_stamp = ++ctx->big_stamp;
+        const bool m4 = prm->trunc == TRMC_TRUNC_RAD && prm->indicator == TRMC_IND_M4;
+        const Real *vx = static_cast<const Real *>(st->vx), *vy = static_cast<const Real *>(st->vy),
+                   *vz = static_cast<const Real *>(st->vz);
+        if (m4) bigsum_kernel<Real, true><<<kBigSlots * kVW, 32, 0, s>>>(vx, vy, vz, st->cell_start, st->n_cells,
+                                                                          ctx->big, a.big_stamp);
+        else bigsum_kernel<Real, false><<<kBigSlots * kVW, 32, 0, s>>>(vx, vy, vz, st->cell_start, st->n_cells,
+                                                                         ctx->big, a.big_stamp);
+    }
     a.slabs = ctx->slabs;
     a.slab_bytes = (ctx->slabs_bytes / size_t(grid)) & ~size_t(255);
     a.smem_bytes = smem;
@@ -2305,6 +2384,8 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
     a.status = status_dev ? status_dev : reinterpret_cast<int *>(D.scratch);
     a.tickets = reinterpret_cast<unsigned int *>(D.scratch + 64);
     a.n_max_host = nullptr;
+    a.big = nullptr;
+    a.big_stamp = 0;
     a.slabs = D.scratch + kStaticControl;
     a.slab_bytes = (avail / size_t(grid)) & ~size_t(255);
     a.smem_bytes = smem;

@@ -7,6 +7,19 @@
 
 #include "trmc.h"
 
+namespace trmc {
+// A cell of at least kBigCell particles gets its moment sums from a pre-pass
+// spread over eight CTAs (one per virtual warp of the canonical sums) instead
+// of its own CTA alone: one table entry per slot, slot = cell mod kBigSlots.
+constexpr int kBigCell = 32768;
+constexpr int kBigSlots = 64;
+struct BigEntry {
+    int64_t cell;                     // the slot's cell in the launch that wrote it
+    uint64_t stamp;                   // that launch's number
+    double part[8 * 5];               // per virtual warp, its K partial sums as the CTA stores them
+};
+}  // namespace trmc
+
 struct trmc_ctx {
     int precision = 0;
     uint64_t seed = 0;
@@ -18,6 +31,8 @@ struct trmc_ctx {
     size_t workspace_bytes = 0;
     int *status = nullptr;            // [0] error code, [1] detail (cell), [2..3] spare
     unsigned int *tickets = nullptr;  // [0] next cell, [1] CTAs done, [2] largest cell (collide)
+    trmc::BigEntry *big = nullptr;    // [kBigSlots] large cells' moment sums (control block)
+    uint64_t big_stamp = 0;           // collide launches that ran the pre-pass
     // host-mapped word: the largest cell of the last collide launch (written by
     // its last CTA; UINT_MAX until the first launch), and its device address
     volatile unsigned int *n_max_host = nullptr;

@@ -79,6 +79,38 @@ def test_whole_mode_with_cells_in_the_slab(precision, shape):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", [T.FP64, T.FP32_MIXED])
+@pytest.mark.parametrize("alpha,ind", [(0.0, T.IND_M4), (1.0, T.IND_PXX)])
+def test_large_cells_moment_prepass_gives_the_same_bits(precision, alpha, ind):
+    """Cells of at least 32768 particles get their moment sums from a pre-pass
+    that spreads the eight virtual warps over eight CTAs; the allocation-free
+    entry point sums them in the cell's own CTA.  Two steps, same bits."""
+    need_gpu()
+    ensure_built()
+    counts = [40000, 5, 70001, 1200, 33000]
+    g = synth.rng(21)
+    v = np.concatenate([synth.bkw(n, 0.6, g=g) for n in counts], axis=1)
+    cs = synth.starts(counts)
+    p = T.collide_params(dt=0.05, eps=0.5, alpha=alpha, rho_scale=1.0 / 40000, trunc=T.TRUNC_RAD, m=2, indicator=ind)
+    sts = []
+    for _ in range(2):
+        st = T.ParticleState(cs, precision=precision, rad=True)
+        st.set_velocities(v)
+        st.m_max.fill_(2)
+        sts.append(st)
+    c = T.trmc_create(precision, 0, 1 << 30)
+    status = torch.zeros(2, dtype=torch.int32, device="cuda")
+    for step in (0, 1):
+        T.trmc_collide(c, sts[0], p, step)
+        T.trmc_check(c)
+        T.trmc_collide_static(sts[1], p, precision, 0, step, max(counts), status)
+        torch.cuda.synchronize()
+        assert status.tolist() == [0, 0]
+        for a, b in ((sts[0].v, sts[1].v), (sts[0].m_max, sts[1].m_max), (sts[0].cell_vmax2, sts[1].cell_vmax2)):
+            assert torch.equal(a, b)
+    T.trmc_destroy(c)
+
+
 def test_sort_schedule_does_not_change_transport():
     """The counting sort is stable whatever its CTA size: shock tubes stepped
     with 64, 128 or 256 threads per cell CTA (and the library's own pick) end
