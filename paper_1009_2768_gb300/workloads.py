@@ -100,6 +100,8 @@ class HomogeneousBKW:
         self.params = T.collide_params(dt=dt, eps=eps, alpha=0.0, rho_scale=1.0 / n, trunc=trunc, m=m_init,
                                        indicator=T.IND_M4)
         self.step_index = 0
+        # a cell of 32768 particles or more: the moment pre-pass, then collide
+        self.launches_per_step = 2 if n >= 32768 else 1
 
     def step(self, stats=None, events=None):
         if events:
@@ -109,8 +111,6 @@ class HomogeneousBKW:
         if events:
             events[2].record()
         self.step_index += 1
-
-    launches_per_step = 1
 
     def close(self):
         T.trmc_destroy(self.ctx)
