@@ -1953,10 +1953,6 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
     return Counts{{cnt[0], cnt[1], cnt[2]}};
 }
 
-// Registers: the FP32 whole-mode kernel is built for three 256-thread CTAs
-// per SM (at most 85 registers a thread; it then spills a few bytes), which
-// runs the stationary shock's 2500-particle cells 4 % faster than two; the
-// others, with more live FP64 state or the compact path, for two.
 // Pre-pass of the large cells' moment sums: CTA (slot, vw) of one warp finds
 // the slot's cell -- the first cell c = slot (mod kBigSlots) of at least
 // kBigCell particles -- and sums virtual warp vw's lanes over it exactly as the
@@ -2011,6 +2007,10 @@ __global__ void __launch_bounds__(32) bigsum_kernel(const Real *__restrict__ gx,
     if (vw == 0 && lane == 0) { e->cell = cell; e->stamp = stamp; }
 }
 
+// Registers: the FP32 whole-mode kernel is built for three 256-thread CTAs
+// per SM (at most 85 registers a thread; it then spills a few bytes), which
+// runs the stationary shock's 2500-particle cells 4 % faster than two; the
+// others, with more live FP64 state or the compact path, for two.
 template <typename Real, int Mode, int TV>
 __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 && Mode == kWhole ? 3 : 2) collide_kernel(Args a)
 {
