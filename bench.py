@@ -58,16 +58,21 @@ METRIC = "particle-steps/s"
 DEFAULT_WORKLOAD = "stationary"
 COMPARE_STEPS = 20          # steps of the oracle comparison (moment error, CPU baseline)
 
-# DRAM traffic per collide launch from `ncu` (dram__bytes_read.sum + dram__bytes_write.sum)
-# of the same command, keyed by the hash of csrc/collide.cu it was taken on; reported as
-# null once the kernel source differs.  See profiles/.
+# Per collide launch, from `ncu` on the same command (one whole-staging launch of the
+# stationary shock and the shock tubes, one dual launch of the batched relaxation): DRAM
+# traffic (dram__bytes_read.sum + dram__bytes_write.sum), issue and warp activity and the
+# leading stall reasons, keyed by the hash of csrc/collide.cu they were taken on; reported
+# as null once the kernel source differs.  See profiles/.
 NCU_TRAFFIC = {
-    "shock": {"collide_sha": "9c49268e95ea6d53", "launch": (128, 3), "bytes": 24382208 + 482048,
-              "fp64_pipe_active_pct": 41.7},
-    "stationary": {"collide_sha": "9c49268e95ea6d53", "launch": (256, 2), "bytes": 123458048 + 75530496,
-                   "fp64_pipe_active_pct": 10.7},
-    "batched": {"collide_sha": "9c49268e95ea6d53", "launch": (256, 2), "bytes": 90179072 + 93251072,
-                "fp64_pipe_active_pct": 8.8},
+    "stationary": {"collide_sha": "82ba48567694e3b1", "launch": (256, 3), "bytes": 123997440 + 98976512,
+                   "issue_active_pct": 34.3, "warps_active_pct": 36.5,
+                   "stalls_per_issue": {"barrier": 7.15, "no_instruction": 2.86, "wait": 2.38, "long_scoreboard": 1.42}},
+    "shock": {"collide_sha": "82ba48567694e3b1", "launch": (128, 4), "bytes": 20232704 + 1046272,
+              "issue_active_pct": 18.0, "warps_active_pct": 22.9,
+              "stalls_per_issue": {"barrier": 6.98, "wait": 4.03, "short_scoreboard": 3.73, "no_instruction": 2.78}},
+    "batched": {"collide_sha": "82ba48567694e3b1", "launch": (256, 2), "bytes": 83904000 + 51153664,
+                "issue_active_pct": 30.9, "warps_active_pct": 24.8,
+                "stalls_per_issue": {"barrier": 4.93, "wait": 2.39, "long_scoreboard": 1.24, "no_instruction": 1.04}},
 }
 
 # Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
@@ -556,8 +561,14 @@ def ours(args):
     roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
             "collide_ms": float(co_ms.mean()), "transport_ms": float(tr_ms.mean()),
-            "algorithmic_bytes_per_launch": abytes,
-            "fp64_pipe_active_pct": tr_rec.get("fp64_pipe_active_pct") if fresh else None}
+            "algorithmic_bytes_per_launch": abytes}
+    if fresh:
+        # what bounds the kernel instead, from the same ncu capture: a kernel
+        # whose DRAM throughput and issue rate are both low waits on latency
+        top = max(tr_rec["stalls_per_issue"], key=tr_rec["stalls_per_issue"].get)
+        roof["limiter"] = {"kind": "latency", "issue_active_pct": tr_rec["issue_active_pct"],
+                           "warps_active_pct": tr_rec["warps_active_pct"],
+                           "stalls_per_issue": tr_rec["stalls_per_issue"], "top_stall": top}
 
     # end to end: host-resident state, H2D + step + D2H every step
     e2e = None
