@@ -511,6 +511,9 @@ def ours(args):
         best = tuned["collide_best"]
         launch = {"threads": best[0], "ctas_per_sm": best[1],
                   "tuned_ms": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in tuned["collide"].items()},
+                  "work_schedule": {"warp_particles": tuned["work_best"][0],
+                                    "records_per_thread": tuned["work_best"][1]},
+                  "work_tuned_ms": {f"{k[0]}/{k[1]}": round(v, 4) for k, v in tuned["work"].items()},
                   "sort_threads": tuned["sort_best"],
                   "sort_tuned_ms": {str(k): round(v, 4) for k, v in tuned["sort"].items()}}
         for _ in range(2):
@@ -798,7 +801,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--tune", action="store_true", help="choose the collide launch shape and the sort schedule with the autotuner")
+    ap.add_argument("--tune", action="store_true", help="choose the collide launch shape, the work schedule inside a cell (particles per warp, records per thread) and the sort schedule with the autotuner")
     ap.add_argument("--launch", default="", help="collide launch shape THREADSxCTAS_PER_SM (default: per workload)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=["stationary", "shock", "batched", "bkw", "serving"])
     ap.add_argument("--rates", default="1,10,50,200", help="serving: arrival rates (requests/s) to sweep")

@@ -184,6 +184,24 @@ trmc_status trmc_check(trmc_ctx *ctx, void *stream);
  * only speed does (the autotuner in the binding sweeps it). */
 trmc_status trmc_set_collide_launch(trmc_ctx *ctx, int32_t threads, int32_t ctas_per_sm);
 
+/* Work schedule of the collision kernel inside a cell.  The paper has no
+ * counterpart (its trees run one collision at a time); results do not depend
+ * on it, only speed does (the autotuner in the binding sweeps it).
+ *  - warp_particles: a tree level of at most this many particles (two per
+ *    collision) runs in one warp, with warp-level synchronisation only; the
+ *    larger ones are spread over the CTA.  Even, in [2, 8192], or 0 for the
+ *    default (64 in FP64 contexts, 256 in FP32-mixed ones).
+ *  - records_per_thread: the input-independent part of every collision (its
+ *    draw, threshold and direction, its input and product slots) is computed
+ *    up front, by the whole CTA, for the levels of at most this many
+ *    collisions per thread (and for every level one warp takes); a level then
+ *    only loads, collides and stores.  In [1, 16], or 0 for the default (4); larger
+ *    values need more shared memory per cell (32 B a collision in FP32-mixed
+ *    contexts, 48 B in FP64), and a cell without room for them computes in
+ *    place.
+ * Returns TRMC_ERR_ARG for values outside those ranges. */
+trmc_status trmc_set_collide_schedule(trmc_ctx *ctx, int32_t warp_particles, int32_t records_per_thread);
+
 /* Launch shape of the transport's counting sort (the count and scatter
  * kernels, one CTA per old cell): threads per CTA, a multiple of 32 in
  * [32, 256], or 0 (the default) for a size picked from the mean cell size

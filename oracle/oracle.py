@@ -74,6 +74,7 @@ def lib():
         _lib.orc_prp_init.argtypes = [P, C.c_uint64, P]
         _lib.orc_prp_fwd.argtypes = [P, C.c_uint64]; _lib.orc_prp_fwd.restype = C.c_uint64
         _lib.orc_prp_inv.argtypes = [P, C.c_uint64]; _lib.orc_prp_inv.restype = C.c_uint64
+        _lib.orc_prp_tables.argtypes = [C.c_uint64, P, C.c_int64, P]
         _lib.orc_collide.argtypes = [P, P, P, P, C.c_int32, P, C.c_uint64, C.c_uint64, P, P, P, P, C.c_int]
         _lib.orc_collide_cell.argtypes = [P, P, P, C.c_int64, C.c_uint64, C.c_uint64, C.c_uint64, P, P, P, P]
         _lib.orc_transport.argtypes = [P, P, P, P, P, C.c_int32, P, C.c_int32, P, P, C.c_uint64, C.c_uint64,
@@ -121,7 +122,7 @@ def below(w, n):
 
 
 class _Prp(C.Structure):
-    _fields_ = [("n", C.c_uint64), ("h", C.c_int), ("key", C.c_uint64 * 4)]
+    _fields_ = [("n", C.c_uint64), ("b", C.c_int), ("key", C.c_uint64 * 4)]
 
 
 def prp_table(n, key, inverse=False):
@@ -131,6 +132,15 @@ def prp_table(n, key, inverse=False):
     lib().orc_prp_init(C.byref(p), n, _p(k))
     f = lib().orc_prp_inv if inverse else lib().orc_prp_fwd
     return np.array([f(C.byref(p), i) for i in range(n)], dtype=np.int64)
+
+
+def prp_tables(n, keys):
+    """Forward tables of many permutations of [0, n): keys [K][4] uint64 ->
+    [K][n] int32, row j = [pi_j(0), ..., pi_j(n-1)]."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    out = np.zeros((k.shape[0], n), dtype=np.int32)
+    lib().orc_prp_tables(n, _p(k), k.shape[0], _p(out))
+    return out
 
 
 def collide_params(dt=0.0, eps=1.0, alpha=0.0, rho_scale=1.0, trunc=TRUNC_FIXED, m=2, m_min=1,

@@ -9,8 +9,21 @@
  *     (c0,c1,c2,c3) -> (hi(M1*c2) ^ c1 ^ k0, lo(M1*c2), hi(M0*c0) ^ c3 ^ k1, lo(M0*c0))
  * with the key bumped by the Weyl constants between rounds.
  *
- * The permutation is a 4-round balanced Feistel network on 2h-bit words
- * (Luby-Rackoff) restricted to [0,n) by cycle walking (Black & Rogaway 2002).
+ * The permutation of [0,n) realises Alg. 4.3's "random choice", so every
+ * subset of it must be close to uniform.  Two constructions, by size:
+ *  - n <= 32: the order of n keys.  Item y gets the 32-bit key
+ *    fmix32((lo(w0) ^ y*0x9E3779B9) + hi(w0)) (fmix32: MurmurHash3's
+ *    finaliser, a bijection, so the n keys are distinct), and pi(y) is the
+ *    number of items with a smaller key.  Feistel networks are far from
+ *    uniform on such small domains, whatever the number of rounds.
+ *  - n > 32: an alternating Feistel network (Luby-Rackoff) on b-bit words,
+ *    2^(b-1) < n <= 2^b: the high ceil(b/2) bits A and the low floor(b/2)
+ *    bits B; eight rounds for b <= 8, six above, round r adding F(B, k_r) to A
+ *    (r even) or F(A, k_r) to B (r odd) by exclusive or; round keys w0..w3 and
+ *    then w0..w3 with their 32-bit halves swapped.  Restricted to [0,n) by
+ *    cycle walking (Black & Rogaway, CT-RSA 2002), which takes fewer than two
+ *    steps on average.
+ * The four words w0..w3 are one Philox draw.
  */
 #include "trmc_oracle.h"
 
@@ -69,42 +82,79 @@ static uint32_t feistel_f(uint32_t r, uint64_t k)
     return z;
 }
 
+static uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
 void orc_prp_init(orc_prp *p, uint64_t n, const uint64_t key[4])
 {
     p->n = n;
-    int h = 1;
-    while ((1ULL << (2 * h)) < n) ++h;
-    p->h = h;
+    int b = 1;
+    while ((1ULL << b) < n) ++b;
+    p->b = b;
     for (int i = 0; i < 4; ++i) p->key[i] = key[i];
+}
+
+/* the key of item y (n <= 32) */
+static uint32_t rank_key(const orc_prp *p, uint64_t y)
+{
+    uint32_t lo = (uint32_t)p->key[0], hi = (uint32_t)(p->key[0] >> 32);
+    return fmix32((lo ^ ((uint32_t)y * 0x9E3779B9u)) + hi);
+}
+
+/* rounds of the Feistel network: eight on words of up to 8 bits, six on
+ * wider ones (where six already pass the permutation pins at 10^5 keys) */
+static int feistel_rounds(const orc_prp *p)
+{
+    return p->b <= 8 ? 8 : 6;
+}
+
+/* round key r of the Feistel network */
+static uint64_t round_key(const orc_prp *p, int r)
+{
+    uint64_t w = p->key[r & 3];
+    return r < 4 ? w : (w << 32) | (w >> 32);
 }
 
 static uint64_t feistel_enc(const orc_prp *p, uint64_t x)
 {
-    uint64_t mask = (1ULL << p->h) - 1;
-    uint64_t L = x >> p->h, R = x & mask;
-    for (int r = 0; r < 4; ++r) {
-        uint64_t nl = R;
-        uint64_t nr = L ^ ((uint64_t)feistel_f((uint32_t)R, p->key[r]) & mask);
-        L = nl; R = nr;
+    int c = p->b / 2, a = p->b - c;
+    uint64_t ma = (1ULL << a) - 1, mb = (1ULL << c) - 1;
+    uint64_t A = x >> c, B = x & mb;
+    for (int r = 0; r < feistel_rounds(p); ++r) {
+        if (r % 2 == 0) A ^= (uint64_t)feistel_f((uint32_t)B, round_key(p, r)) & ma;
+        else B ^= (uint64_t)feistel_f((uint32_t)A, round_key(p, r)) & mb;
     }
-    return (L << p->h) | R;
+    return (A << c) | B;
 }
 
 static uint64_t feistel_dec(const orc_prp *p, uint64_t y)
 {
-    uint64_t mask = (1ULL << p->h) - 1;
-    uint64_t L = y >> p->h, R = y & mask;
-    for (int r = 3; r >= 0; --r) {
-        uint64_t pr = L;
-        uint64_t pl = R ^ ((uint64_t)feistel_f((uint32_t)L, p->key[r]) & mask);
-        L = pl; R = pr;
+    int c = p->b / 2, a = p->b - c;
+    uint64_t ma = (1ULL << a) - 1, mb = (1ULL << c) - 1;
+    uint64_t A = y >> c, B = y & mb;
+    for (int r = feistel_rounds(p) - 1; r >= 0; --r) {
+        if (r % 2 == 0) A ^= (uint64_t)feistel_f((uint32_t)B, round_key(p, r)) & ma;
+        else B ^= (uint64_t)feistel_f((uint32_t)A, round_key(p, r)) & mb;
     }
-    return (L << p->h) | R;
+    return (A << c) | B;
 }
 
 uint64_t orc_prp_fwd(const orc_prp *p, uint64_t x)
 {
     if (p->n <= 1) return 0;
+    if (p->n <= 32) {
+        uint32_t kx = rank_key(p, x);
+        uint64_t r = 0;
+        for (uint64_t y = 0; y < p->n; ++y) r += rank_key(p, y) < kx;
+        return r;
+    }
     uint64_t y = feistel_enc(p, x);
     while (y >= p->n) y = feistel_enc(p, y);
     return y;
@@ -113,7 +163,23 @@ uint64_t orc_prp_fwd(const orc_prp *p, uint64_t x)
 uint64_t orc_prp_inv(const orc_prp *p, uint64_t y)
 {
     if (p->n <= 1) return 0;
+    if (p->n <= 32) {
+        for (uint64_t x = 0; x < p->n; ++x)
+            if (orc_prp_fwd(p, x) == y) return x;
+        return 0;     /* not reached for y < n */
+    }
     uint64_t x = feistel_dec(p, y);
     while (x >= p->n) x = feistel_dec(p, x);
     return x;
+}
+
+/* forward tables of K permutations of [0,n) at once, for the statistical pins:
+ * out[j][x] = pi_j(x), pi_j keyed by keys[j][0..3] */
+void orc_prp_tables(uint64_t n, const uint64_t *keys, int64_t K, int32_t *out)
+{
+    for (int64_t j = 0; j < K; ++j) {
+        orc_prp p;
+        orc_prp_init(&p, n, keys + 4 * j);
+        for (uint64_t x = 0; x < n; ++x) out[j * (int64_t)n + (int64_t)x] = (int32_t)orc_prp_fwd(&p, x);
+    }
 }

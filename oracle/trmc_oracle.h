@@ -41,11 +41,14 @@ double orc_u01(uint64_t w);         /* [0,1), 53 bits        */
 double orc_u01_open(uint64_t w);    /* (0,1], 53 bits        */
 uint32_t orc_below(uint64_t w, uint32_t n);   /* integer in [0,n) */
 
-/* --- pseudo-random permutation of [0,n): 4-round Feistel + cycle walking - */
-typedef struct { uint64_t n; int h; uint64_t key[4]; } orc_prp;
+/* --- pseudo-random permutation of [0,n): key order (n <= 32), else an
+ *     alternating Feistel network (8 or 6 rounds) on 2^b >= n with cycle
+ *     walking ---------------------------------------------------------------- */
+typedef struct { uint64_t n; int b; uint64_t key[4]; } orc_prp;
 void orc_prp_init(orc_prp *p, uint64_t n, const uint64_t key[4]);
 uint64_t orc_prp_fwd(const orc_prp *p, uint64_t x);
 uint64_t orc_prp_inv(const orc_prp *p, uint64_t y);
+void orc_prp_tables(uint64_t n, const uint64_t *keys, int64_t K, int32_t *out);
 
 /* --- collision step ------------------------------------------------------ */
 enum { ORC_TRUNC_FIXED = 0, ORC_TRUNC_RAD = 1, ORC_TRUNC_UNLIMITED = 2, ORC_TRUNC_WB = 3 };

@@ -168,6 +168,18 @@ trmc_status trmc_set_collide_launch(trmc_ctx *ctx, int32_t threads, int32_t ctas
     return TRMC_OK;
 }
 
+trmc_status trmc_set_collide_schedule(trmc_ctx *ctx, int32_t warp_particles, int32_t records_per_thread)
+{
+    if (!ctx) return TRMC_ERR_ARG;
+    if (warp_particles != 0 && (warp_particles < 2 || warp_particles > 8192 || warp_particles % 2 != 0))
+        return set_error(ctx, TRMC_ERR_ARG, "warp_particles must be 0 or even in [2, 8192]");
+    if (records_per_thread < 0 || records_per_thread > 16)
+        return set_error(ctx, TRMC_ERR_ARG, "records_per_thread must be 0 or in [1, 16]");
+    ctx->collide_warp_particles = warp_particles;
+    ctx->collide_records_per_thread = records_per_thread;
+    return TRMC_OK;
+}
+
 trmc_status trmc_set_transport_launch(trmc_ctx *ctx, int32_t threads)
 {
     if (!ctx) return TRMC_ERR_ARG;

@@ -12,7 +12,7 @@
 //      and keeping a surplus output), each taking k uniform in {0..n-1}
 //      (Alg. 4.1/4.3); the label histogram of level n fixes the demand D_k
 //      on the levels below; leaves that cannot be served lower the depth;
-//   4. roles: a Feistel permutation of the cell's particles picks the
+//   4. roles: a pseudo-random permutation of the cell's particles picks the
 //      uncollided, the leaves and the thermalised set (the "random choice");
 //   5. collision waves, level 1 first, all collisions of a level in
 //      parallel (Eq. Maxwell_coll, sigma from Eq. n3d, VHS acceptance of
@@ -45,6 +45,7 @@ constexpr int NLEV = kMC + 2;
 // in dependency order from precomputed records, the others by the whole CTA.
 // Measured on GB300: 32 for FP64 (its collisions are slow; spread them over the
 // CTA), 128 for FP32.
+// Both are defaults of the context's schedule (trmc_set_collide_schedule).
 constexpr int kWarpLevel64 = 32, kWarpLevel32 = 128;
 constexpr int kRecordPerThread = 4;
 constexpr int kPreLabels = 16;     // labels per level drawn ahead of the plan, at least
@@ -73,7 +74,8 @@ struct Args {
     char *slabs;
     size_t slab_bytes;
     int smem_bytes;
-    int warp_level;
+    int warp_level;                  // collisions of the largest level one warp takes alone
+    int rec_per_thread;              // records precomputed for levels of up to this many collisions a thread
     const BigEntry *big;             // NULL, or the pre-pass's sums of this launch's large cells
     uint64_t big_stamp;              // this launch's number in big[].stamp
 };
@@ -85,7 +87,8 @@ struct Sh {
     uint64_t uSK[NLEV];              // split uniforms of the levels, u = uSK 2^-53
     U64x4 keys[NLEV];
     double red[kRedScratch];
-    uint8_t lab[NLEV][kMaxPre];      // labels of the first npre[lv] collisions of each level
+    uint8_t lab[NLEV][kMaxPre];      // labels of the first npre[lv] collisions of each level; after
+                                     // the plan, the dealing table of a level of at most 32 products
     uint8_t npre[NLEV];
     int32_t dbase[NLEV + 1], ndraws; // first draw of each level in the level-draw phase, their number
     int32_t cell, n, m, lo, m_eff, pass, n0, D0, R, npart, m_next, Dge1;
@@ -583,7 +586,7 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
     // direction) is computed up front for every level of at most rec_max
     // collisions, a few per thread: there it takes latency off the level's
     // wave; bigger levels keep every thread busy and compute it in place
-    const int rec_max = max(a.warp_level, kRecordPerThread * bs);
+    const int rec_max = max(a.warp_level, a.rec_per_thread * bs);
     const trmc_collide_params &prm = a.prm;
 
     if (tid == 0) {
@@ -1365,7 +1368,8 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
             // the draw and the product slots do not depend on the inputs:
             // issue them first so their latency overlaps the loads
             const U64x4 w = rng().draw(uint64_t(c), uint64_t(lv), uint32_t(pass), TAG_COLL);
-            const int t0 = int(pk.fwd(uint32_t(2 * c))), t1 = int(pk.fwd(uint32_t(2 * c + 1)));
+            int t0, t1;
+            pk.fwd2(uint32_t(2 * c), uint32_t(2 * c + 1), t0, t1);
             const int Dn = sh.D[lv], On = sh.O[lv], IBn = sh.IB[lv];
             const int32_t *row = sh.Mt + tri(lv), *srow = sh.St + tri(lv);
             // label of collision c: Pn[k] <= c < Pn[k+1]
@@ -1458,6 +1462,17 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
                 a1 += __shfl_sync(0xffffffffu, a0, 31);
                 if (lane < lv) pr[lane] = a0 - r0;
                 if (lane + 32 < lv) pr[lane + 32] = a1 - r1;
+                // a level of at most 32 products: its dealing permutation as a
+                // table, the rank of each product's key among the level's keys
+                // (perm_fwd2's own rule), in the level's label row, which the
+                // plan no longer needs
+                const int np = 2 * sh.C[lv];
+                if (np <= 32) {
+                    const uint32_t ky = lane < np ? rank_key(uint32_t(lane), sh.keys[lv].w[0]) : 0u;
+                    uint32_t rk = 0;
+                    for (int j = 0; j < np; ++j) rk += __shfl_sync(0xffffffffu, ky, j) < ky;
+                    if (lane < np) sh.lab[lv][lane] = uint8_t(rk);
+                }
             }
             __syncthreads();
             const int W = sh.WB[nWL];
@@ -1479,9 +1494,15 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
                 int2 sr, ds;
                 sr.x = k == 0 ? ~pos(n0 + s0) : sh.IB[k] + s0;
                 sr.y = j == 0 ? ~pos(n0 + s1) : sh.IB[j] + s1;
-                Perm pk;
-                pk.init(uint32_t(2 * sh.C[lv]), sh.keys[lv]);
-                const int t0 = int(pk.fwd(uint32_t(2 * c))), t1 = int(pk.fwd(uint32_t(2 * c + 1)));
+                int t0, t1;
+                if (2 * sh.C[lv] <= 32) {
+                    t0 = sh.lab[lv][2 * c];
+                    t1 = sh.lab[lv][2 * c + 1];
+                } else {
+                    Perm pk;
+                    pk.init(uint32_t(2 * sh.C[lv]), sh.keys[lv]);
+                    pk.fwd2(uint32_t(2 * c), uint32_t(2 * c + 1), t0, t1);
+                }
                 const int Dn = sh.D[lv];
                 ds.x = t0 < Dn ? sh.IB[lv] + t0 : ~(sh.O[lv] + t0 - Dn);
                 ds.y = t1 < Dn ? sh.IB[lv] + t1 : ~(sh.O[lv] + t1 - Dn);
@@ -2275,7 +2296,9 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     a.slabs = ctx->slabs;
     a.slab_bytes = (ctx->slabs_bytes / size_t(grid)) & ~size_t(255);
     a.smem_bytes = smem;
-    a.warp_level = sizeof(Real) == 8 ? kWarpLevel64 : kWarpLevel32;
+    a.warp_level = ctx->collide_warp_particles > 0 ? ctx->collide_warp_particles / 2
+                   : sizeof(Real) == 8 ? kWarpLevel64 : kWarpLevel32;
+    a.rec_per_thread = ctx->collide_records_per_thread > 0 ? ctx->collide_records_per_thread : kRecordPerThread;
     if (st->cell_cost && st->cell_order) order_kernel<<<1, 1024, 0, s>>>(st->cell_cost, st->n_cells, st->cell_order);
     fn<<<grid, threads, smem, s>>>(a);
     e = cudaGetLastError();
@@ -2390,6 +2413,7 @@ trmc_status launch_static(trmc_state *st, const trmc_collide_params *prm, uint64
     a.slab_bytes = (avail / size_t(grid)) & ~size_t(255);
     a.smem_bytes = smem;
     a.warp_level = sizeof(Real) == 8 ? kWarpLevel64 : kWarpLevel32;
+    a.rec_per_thread = kRecordPerThread;
     fn<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? TRMC_OK : TRMC_ERR_CUDA;
 }

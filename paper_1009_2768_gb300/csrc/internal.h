@@ -47,6 +47,9 @@ struct trmc_ctx {
     // collide launch shape (trmc_set_collide_launch)
     int collide_threads = 128;
     int collide_ctas_per_sm = 4;
+    // collide work schedule (trmc_set_collide_schedule; 0: the precision's default)
+    int collide_warp_particles = 0;
+    int collide_records_per_thread = 0;
     // transport sort launch shape (trmc_set_transport_launch; 0: by mean cell size)
     int transport_threads = 0;
     std::string last_error;

@@ -7,9 +7,11 @@
 // (seed, problem | index, aux, cell, step/pass/tag), so a cell's result does
 // not depend on launch shape or batch placement.
 //
-// Permutation: 4-round balanced Feistel network on 2h-bit words with cycle
-// walking onto [0, n) (Black & Rogaway, CT-RSA 2002).  It realises the
-// "random choice" of particles in Alg. 4.3 without materialising shuffles.
+// Permutation of [0, n): it realises the "random choice" of particles in
+// Alg. 4.3 without materialising shuffles, so every subset of it must be close
+// to uniform.  For n <= 32 it is the order of n distinct hashed keys; above,
+// an 8-round alternating Feistel network on the smallest 2^b >= n with cycle
+// walking onto [0, n) (Black & Rogaway, CT-RSA 2002).
 #pragma once
 #include <cstdint>
 
@@ -44,13 +46,23 @@ __device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_
 // Keyed stream of one cell: key = (seed, problem); the fourth counter word
 // packs step, pass and purpose tag.  A draw is about 300 instructions and the
 // collision kernel makes them in many places: one shared copy (not inlined)
-// keeps the kernel's code small enough for the instruction caches.
+// keeps the kernel's code small enough for the instruction caches.  The
+// shared copy takes its words as arguments, which travel in registers; a
+// member function would need its object's address, and so a copy of the
+// object in local memory at every call (on GB300, with most of the SM's
+// unified memory given to shared memory, local memory lives mostly in L2).
+static __device__ __noinline__ U64x4 philox_draw(uint64_t index, uint64_t aux, uint64_t cell, uint64_t c3,
+                                                 uint64_t seed, uint64_t problem)
+{
+    return philox4x64_10(index, aux, cell, c3, seed, problem);
+}
+
 struct CellRng {
     uint64_t seed, problem, cell, step;
-    __device__ __noinline__ U64x4 draw(uint64_t index, uint64_t aux, uint32_t pass, uint32_t tag) const
+    __device__ __forceinline__ U64x4 draw(uint64_t index, uint64_t aux, uint32_t pass, uint32_t tag) const
     {
         const uint64_t c3 = (step << 16) | (uint64_t(pass & 0xFFu) << 8) | uint64_t(tag & 0xFFu);
-        return philox4x64_10(index, aux, cell, c3, seed, problem);
+        return philox_draw(index, aux, cell, c3, seed, problem);
     }
 };
 
@@ -64,7 +76,7 @@ __device__ __forceinline__ uint32_t below(uint64_t w, uint32_t n)
     return uint32_t(((w >> 32) * uint64_t(n)) >> 32);
 }
 
-// ---- Feistel permutation of [0, n) ------------------------------------------
+// ---- permutation of [0, n) ---------------------------------------------------
 __device__ __forceinline__ uint32_t feistel_round(uint32_t r, uint64_t k)
 {
     uint32_t z = (r ^ uint32_t(k)) * 0x9E3779B1u;
@@ -74,60 +86,118 @@ __device__ __forceinline__ uint32_t feistel_round(uint32_t r, uint64_t k)
     return z;
 }
 
+// Round key r of the Feistel network: the draw's four words, then the same
+// words with their 32-bit halves swapped.
+__device__ __forceinline__ uint64_t swap32(uint64_t w) { return (w << 32) | (w >> 32); }
+
+// One pass of the rounds (enc) and the rounds undone, last first (dec), on a
+// b-bit word: A, the high ceil(b/2) bits, takes F of B in the even rounds; B,
+// the low floor(b/2) bits, takes F of A in the odd ones.  Eight rounds for
+// b <= 8, six for wider words (where six already pass the permutation pins at
+// 10^5 keys).
+__device__ __forceinline__ uint32_t feistel_enc(uint32_t x, uint32_t b, uint64_t k0, uint64_t k1, uint64_t k2,
+                                                uint64_t k3)
+{
+    const uint32_t c = b >> 1, ma = (1u << (b - c)) - 1u, mb = (1u << c) - 1u;
+    uint32_t A = x >> c, B = x & mb;
+    A ^= feistel_round(B, k0) & ma; B ^= feistel_round(A, k1) & mb;
+    A ^= feistel_round(B, k2) & ma; B ^= feistel_round(A, k3) & mb;
+    A ^= feistel_round(B, swap32(k0)) & ma; B ^= feistel_round(A, swap32(k1)) & mb;
+    if (b <= 8) { A ^= feistel_round(B, swap32(k2)) & ma; B ^= feistel_round(A, swap32(k3)) & mb; }
+    return (A << c) | B;
+}
+__device__ __forceinline__ uint32_t feistel_dec(uint32_t y, uint32_t b, uint64_t k0, uint64_t k1, uint64_t k2,
+                                                uint64_t k3)
+{
+    const uint32_t c = b >> 1, ma = (1u << (b - c)) - 1u, mb = (1u << c) - 1u;
+    uint32_t A = y >> c, B = y & mb;
+    if (b <= 8) { B ^= feistel_round(A, swap32(k3)) & mb; A ^= feistel_round(B, swap32(k2)) & ma; }
+    B ^= feistel_round(A, swap32(k1)) & mb; A ^= feistel_round(B, swap32(k0)) & ma;
+    B ^= feistel_round(A, k3) & mb; A ^= feistel_round(B, k2) & ma;
+    B ^= feistel_round(A, k1) & mb; A ^= feistel_round(B, k0) & ma;
+    return (A << c) | B;
+}
+
+// Key of item y for n <= 32: MurmurHash3's 32-bit finaliser (a bijection) of
+// a bijection of y, so the keys of distinct items differ.
+__device__ __forceinline__ uint32_t rank_key(uint32_t y, uint64_t k0)
+{
+    uint32_t h = (uint32_t(k0) ^ (y * 0x9E3779B9u)) + uint32_t(k0 >> 32);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// pi(x0) and pi(x1) for x0, x1 < n, in one call (the two products of a
+// collision).  n <= 32: pi(x) is the number of items with a smaller key (the
+// keys are hashed once for both); else encrypt, and again while the word lies
+// outside [0, n) (the two walks side by side).  Returned as
+// pi(x0) | pi(x1) << 32.
+static __device__ __noinline__ uint64_t perm_fwd2(uint32_t x0, uint32_t x1, uint32_t n, uint32_t b, uint64_t k0,
+                                                  uint64_t k1, uint64_t k2, uint64_t k3)
+{
+    if (n <= 1) return 0;
+    uint32_t y0 = 0, y1 = 0;
+    if (n <= 32) {
+        const uint32_t kx0 = rank_key(x0, k0), kx1 = rank_key(x1, k0);
+        for (uint32_t y = 0; y < n; ++y) {
+            const uint32_t ky = rank_key(y, k0);
+            y0 += ky < kx0;
+            y1 += ky < kx1;
+        }
+    } else {
+        y0 = feistel_enc(x0, b, k0, k1, k2, k3);
+        y1 = feistel_enc(x1, b, k0, k1, k2, k3);
+        while (y0 >= n || y1 >= n) {
+            if (y0 >= n) y0 = feistel_enc(y0, b, k0, k1, k2, k3);
+            if (y1 >= n) y1 = feistel_enc(y1, b, k0, k1, k2, k3);
+        }
+    }
+    return uint64_t(y0) | (uint64_t(y1) << 32);
+}
+// pi^-1(y) for y < n (n <= 32: the item whose key has y smaller ones; else
+// the cycle through y walked backwards)
+static __device__ __noinline__ uint32_t perm_inv(uint32_t y, uint32_t n, uint32_t b, uint64_t k0, uint64_t k1,
+                                                 uint64_t k2, uint64_t k3)
+{
+    if (n <= 1) return 0;
+    if (n <= 32) {
+        for (uint32_t x = 0; x < n; ++x) {
+            const uint32_t kx = rank_key(x, k0);
+            uint32_t r = 0;
+            for (uint32_t z = 0; z < n; ++z) r += rank_key(z, k0) < kx;
+            if (r == y) return x;
+        }
+        return 0;     // not reached for y < n
+    }
+    uint32_t x = feistel_dec(y, b, k0, k1, k2, k3);
+    while (x >= n) x = feistel_dec(x, b, k0, k1, k2, k3);
+    return x;
+}
+
 struct Perm {
     uint32_t n;
-    uint32_t h;       // half width in bits; domain 4^h >= n
+    uint32_t b;       // word width in bits: 2^(b-1) < n <= 2^b
     uint64_t k[4];
 
     __device__ __forceinline__ void init(uint32_t n_, const U64x4 &key)
     {
         n = n_;
-        uint32_t hh = 1;
-        while ((1ull << (2 * hh)) < uint64_t(n_)) ++hh;
-        h = hh;
+        b = n_ <= 1 ? 0u : 32u - uint32_t(__clz(n_ - 1u));
         k[0] = key.w[0]; k[1] = key.w[1]; k[2] = key.w[2]; k[3] = key.w[3];
     }
-    __device__ __forceinline__ uint32_t enc(uint32_t x) const
+    // pi(x0) and pi(x1), and pi^-1(y): one shared copy each (not inlined),
+    // given the key words as arguments like philox_draw
+    __device__ __forceinline__ void fwd2(uint32_t x0, uint32_t x1, int &y0, int &y1) const
     {
-        const uint32_t mask = (1u << h) - 1u;
-        uint32_t L = x >> h, R = x & mask;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const uint32_t t = L ^ (feistel_round(R, k[r]) & mask);
-            L = R;
-            R = t;
-        }
-        return (L << h) | R;
+        const uint64_t y = perm_fwd2(x0, x1, n, b, k[0], k[1], k[2], k[3]);
+        y0 = int(uint32_t(y));
+        y1 = int(uint32_t(y >> 32));
     }
-    // the rounds of enc undone, last first
-    __device__ __forceinline__ uint32_t dec(uint32_t y) const
-    {
-        const uint32_t mask = (1u << h) - 1u;
-        uint32_t L = y >> h, R = y & mask;
-#pragma unroll
-        for (int r = 3; r >= 0; --r) {
-            const uint32_t t = R ^ (feistel_round(L, k[r]) & mask);
-            R = L;
-            L = t;
-        }
-        return (L << h) | R;
-    }
-    // pi(x) for x < n (not inlined: one copy serves every call site)
-    __device__ __noinline__ uint32_t fwd(uint32_t x) const
-    {
-        if (n <= 1) return 0;
-        uint32_t y = enc(x);
-        while (y >= n) y = enc(y);
-        return y;
-    }
-    // pi^-1(y) for y < n: the cycle through y walked backwards (not inlined)
-    __device__ __noinline__ uint32_t inv(uint32_t y) const
-    {
-        if (n <= 1) return 0;
-        uint32_t x = dec(y);
-        while (x >= n) x = dec(x);
-        return x;
-    }
+    __device__ __forceinline__ uint32_t inv(uint32_t y) const { return perm_inv(y, n, b, k[0], k[1], k[2], k[3]); }
 };
 
 // ---- warp / block reductions (fixed order, hence deterministic) --------------

@@ -15,10 +15,12 @@ simulation back where it found it.
 * autotune_collide times candidate (CTA size, CTAs per SM) shapes on the
   live workload, keeps the fastest and then restores the state it stepped
   (velocities, positions, cell starts, RAD depths, carries, step counters).
-  The CTA size also sets how many particles of a cell each warp handles
-  (cell size / warps per CTA).  autotune_transport does the same for the
-  sort schedule (threads per CTA of the counting sort's count and scatter
-  kernels, one CTA per cell), and autotune runs both.
+  autotune_schedule then sweeps the work schedule inside a cell at that
+  shape: the particles per warp (the largest tree level one warp takes alone)
+  and the levels whose collisions are precomputed as records (collisions per
+  thread).  autotune_transport does the same for the sort schedule (threads
+  per CTA of the counting sort's count and scatter kernels, one CTA per
+  cell), and autotune runs all three.
 * largest_first orders cells by particle count, biggest first, so the
   longest cells start early and the launch does not end on one of them.
 """
@@ -28,6 +30,8 @@ from . import trmc as T
 
 DEFAULT_SHAPES = ((256, 3), (256, 2), (128, 4), (128, 3), (160, 3), (192, 2), (64, 8))
 SORT_SCHEDULES = (0, 64, 128, 256)     # transport threads per cell CTA (0: by mean cell size)
+# (particles per warp, records per thread); (0, 0) is the library's default
+WORK_SCHEDULES = ((0, 0), (32, 4), (128, 4), (512, 4), (0, 2), (0, 8))
 
 
 def largest_first(cell_start):
@@ -124,6 +128,35 @@ def autotune_collide(sim, shapes=DEFAULT_SHAPES, steps=6, flush_bytes=256 << 20)
     return times, best
 
 
+def autotune_schedule(sim, choices=WORK_SCHEDULES, steps=6, flush_bytes=256 << 20):
+    """Time `steps` collide launches of the live workload for every work
+    schedule (particles per warp, records per thread) at the current launch
+    shape, with an L2 flush before each, keep the fastest and restore the
+    simulation.  Returns ({schedule: median collide ms}, best)."""
+    import torch
+    flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    snap = _snapshot(sim)
+    times = {}
+    for sch in choices:
+        T.trmc_set_collide_schedule(sim.ctx, *sch)
+        sim.step()
+        ms = []
+        for _ in range(steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            flush.zero_()
+            sim.step(events=ev)
+            torch.cuda.synchronize()
+            ms.append(ev[1].elapsed_time(ev[2]))
+        times[sch] = float(np.median(ms))
+    best = min(times, key=times.get)
+    T.trmc_set_collide_schedule(sim.ctx, *best)
+    T.trmc_check(sim.ctx)
+    _restore(sim, snap)
+    torch.cuda.synchronize()
+    return times, best
+
+
 def autotune_transport(sim, choices=SORT_SCHEDULES, steps=6, flush_bytes=256 << 20):
     """Time `steps` transports of the live workload for every sort schedule
     (threads per CTA of the count and scatter kernels; 0 lets the library
@@ -156,9 +189,12 @@ def autotune_transport(sim, choices=SORT_SCHEDULES, steps=6, flush_bytes=256 << 
     return times, best
 
 
-def autotune(sim, shapes=DEFAULT_SHAPES, schedules=SORT_SCHEDULES, steps=6):
-    """The collide launch shape and the sort schedule for the live workload
-    (both left set; the simulation is restored)."""
+def autotune(sim, shapes=DEFAULT_SHAPES, schedules=SORT_SCHEDULES, steps=6, work=WORK_SCHEDULES):
+    """The collide launch shape, then the work schedule inside a cell at that
+    shape, and the sort schedule for the live workload (all left set; the
+    simulation is restored)."""
     collide_times, shape = autotune_collide(sim, shapes, steps)
+    work_times, wsched = autotune_schedule(sim, work, steps)
     sort_times, sched = autotune_transport(sim, schedules, steps)
-    return {"collide": collide_times, "collide_best": shape, "sort": sort_times, "sort_best": sched}
+    return {"collide": collide_times, "collide_best": shape, "work": work_times, "work_best": wsched,
+            "sort": sort_times, "sort_best": sched}

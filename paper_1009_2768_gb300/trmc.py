@@ -27,7 +27,7 @@ REPORT_FIELDS = ["N", "passes", "m_first", "m_last", "m_next", "R_final", "N0", 
                  "coll", "dummy", "exceed", "feas", "pdrop", "psurp", "m_eff0", "wbrej"]
 EXPORTS = ["trmc_create", "trmc_destroy", "trmc_last_error", "trmc_check", "trmc_init_cells",
            "trmc_collide", "trmc_transport", "trmc_moments", "trmc_collide_static", "trmc_set_collide_launch",
-           "trmc_set_transport_launch",
+           "trmc_set_transport_launch", "trmc_set_collide_schedule",
            "trmc_fp64_selftest", "trmc_split_selftest"]
 STATIC_SCRATCH_BYTES = 32 << 20
 
@@ -113,6 +113,7 @@ def load():
         lib.trmc_moments.argtypes = [P, C.POINTER(State), P, P]
         lib.trmc_set_collide_launch.argtypes = [P, C.c_int32, C.c_int32]
         lib.trmc_set_transport_launch.argtypes = [P, C.c_int32]
+        lib.trmc_set_collide_schedule.argtypes = [P, C.c_int32, C.c_int32]
         lib.trmc_collide_static.argtypes = [C.POINTER(State), C.POINTER(CollideParams), C.c_int32, C.c_uint64,
                                             C.c_uint64, C.c_int32, P, P]
         lib.trmc_fp64_selftest.argtypes = [P, C.c_int32, P, P]
@@ -159,6 +160,10 @@ def trmc_check(ctx, stream=None):
 
 def trmc_set_collide_launch(ctx, threads, ctas_per_sm):
     _raise(ctx, load().trmc_set_collide_launch(ctx, threads, ctas_per_sm))
+
+
+def trmc_set_collide_schedule(ctx, warp_particles, records_per_thread):
+    _raise(ctx, load().trmc_set_collide_schedule(ctx, warp_particles, records_per_thread))
 
 
 def trmc_set_transport_launch(ctx, threads):

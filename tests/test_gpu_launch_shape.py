@@ -2,7 +2,8 @@
 (moments, the collisions' change, the thermalised set, the Maxwellian
 samples, the carry) runs over the same 256 virtual lanes and 8 virtual warps
 in a fixed tree whatever the CTA size, so the bound, q, the split and every
-velocity have the same bits for every (threads per CTA, CTAs per SM)."""
+velocity have the same bits for every (threads per CTA, CTAs per SM).  Nor on
+the work schedule inside a cell (particles per warp, records per thread)."""
 import numpy as np
 import pytest
 
@@ -15,7 +16,7 @@ COUNTS = [2, 3, 17, 64, 255, 257, 889, 2500, 6000, 9001]
 SHAPES = [(64, 8), (128, 4), (256, 2), (96, 3), (32, 8)]
 
 
-def run_shape(precision, shape, params, counts, steps=2, carry=False):
+def run_shape(precision, shape, params, counts, steps=2, carry=False, schedule=None):
     ensure_built()
     g = synth.rng(77)
     v = np.concatenate([synth.bimaxwellian(n, 2.0, 0.5, u=(0.3, -0.2, 0.1), g=g) for n in counts], axis=1)
@@ -29,6 +30,8 @@ def run_shape(precision, shape, params, counts, steps=2, carry=False):
         st.m_max.fill_(2)
     c = T.trmc_create(precision, 11, 1 << 30)
     T.trmc_set_collide_launch(c, *shape)
+    if schedule is not None:
+        T.trmc_set_collide_schedule(c, *schedule)
     rep = torch.zeros((nc, T.REPORT_LEN), dtype=torch.int64, device="cuda")
     for s in range(steps):
         T.trmc_collide(c, st, params, 3 + s, report=rep)
@@ -60,6 +63,37 @@ def test_results_are_bit_identical_across_launch_shapes(precision, name):
         got = run_shape(precision, shape, PARAMS[name], COUNTS, carry=carry)
         for a, b in zip(ref, got):
             assert np.array_equal(a, b), f"launch shape {shape} differs from {SHAPES[0]} ({name})"
+
+
+# (particles per warp, records per thread; 0: the default): levels from one
+# collision up in CTA-wide waves, or every level in one warp; records for few
+# levels or for the largest ones
+SCHEDULES = [(0, 0), (2, 1), (16, 1), (256, 16), (4096, 4), (8192, 16)]
+
+
+@pytest.mark.parametrize("precision", [T.FP64, T.FP32_MIXED])
+@pytest.mark.parametrize("name", sorted(PARAMS))
+def test_results_are_bit_identical_across_work_schedules(precision, name):
+    # which warps run a level, and which levels' collisions are precomputed,
+    # moves work between threads only: same draws, same sums, same bits
+    need_gpu()
+    carry = precision == T.FP32_MIXED
+    ref = run_shape(precision, (128, 4), PARAMS[name], COUNTS, carry=carry, schedule=SCHEDULES[0])
+    for sch in SCHEDULES[1:]:
+        got = run_shape(precision, (128, 4), PARAMS[name], COUNTS, carry=carry, schedule=sch)
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b), f"work schedule {sch} differs from the default ({name})"
+
+
+def test_work_schedule_arguments_are_checked():
+    need_gpu()
+    ensure_built()
+    c = T.trmc_create(T.FP64, 0, 1 << 20)
+    for bad in ((3, 0), (1, 0), (8194, 0), (-2, 0), (0, 17), (0, -1)):
+        with pytest.raises(T.TrmcError):
+            T.trmc_set_collide_schedule(c, *bad)
+    T.trmc_set_collide_schedule(c, 64, 4)
+    T.trmc_destroy(c)
 
 
 @pytest.mark.parametrize("precision,shape", [(T.FP32_MIXED, (256, 3)), (T.FP64, (256, 2))])

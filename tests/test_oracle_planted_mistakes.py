@@ -2,7 +2,8 @@
 oracle's C source, each with one mistake planted (a dropped factor, a sign,
 a missing renormalisation, q and tau swapped, a skewed label law, a biased
 rule for odd counts, lowering the depth where leaves can be borrowed, a
-wall that forgets to reverse v_x), are built into their own libraries and run
+wall that forgets to reverse v_x, a permutation with too few rounds or a
+Feistel network on domains too small for one), are built into their own libraries and run
 through the pins of tests/test_oracle_*.py; every copy must fail at least
 one of them.  The oracle itself is untouched: the copies live in a
 temporary directory and the module is pointed back at the real library
@@ -17,6 +18,7 @@ from oracle import oracle as O
 from tests import test_oracle_euler_limit as E
 from tests import test_oracle_physics as P
 from tests import test_oracle_plan_law as PL
+from tests import test_oracle_rng as RNG
 from tests import test_oracle_transport_init as TI
 
 ORACLE_DIR = os.path.dirname(os.path.abspath(O.__file__))
@@ -41,6 +43,10 @@ MISTAKES = {
         ("collide.c", "if (pl->Nn[n] >= 1 && orc_u01(w[0]) < 0.5)", "if (pl->Nn[n] >= 1)"),
     "leaves: the depth lowered instead of borrowing from level 0":
         ("collide.c", "if (deficit <= n0) {", "if (0) {"),
+    "permutation: four Feistel rounds":
+        ("rng.c", "    return p->b <= 8 ? 8 : 6;", "    return 4;"),
+    "permutation: the Feistel network for cells of up to 32 items too":
+        ("rng.c", "    if (p->n <= 32) {\n        uint32_t kx", "    if (0) {\n        uint32_t kx"),
     "walls: the right wall keeps v_x":
         ("transport.c", "else if (xn > hi) { xn = 2.0 * hi - xn; vx[i] = -vx[i]; }",
          "else if (xn > hi) { xn = 2.0 * hi - xn; }"),
@@ -49,6 +55,9 @@ MISTAKES = {
 # cheap pins first; a copy stops at the first pin it fails
 PINS = [
     ("transport hand example", TI.test_transport_hand_example),
+    ("permutation: top ranks of 5 items", lambda: RNG.test_prp_top_ranks_form_a_uniform_subset(5)),
+    ("permutation: top ranks of 33 items", lambda: RNG.test_prp_top_ranks_form_a_uniform_subset(33)),
+    ("permutation: top ranks in a block of 500", lambda: RNG.test_prp_top_ranks_in_a_block_are_hypergeometric(500, 12000)),
     ("conservation, hard spheres, TRMC-RAD", lambda: P.test_conservation(1.0, 0.05, O.TRUNC_RAD, 2)),
     ("conservation, Maxwell molecules, eps 1e-4", lambda: P.test_conservation(0.0, 1e-4, O.TRUNC_FIXED, 1)),
     ("level occupation", P.test_level_occupation_expectation),
