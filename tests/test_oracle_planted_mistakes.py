@@ -45,6 +45,8 @@ MISTAKES = {
         ("collide.c", "if (deficit <= n0) {", "if (0) {"),
     "permutation: four Feistel rounds":
         ("rng.c", "    return p->b <= 8 ? 8 : 6;", "    return 4;"),
+    "permutation: five Feistel rounds on words wider than 8 bits":
+        ("rng.c", "    return p->b <= 8 ? 8 : 6;", "    return p->b <= 8 ? 8 : 5;"),
     "permutation: the Feistel network for cells of up to 32 items too":
         ("rng.c", "    if (p->n <= 32) {\n        uint32_t kx", "    if (0) {\n        uint32_t kx"),
     "walls: the right wall keeps v_x":
@@ -58,6 +60,7 @@ PINS = [
     ("permutation: top ranks of 5 items", lambda: RNG.test_prp_top_ranks_form_a_uniform_subset(5)),
     ("permutation: top ranks of 33 items", lambda: RNG.test_prp_top_ranks_form_a_uniform_subset(33)),
     ("permutation: top ranks in a block of 500", lambda: RNG.test_prp_top_ranks_in_a_block_are_hypergeometric(500, 12000)),
+    ("permutation: fixed points of 300 items", lambda: RNG.test_prp_fixed_points_are_poisson(300, 30000)),
     ("conservation, hard spheres, TRMC-RAD", lambda: P.test_conservation(1.0, 0.05, O.TRUNC_RAD, 2)),
     ("conservation, Maxwell molecules, eps 1e-4", lambda: P.test_conservation(0.0, 1e-4, O.TRUNC_FIXED, 1)),
     ("level occupation", P.test_level_occupation_expectation),

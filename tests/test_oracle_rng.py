@@ -10,7 +10,8 @@ leaves or are thermalised, and how a level's products are dealt -- to choose
 subsets with the law of a uniform random permutation: the exact law of the
 set holding the top ranks for cells up to 40 items, of whole permutations for
 up to five, the hypergeometric law of how many top ranks fall in a block of
-items for 64 to 2500, and the chance that two siblings land in the same half.
+items for 64 to 2500, the Poisson(1) law of the number of fixed points, and
+the chance that two siblings land in the same half.
 """
 import itertools
 import math
@@ -155,4 +156,15 @@ def test_prp_siblings_share_a_half_as_often_as_uniform(n):
     p = (h * (h - 1) + (n - h) * (n - h - 1)) / (n * (n - 1))
     z = (same.mean() - p) / np.sqrt(p * (1 - p) / K)
     assert abs(z) < 4.5, (n, z)
+
+
+@pytest.mark.parametrize("n,K", [(40, 30000), (300, 30000), (1000, 20000)])
+def test_prp_fixed_points_are_poisson(n, K):
+    # the number of items a uniform permutation leaves in place is, for large
+    # n, Poisson with mean 1 (chi-square over 0..4 and 5 or more)
+    t = O.prp_tables(n, _keys(500 + n, K))
+    fp = (t == np.arange(n, dtype=np.int32)).sum(1)
+    obs = np.bincount(np.minimum(fp, 5), minlength=6).astype(float)
+    exp = np.append(stats.poisson(1).pmf(np.arange(5)), stats.poisson(1).sf(4)) * K
+    assert stats.chisquare(obs, exp).pvalue > 1e-4, n
 
