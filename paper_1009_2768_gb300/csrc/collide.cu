@@ -1464,7 +1464,7 @@ __device__ __forceinline__ Counts process_cell(const Args &a, uint64_t step, Sh<
                 if (lane + 32 < lv) pr[lane + 32] = a1 - r1;
                 // a level of at most 32 products: its dealing permutation as a
                 // table, the rank of each product's key among the level's keys
-                // (perm_fwd2's own rule), in the level's label row, which the
+                // (perm_rank2's own rule), in the level's label row, which the
                 // plan no longer needs
                 const int np = 2 * sh.C[lv];
                 if (np <= 32) {

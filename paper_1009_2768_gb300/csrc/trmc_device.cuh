@@ -131,50 +131,46 @@ __device__ __forceinline__ uint32_t rank_key(uint32_t y, uint64_t k0)
     return h;
 }
 
-// pi(x0) and pi(x1) for x0, x1 < n, in one call (the two products of a
-// collision).  n <= 32: pi(x) is the number of items with a smaller key (the
-// keys are hashed once for both); else encrypt, and again while the word lies
-// outside [0, n) (the two walks side by side).  Returned as
-// pi(x0) | pi(x1) << 32.
-static __device__ __noinline__ uint64_t perm_fwd2(uint32_t x0, uint32_t x1, uint32_t n, uint32_t b, uint64_t k0,
-                                                  uint64_t k1, uint64_t k2, uint64_t k3)
+// The evaluations below are noinline, each with one copy of the rounds: the
+// collision kernel calls them from several phases, and on GB300 the size of
+// its code (instruction fetch) costs more than the calls.
+// n <= 32: pi(x0) | pi(x1) << 32, each the number of items with a smaller key
+static __device__ __noinline__ uint64_t perm_rank2(uint32_t x0, uint32_t x1, uint32_t n, uint64_t k0)
 {
-    if (n <= 1) return 0;
+    const uint32_t kx0 = rank_key(x0, k0), kx1 = rank_key(x1, k0);
     uint32_t y0 = 0, y1 = 0;
-    if (n <= 32) {
-        const uint32_t kx0 = rank_key(x0, k0), kx1 = rank_key(x1, k0);
-        for (uint32_t y = 0; y < n; ++y) {
-            const uint32_t ky = rank_key(y, k0);
-            y0 += ky < kx0;
-            y1 += ky < kx1;
-        }
-    } else {
-        y0 = feistel_enc(x0, b, k0, k1, k2, k3);
-        y1 = feistel_enc(x1, b, k0, k1, k2, k3);
-        while (y0 >= n || y1 >= n) {
-            if (y0 >= n) y0 = feistel_enc(y0, b, k0, k1, k2, k3);
-            if (y1 >= n) y1 = feistel_enc(y1, b, k0, k1, k2, k3);
-        }
+    for (uint32_t y = 0; y < n; ++y) {
+        const uint32_t ky = rank_key(y, k0);
+        y0 += ky < kx0;
+        y1 += ky < kx1;
     }
     return uint64_t(y0) | (uint64_t(y1) << 32);
 }
-// pi^-1(y) for y < n (n <= 32: the item whose key has y smaller ones; else
-// the cycle through y walked backwards)
-static __device__ __noinline__ uint32_t perm_inv(uint32_t y, uint32_t n, uint32_t b, uint64_t k0, uint64_t k1,
-                                                 uint64_t k2, uint64_t k3)
+// n <= 32: pi^-1(y), the item whose key has y smaller ones
+static __device__ __noinline__ uint32_t perm_rank_inv(uint32_t y, uint32_t n, uint64_t k0)
 {
-    if (n <= 1) return 0;
-    if (n <= 32) {
-        for (uint32_t x = 0; x < n; ++x) {
-            const uint32_t kx = rank_key(x, k0);
-            uint32_t r = 0;
-            for (uint32_t z = 0; z < n; ++z) r += rank_key(z, k0) < kx;
-            if (r == y) return x;
-        }
-        return 0;     // not reached for y < n
+    for (uint32_t x = 0; x < n; ++x) {
+        const uint32_t kx = rank_key(x, k0);
+        uint32_t r = 0;
+        for (uint32_t z = 0; z < n; ++z) r += rank_key(z, k0) < kx;
+        if (r == y) return x;
     }
-    uint32_t x = feistel_dec(y, b, k0, k1, k2, k3);
-    while (x >= n) x = feistel_dec(x, b, k0, k1, k2, k3);
+    return 0;     // not reached for y < n
+}
+// n > 32: encrypt x, and again while the word lies outside [0, n)
+static __device__ __noinline__ uint32_t perm_walk(uint32_t x, uint32_t n, uint32_t b, uint64_t k0, uint64_t k1,
+                                                  uint64_t k2, uint64_t k3)
+{
+    uint32_t y = x;
+    do { y = feistel_enc(y, b, k0, k1, k2, k3); } while (y >= n);
+    return y;
+}
+// n > 32: the cycle through y walked backwards
+static __device__ __noinline__ uint32_t perm_walk_back(uint32_t y, uint32_t n, uint32_t b, uint64_t k0, uint64_t k1,
+                                                       uint64_t k2, uint64_t k3)
+{
+    uint32_t x = y;
+    do { x = feistel_dec(x, b, k0, k1, k2, k3); } while (x >= n);
     return x;
 }
 
@@ -189,15 +185,26 @@ struct Perm {
         b = n_ <= 1 ? 0u : 32u - uint32_t(__clz(n_ - 1u));
         k[0] = key.w[0]; k[1] = key.w[1]; k[2] = key.w[2]; k[3] = key.w[3];
     }
-    // pi(x0) and pi(x1), and pi^-1(y): one shared copy each (not inlined),
-    // given the key words as arguments like philox_draw
+    // pi(x0) and pi(x1) (a collision's two products), and pi^-1(y), for
+    // arguments below n; the key words travel as arguments like philox_draw's
     __device__ __forceinline__ void fwd2(uint32_t x0, uint32_t x1, int &y0, int &y1) const
     {
-        const uint64_t y = perm_fwd2(x0, x1, n, b, k[0], k[1], k[2], k[3]);
-        y0 = int(uint32_t(y));
-        y1 = int(uint32_t(y >> 32));
+        if (n <= 1) { y0 = y1 = 0; return; }
+        if (n <= 32) {
+            const uint64_t y = perm_rank2(x0, x1, n, k[0]);
+            y0 = int(uint32_t(y));
+            y1 = int(uint32_t(y >> 32));
+            return;
+        }
+        y0 = int(perm_walk(x0, n, b, k[0], k[1], k[2], k[3]));
+        y1 = int(perm_walk(x1, n, b, k[0], k[1], k[2], k[3]));
     }
-    __device__ __forceinline__ uint32_t inv(uint32_t y) const { return perm_inv(y, n, b, k[0], k[1], k[2], k[3]); }
+    __device__ __forceinline__ uint32_t inv(uint32_t y) const
+    {
+        if (n <= 1) return 0;
+        if (n <= 32) return perm_rank_inv(y, n, k[0]);
+        return perm_walk_back(y, n, b, k[0], k[1], k[2], k[3]);
+    }
 };
 
 // ---- warp / block reductions (fixed order, hence deterministic) --------------
