@@ -64,15 +64,15 @@ COMPARE_STEPS = 20          # steps of the oracle comparison (moment error, CPU 
 # leading stall reasons, keyed by the hash of csrc/collide.cu they were taken on; reported
 # as null once the kernel source differs.  See profiles/.
 NCU_TRAFFIC = {
-    "stationary": {"collide_sha": "82ba48567694e3b1", "launch": (256, 3), "bytes": 123997440 + 98976512,
-                   "issue_active_pct": 34.3, "warps_active_pct": 36.5,
-                   "stalls_per_issue": {"barrier": 7.15, "no_instruction": 2.86, "wait": 2.38, "long_scoreboard": 1.42}},
-    "shock": {"collide_sha": "82ba48567694e3b1", "launch": (128, 4), "bytes": 20232704 + 1046272,
-              "issue_active_pct": 18.0, "warps_active_pct": 22.9,
-              "stalls_per_issue": {"barrier": 6.98, "wait": 4.03, "short_scoreboard": 3.73, "no_instruction": 2.78}},
-    "batched": {"collide_sha": "82ba48567694e3b1", "launch": (256, 2), "bytes": 83904000 + 51153664,
-                "issue_active_pct": 30.9, "warps_active_pct": 24.8,
-                "stalls_per_issue": {"barrier": 4.93, "wait": 2.39, "long_scoreboard": 1.24, "no_instruction": 1.04}},
+    "stationary": {"collide_sha": "c09e78b001fece85", "launch": (256, 3), "bytes": 121858560 + 65395200,
+                   "issue_active_pct": 33.8, "warps_active_pct": 36.6,
+                   "stalls_per_issue": {"barrier": 7.18, "no_instruction": 3.49, "wait": 2.30, "long_scoreboard": 1.15}},
+    "shock": {"collide_sha": "c09e78b001fece85", "launch": (128, 4), "bytes": 19963392 + 124928,
+              "issue_active_pct": 18.1, "warps_active_pct": 22.9,
+              "stalls_per_issue": {"barrier": 6.96, "wait": 3.99, "short_scoreboard": 3.63, "no_instruction": 3.08}},
+    "batched": {"collide_sha": "c09e78b001fece85", "launch": (256, 2), "bytes": 83218688 + 24525312,
+                "issue_active_pct": 30.8, "warps_active_pct": 24.8,
+                "stalls_per_issue": {"barrier": 5.14, "wait": 2.35, "no_instruction": 1.20, "long_scoreboard": 1.05}},
 }
 
 # Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
