@@ -396,11 +396,12 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int64_t *counts, int n
 }
 
 // Kernel 4: refill the ghost cells of reservoir domains from their
-// Maxwellians (kRefillCTAs CTAs per ghost cell: a ghost cell takes thousands
-// of particles, each a chain of FP64 transcendentals), uniform positions in
-// the cell.  The ghost cell's max |v|^2 (zeroed by kernel 1) is the maximum
+// Maxwellians (kRefillCTAs CTAs per ghost cell, so that the two ghost cells of
+// a domain occupy every SM: a ghost cell takes thousands of particles, each a
+// chain of FP64 transcendentals, and GB300 has 2 FP64 lanes per SM), uniform
+// positions in the cell.  The ghost cell's max |v|^2 (zeroed by kernel 1) is the maximum
 // over the CTAs, taken on the bit patterns of the non-negative values.
-constexpr int kRefillCTAs = 32;
+constexpr int kRefillCTAs = 76;
 template <typename Real>
 __global__ void __launch_bounds__(kTT) refill_kernel(const trmc_domain *doms, int nd, int nc_total,
                                                      const int64_t *new_start, const uint64_t *cell_key,
