@@ -507,7 +507,7 @@ def ours(args):
         # the collide launch shape for this workload's cell sizes, measured on
         # the live state before timing
         from paper_1009_2768_gb300 import runtime as RT
-        tuned = RT.autotune(sim, steps=3)
+        tuned = RT.autotune(sim, steps=2, rounds=4)
         best = tuned["collide_best"]
         launch = {"threads": best[0], "ctas_per_sm": best[1],
                   "tuned_ms": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in tuned["collide"].items()},

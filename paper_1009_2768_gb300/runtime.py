@@ -13,8 +13,10 @@ simulation back where it found it.
   the workload transports: the sort's ping-pong buffers are then back in
   their original roles at the end of every replay.
 * autotune_collide times candidate (CTA size, CTAs per SM) shapes on the
-  live workload, keeps the fastest and then restores the state it stepped
-  (velocities, positions, cell starts, RAD depths, carries, step counters).
+  live workload in interleaved rounds (every candidate once per round, so a
+  drift over the sweep falls on all of them alike), keeps the one with the
+  smallest median and then restores the state it stepped (velocities,
+  positions, cell starts, RAD depths, carries, step counters).
   autotune_schedule then sweeps the work schedule inside a cell at that
   shape: the particles per warp (the largest tree level one warp takes alone)
   and the levels whose collisions are precomputed as records (collisions per
@@ -99,102 +101,68 @@ def _restore(sim, snap):
     st._fill()
 
 
-def autotune_collide(sim, shapes=DEFAULT_SHAPES, steps=6, flush_bytes=256 << 20):
-    """Time `steps` collide launches of the live workload for every (threads,
-    CTAs per SM) shape, with an L2 flush before each, and keep the fastest.
-    The simulation is put back in the state it had before tuning.  Returns
-    {shape: median collide ms} and leaves the best shape set."""
+def _sweep(sim, choices, apply, which, rounds, steps, flush_bytes):
+    """Time every choice in `rounds` interleaved rounds (each round sets every
+    choice in turn, takes one untimed step and `steps` timed ones, an L2
+    flush before each), so that a drift of the state or of the GPU over the
+    sweep falls on all choices alike; keep the choice with the smallest
+    median, restore the simulation and return ({choice: median ms}, best).
+    `which` picks the timed part of a step: 0 transport, 1 collide."""
     import torch
     flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     snap = _snapshot(sim)
-    times = {}
-    for shape in shapes:
-        T.trmc_set_collide_launch(sim.ctx, *shape)
-        sim.step()                                    # configure this shape outside the timing
-        ms = []
-        for _ in range(steps):
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            flush.zero_()
-            sim.step(events=ev)
-            torch.cuda.synchronize()
-            ms.append(ev[1].elapsed_time(ev[2]))
-        times[shape] = float(np.median(ms))
+    samples = {c: [] for c in choices}
+    for _ in range(rounds):
+        for c in choices:
+            apply(c)
+            sim.step()                                # configure this choice outside the timing
+            for _ in range(steps):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                flush.zero_()
+                sim.step(events=ev)
+                torch.cuda.synchronize()
+                samples[c].append(ev[which].elapsed_time(ev[which + 1]))
+    times = {c: float(np.median(v)) for c, v in samples.items()}
     best = min(times, key=times.get)
-    T.trmc_set_collide_launch(sim.ctx, *best)
+    apply(best)
     T.trmc_check(sim.ctx)
     _restore(sim, snap)
     torch.cuda.synchronize()
     return times, best
 
 
-def autotune_schedule(sim, choices=WORK_SCHEDULES, steps=6, flush_bytes=256 << 20):
-    """Time `steps` collide launches of the live workload for every work
-    schedule (particles per warp, records per thread) at the current launch
-    shape, with an L2 flush before each, keep the fastest and restore the
-    simulation.  Returns ({schedule: median collide ms}, best)."""
-    import torch
-    flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
-    torch.cuda.synchronize()
-    snap = _snapshot(sim)
-    times = {}
-    for sch in choices:
-        T.trmc_set_collide_schedule(sim.ctx, *sch)
-        sim.step()
-        ms = []
-        for _ in range(steps):
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            flush.zero_()
-            sim.step(events=ev)
-            torch.cuda.synchronize()
-            ms.append(ev[1].elapsed_time(ev[2]))
-        times[sch] = float(np.median(ms))
-    best = min(times, key=times.get)
-    T.trmc_set_collide_schedule(sim.ctx, *best)
-    T.trmc_check(sim.ctx)
-    _restore(sim, snap)
-    torch.cuda.synchronize()
-    return times, best
+def autotune_collide(sim, shapes=DEFAULT_SHAPES, steps=2, rounds=4, flush_bytes=256 << 20):
+    """The fastest (threads, CTAs per SM) collide launch shape for the live
+    workload (median collide time over interleaved rounds); the simulation is
+    put back in the state it had.  Returns ({shape: median ms}, best), the
+    best shape left set."""
+    return _sweep(sim, shapes, lambda c: T.trmc_set_collide_launch(sim.ctx, *c), 1, rounds, steps, flush_bytes)
 
 
-def autotune_transport(sim, choices=SORT_SCHEDULES, steps=6, flush_bytes=256 << 20):
-    """Time `steps` transports of the live workload for every sort schedule
-    (threads per CTA of the count and scatter kernels; 0 lets the library
-    pick from the mean cell size), with an L2 flush before each, keep the
-    fastest and restore the simulation.  Returns ({threads: median transport ms}, best);
-    a workload without transport returns ({}, None)."""
-    import torch
+def autotune_schedule(sim, choices=WORK_SCHEDULES, steps=2, rounds=4, flush_bytes=256 << 20):
+    """The fastest work schedule inside a cell (particles per warp, records
+    per thread) at the current launch shape, timed like autotune_collide.
+    Returns ({schedule: median ms}, best), the best left set."""
+    return _sweep(sim, choices, lambda c: T.trmc_set_collide_schedule(sim.ctx, *c), 1, rounds, steps, flush_bytes)
+
+
+def autotune_transport(sim, choices=SORT_SCHEDULES, steps=2, rounds=4, flush_bytes=256 << 20):
+    """The fastest sort schedule (threads per CTA of the counting sort's count
+    and scatter kernels; 0 lets the library pick from the mean cell size),
+    timed on the transport like autotune_collide.  A workload without
+    transport returns ({}, None)."""
     if not getattr(sim, "transports", False):
         return {}, None
-    flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
-    torch.cuda.synchronize()
-    snap = _snapshot(sim)
-    times = {}
-    for tt in choices:
-        T.trmc_set_transport_launch(sim.ctx, tt)
-        sim.step()
-        ms = []
-        for _ in range(steps):
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            flush.zero_()
-            sim.step(events=ev)
-            torch.cuda.synchronize()
-            ms.append(ev[0].elapsed_time(ev[1]))
-        times[tt] = float(np.median(ms))
-    best = min(times, key=times.get)
-    T.trmc_set_transport_launch(sim.ctx, best)
-    T.trmc_check(sim.ctx)
-    _restore(sim, snap)
-    torch.cuda.synchronize()
-    return times, best
+    return _sweep(sim, choices, lambda c: T.trmc_set_transport_launch(sim.ctx, c), 0, rounds, steps, flush_bytes)
 
 
-def autotune(sim, shapes=DEFAULT_SHAPES, schedules=SORT_SCHEDULES, steps=6, work=WORK_SCHEDULES):
+def autotune(sim, shapes=DEFAULT_SHAPES, schedules=SORT_SCHEDULES, steps=2, work=WORK_SCHEDULES, rounds=4):
     """The collide launch shape, then the work schedule inside a cell at that
     shape, and the sort schedule for the live workload (all left set; the
     simulation is restored)."""
-    collide_times, shape = autotune_collide(sim, shapes, steps)
-    work_times, wsched = autotune_schedule(sim, work, steps)
-    sort_times, sched = autotune_transport(sim, schedules, steps)
+    collide_times, shape = autotune_collide(sim, shapes, steps, rounds)
+    work_times, wsched = autotune_schedule(sim, work, steps, rounds)
+    sort_times, sched = autotune_transport(sim, schedules, steps, rounds)
     return {"collide": collide_times, "collide_best": shape, "work": work_times, "work_best": wsched,
             "sort": sort_times, "sort_best": sched}

@@ -115,11 +115,11 @@ def test_adaptive_order_does_not_change_results(precision):
 
 
 def test_autotuner_puts_the_simulation_back():
-    """The autotuners step the live workload once per candidate collide shape
-    or sort schedule and then restore it: the next step equals that of an
-    untuned twin."""
+    """The autotuners step the live workload for every candidate collide
+    shape, work schedule or sort schedule and then restore it: the next step
+    equals that of an untuned twin."""
     need_gpu()
-    from paper_1009_2768_gb300.runtime import autotune_collide, autotune_transport
+    from paper_1009_2768_gb300.runtime import autotune_collide, autotune_schedule, autotune_transport
     from paper_1009_2768_gb300.workloads import ShockTubes
     ref = ShockTubes((1e-2, 1e-3), n_cells=48, mean_per_cell=150, seed=9)
     tun = ShockTubes((1e-2, 1e-3), n_cells=48, mean_per_cell=150, seed=9)
@@ -130,6 +130,9 @@ def test_autotuner_puts_the_simulation_back():
     times, best = autotune_collide(tun, shapes=((64, 8), (128, 4), (96, 3)), steps=1)
     assert best in times and same(before, snapshot(tun))
     assert tun.step_index == ref.step_index
+    work_times, work = autotune_schedule(tun, choices=((0, 0), (16, 1), (512, 8)), steps=1, rounds=2)
+    assert set(work_times) == {(0, 0), (16, 1), (512, 8)} and work_times[work] == min(work_times.values())
+    assert same(before, snapshot(tun)) and tun.step_index == ref.step_index
     sort_times, sched = autotune_transport(tun, choices=(0, 64, 256), steps=1)
     assert set(sort_times) == {0, 64, 256} and sort_times[sched] == min(sort_times.values())
     assert same(before, snapshot(tun)) and tun.step_index == ref.step_index
