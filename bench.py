@@ -77,7 +77,7 @@ NCU_TRAFFIC = {
 
 # Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
 # runtime.autotune_collide's candidates on GB300 (--tune measures them again).
-LAUNCH = {"shock": (128, 4), "stationary": (256, 3), "batched": (256, 2), "bkw": (256, 2)}
+LAUNCH = {"shock": (128, 4), "stationary": (256, 3), "batched": (256, 2), "bkw": (512, 1)}
 
 
 def collide_sha():

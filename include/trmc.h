@@ -179,9 +179,11 @@ const char *trmc_last_error(const trmc_ctx *ctx);
 trmc_status trmc_check(trmc_ctx *ctx, void *stream);
 
 /* Launch shape of the collision kernel: CTA size (a multiple of 32 in
- * [32, 256]) and the number of CTAs resident per SM the shared-memory budget
- * is split for (1..16).  Defaults 128 and 4.  Results do not depend on it;
- * only speed does (the autotuner in the binding sweeps it). */
+ * [32, 512]; above 256 every launch runs the kernel built for cells too large
+ * for shared memory, which stages the others whole all the same) and the
+ * number of CTAs resident per SM the shared-memory budget is split for
+ * (1..16).  Defaults 128 and 4.  Results do not depend on it; only speed does
+ * (the autotuner in the binding sweeps it). */
 trmc_status trmc_set_collide_launch(trmc_ctx *ctx, int32_t threads, int32_t ctas_per_sm);
 
 /* Work schedule of the collision kernel inside a cell.  The paper has no

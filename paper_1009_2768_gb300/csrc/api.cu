@@ -160,8 +160,8 @@ trmc_status trmc_check(trmc_ctx *ctx, void *stream)
 trmc_status trmc_set_collide_launch(trmc_ctx *ctx, int32_t threads, int32_t ctas_per_sm)
 {
     if (!ctx) return TRMC_ERR_ARG;
-    if (threads < 32 || threads > kThreads || threads % 32 != 0)
-        return set_error(ctx, TRMC_ERR_ARG, "threads must be a multiple of 32 in [32, 256]");
+    if (threads < 32 || threads > kThreadsDual || threads % 32 != 0)
+        return set_error(ctx, TRMC_ERR_ARG, "threads must be a multiple of 32 in [32, 512]");
     if (ctas_per_sm < 1 || ctas_per_sm > 16) return set_error(ctx, TRMC_ERR_ARG, "ctas_per_sm outside [1, 16]");
     ctx->collide_threads = threads;
     ctx->collide_ctas_per_sm = ctas_per_sm;

@@ -2031,9 +2031,13 @@ __global__ void __launch_bounds__(32) bigsum_kernel(const Real *__restrict__ gx,
 // Registers: the FP32 whole-mode kernel is built for three 256-thread CTAs
 // per SM (at most 85 registers a thread; it then spills a few bytes), which
 // runs the stationary shock's 2500-particle cells 4 % faster than two; the
-// others, with more live FP64 state or the compact path, for two.
+// FP64 one, with more live FP64 state, for two; the dual-mode kernels for one
+// CTA of up to 512 threads, the same 128 registers a thread as two of 256: a
+// problem of one very large cell (the BKW cell of 1e5 particles) runs its
+// parallel phases on twice the threads of one SM.
 template <typename Real, int Mode, int TV>
-__global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 && Mode == kWhole ? 3 : 2) collide_kernel(Args a)
+__global__ void __launch_bounds__(Mode == kDual ? kThreadsDual : kThreads,
+                                  Mode == kDual ? 1 : sizeof(Real) == 4 ? 3 : 2) collide_kernel(Args a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ Sh<Real> sh;
@@ -2230,9 +2234,11 @@ trmc_status launch_t(trmc_ctx *ctx, trmc_state *st, const trmc_collide_params *p
     // the mode: staged whole, unless the previous launch met a cell too large
     // for shared memory and for the whole-mode rule above (the first launch
     // of a context does not know: dual)
+    // (CTAs of more than kThreads threads run the dual kernel, the only one
+    // built for them; it stages the cells that fit whole all the same)
     const uint64_t nmax = ctx->n_max_host ? *ctx->n_max_host : ~0ull;
-    bool dual = !fits_whole<Real>(nmax, smem);
-    const bool near = dual && near_whole<Real>(nmax, smem);
+    bool dual = threads > kThreads || !fits_whole<Real>(nmax, smem);
+    const bool near = dual && threads <= kThreads && near_whole<Real>(nmax, smem);
     CollideFn fn = nullptr;
     cudaError_t e = collide_fn<Real>(ctx->device, int(ctx->smem_optin), dual && !near, prm, fn);
     if (e != cudaSuccess) return cuda_error(ctx, e, "cudaFuncSetAttribute(collide)");

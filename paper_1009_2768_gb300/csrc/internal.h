@@ -58,7 +58,8 @@ struct trmc_ctx {
 namespace trmc {
 
 constexpr int kMC = TRMC_MCAP;
-constexpr int kThreads = 256;         // collide CTA size
+constexpr int kThreads = 256;         // collide CTA size, at most (whole-staging kernels)
+constexpr int kThreadsDual = 512;     // the dual-mode kernels', and the most a context may set
 
 trmc_status set_error(trmc_ctx *ctx, trmc_status code, const std::string &msg);
 // Host checks of a collision step's state and parameters, shared by

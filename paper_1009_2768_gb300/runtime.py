@@ -30,7 +30,7 @@ import numpy as np
 
 from . import trmc as T
 
-DEFAULT_SHAPES = ((256, 3), (256, 2), (128, 4), (128, 3), (160, 3), (192, 2), (64, 8))
+DEFAULT_SHAPES = ((256, 3), (256, 2), (128, 4), (128, 3), (160, 3), (192, 2), (64, 8), (512, 1))
 SORT_SCHEDULES = (0, 64, 128, 256)     # transport threads per cell CTA (0: by mean cell size)
 # (particles per warp, records per thread); (0, 0) is the library's default
 WORK_SCHEDULES = ((0, 0), (32, 4), (128, 4), (512, 4), (0, 2), (0, 8))

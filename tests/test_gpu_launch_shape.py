@@ -13,7 +13,7 @@ from tests.gpu_common import T, need_gpu, torch, ensure_built
 pytestmark = pytest.mark.gpu
 
 COUNTS = [2, 3, 17, 64, 255, 257, 889, 2500, 6000, 9001]
-SHAPES = [(64, 8), (128, 4), (256, 2), (96, 3), (32, 8)]
+SHAPES = [(64, 8), (128, 4), (256, 2), (96, 3), (32, 8), (512, 1)]
 
 
 def run_shape(precision, shape, params, counts, steps=2, carry=False, schedule=None):
