@@ -64,15 +64,15 @@ COMPARE_STEPS = 20          # steps of the oracle comparison (moment error, CPU 
 # leading stall reasons, keyed by the hash of csrc/collide.cu they were taken on; reported
 # as null once the kernel source differs.  See profiles/.
 NCU_TRAFFIC = {
-    "stationary": {"collide_sha": "c09e78b001fece85", "launch": (256, 3), "bytes": 121858560 + 65395200,
-                   "issue_active_pct": 33.8, "warps_active_pct": 36.6,
-                   "stalls_per_issue": {"barrier": 7.18, "no_instruction": 3.49, "wait": 2.30, "long_scoreboard": 1.15}},
-    "shock": {"collide_sha": "c09e78b001fece85", "launch": (128, 4), "bytes": 19963392 + 124928,
-              "issue_active_pct": 18.1, "warps_active_pct": 22.9,
-              "stalls_per_issue": {"barrier": 6.96, "wait": 3.99, "short_scoreboard": 3.63, "no_instruction": 3.08}},
-    "batched": {"collide_sha": "c09e78b001fece85", "launch": (256, 2), "bytes": 83218688 + 24525312,
-                "issue_active_pct": 30.8, "warps_active_pct": 24.8,
-                "stalls_per_issue": {"barrier": 5.14, "wait": 2.35, "no_instruction": 1.20, "long_scoreboard": 1.05}},
+    "stationary": {"collide_sha": "674f83b37ff2bfd5", "launch": (256, 3), "bytes": 121820928 + 65572352,
+              "issue_active_pct": 34.1, "warps_active_pct": 36.7,
+              "stalls_per_issue": {"barrier": 7.15, "no_instruction": 3.44, "wait": 2.30, "long_scoreboard": 1.15}},
+    "shock": {"collide_sha": "674f83b37ff2bfd5", "launch": (128, 4), "bytes": 19977728 + 96768,
+              "issue_active_pct": 17.7, "warps_active_pct": 22.8,
+              "stalls_per_issue": {"barrier": 7.06, "wait": 3.99, "short_scoreboard": 3.66, "no_instruction": 3.06}},
+    "batched": {"collide_sha": "674f83b37ff2bfd5", "launch": (256, 2), "bytes": 83151104 + 24946944,
+              "issue_active_pct": 30.9, "warps_active_pct": 24.8,
+              "stalls_per_issue": {"barrier": 5.12, "wait": 2.35, "no_instruction": 1.22, "long_scoreboard": 1.05}},
 }
 
 # Collide launch shape (threads per CTA, CTAs per SM) per workload: the fastest of
