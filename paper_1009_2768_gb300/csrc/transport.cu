@@ -213,8 +213,16 @@ __global__ void cfl_kernel(const trmc_domain *doms, int nd, int nc_total, const 
     // maximum on the bit patterns of the non-negative values: no FP64 instruction
     // per cell; the step itself is computed once, by thread 0
     long long vb = 0;
-    for (int c = threadIdx.x; c < D.n_cells; c += blockDim.x)
-        vb = max(vb, __double_as_longlong(cell_vmax2[D.cell_begin + c]));
+    for (int c0 = threadIdx.x; c0 < D.n_cells; c0 += 4 * blockDim.x) {
+        long long t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * int(blockDim.x);
+            t[u] = c < D.n_cells ? __double_as_longlong(cell_vmax2[D.cell_begin + c]) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vb = max(vb, t[u]);
+    }
     const double vm = block_max_nonneg(__longlong_as_double(vb), red);
     if (threadIdx.x == 0) {
         const double dx = __ddiv_rn(__dsub_rn(D.x_hi, D.x_lo), double(interior_cells(D)));
@@ -295,7 +303,7 @@ __global__ void __launch_bounds__(kTT) count_kernel(const Real *x, const Real *v
     if constexpr (Vec) {
         // one 16-byte vector of x and of v_x per thread and step
         constexpr int V = Vec16<Real>::V;
-        constexpr int U = 2;                        // vectors issued together
+        constexpr int U = 4;                        // vectors issued together
         const int64_t g0 = b / V, g1 = (e + V - 1) / V;
         for (int64_t q0 = g0 + threadIdx.x; q0 < g1; q0 += U * blockDim.x) {
             Vec16<Real> xs[U], vs[U];
